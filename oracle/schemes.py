@@ -1,0 +1,111 @@
+"""Oracle: time integrators that consume the successive-convolution partial sums.
+
+TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__``.
+
+* Heat (Sec. 2.1 diffusion, Sec. 2.5 RK coupling): u_t = kappa Lap u with
+  d_xx ~ -alpha^2 S_P per axis (Eq. "representation of second derivative in
+  D"), alpha = beta/sqrt(kappa dt) (Sec. 2.1), so dt*F(u) = -beta^2 sum_d S_{P,d}[u].
+  Integrator (reading: the paper couples an s-stage RK method with an s-term
+  partial sum, Sec. 2.5; we take the 3-stage SSP Runge-Kutta method in
+  Shu-Osher form with P = 3).
+* Wave (Sec. 2.1 wave equation): central differencing in time with
+  d_xx ~ -alpha^2 S_P, alpha = beta/(c dt):
+      u^{n+1} = 2u^n - u^{n-1} - beta^2 sum_d S_{P,d}[u^n].
+  Reading: a start from rest (u_t = 0) takes the second-order Taylor step
+  u^1 = u^0 - beta^2/2 sum_d S_{P,d}[u^0].
+* Hamilton-Jacobi (Sec. 2.5, numerical Hamiltonian; Sec. 4.4 adaptive rule;
+  Algorithm 1): u^{n+1} = u^n - dt^n H^(u_x^-, u_x^+, u_y^-, u_y^+) with
+  d_x^- u = alpha D_R[u], d_x^+ u = -alpha D_L[u] (P = 1, Eq.
+  "representations used in paper"), the monotone (Lax-Friedrichs) numerical
+  Hamiltonian H^ = H(mean) + sum_d r_d (v_d^- - v_d^+)/2 and
+  dt^n = CFL * min_d(dx_d / c_d) from the wave speeds of the previous step
+  ("lagged", Algorithm 1).  Readings: H = |grad u|^2/2 so r_d =
+  max(|v_d^-|, |v_d^+|) pointwise (local LF); c_d = max over the grid of r_d;
+  alpha = beta/(CFL dx) (= beta/(c_max dt) whenever the CFL rule sets dt, so
+  nu = beta/CFL stays fixed); dt is capped at 10 dx when c -> 0; at the first
+  step the speeds of u^0 serve as the lagged speeds.
+"""
+import numpy as np
+
+from .sweep import partial_sum, BC_PERIODIC
+
+# 3-stage SSP RK in Shu-Osher form: u_s = a0 u^n + a1 (u_{s-1} + dt F(u_{s-1}))
+SSPRK3 = ((0.0, 1.0), (0.75, 0.25), (1.0 / 3.0, 2.0 / 3.0))
+
+
+def heat_rhs_dt(u, dxs, dt, kappa, beta, bc, npts, P):
+    """dt * F(u) = -kappa alpha^2 dt sum_d S_{P,d}[u] = -beta^2 sum_d S_{P,d}[u]."""
+    alpha = beta / np.sqrt(kappa * dt)
+    acc = np.zeros_like(u)
+    for ax in range(u.ndim):
+        acc += partial_sum(u, ax, alpha, dxs[ax], "0", bc[ax], npts, P)
+    return -kappa * alpha * alpha * dt * acc
+
+
+def heat_step(u, dxs, dt, kappa=1.0, beta=0.6, bc=None, npts=3, P=3):
+    """One SSP-RK3 step of the heat equation."""
+    bc = bc or [BC_PERIODIC] * u.ndim
+    un = np.asarray(u, dtype=np.float64)
+    us = un
+    for a0, a1 in SSPRK3:
+        us = a0 * un + a1 * (us + heat_rhs_dt(us, dxs, dt, kappa, beta, bc, npts, P))
+    return us
+
+
+def wave_step(u, u_prev, dxs, dt, c=1.0, beta=0.8, bc=None, npts=6, P=2, from_rest=False):
+    """One step of the wave equation; returns u^{n+1}."""
+    bc = bc or [BC_PERIODIC] * u.ndim
+    alpha = beta / (c * dt)
+    S = np.zeros_like(u, dtype=np.float64)
+    for ax in range(u.ndim):
+        S += partial_sum(u, ax, alpha, dxs[ax], "0", bc[ax], npts, P)
+    # c^2 dt^2 d_xx ~ -c^2 dt^2 alpha^2 S = -beta^2 S
+    if from_rest:
+        return u - 0.5 * beta * beta * S
+    return 2.0 * u - u_prev - beta * beta * S
+
+
+def hj_derivatives(u, alpha, dxs, npts=5, weights="wenoz", weight_fn=None):
+    """(v_d^-, v_d^+) for every axis d: v^- = alpha D_R[u], v^+ = -alpha D_L[u]."""
+    out = []
+    for ax in range(u.ndim):
+        dm = alpha * partial_sum(u, ax, alpha, dxs[ax], "R", BC_PERIODIC, npts, 1, weights, weight_fn)
+        dp = -alpha * partial_sum(u, ax, alpha, dxs[ax], "L", BC_PERIODIC, npts, 1, weights, weight_fn)
+        out.append((dm, dp))
+    return out
+
+
+def hj_hamiltonian(ders):
+    """Local Lax-Friedrichs numerical Hamiltonian for H(p) = |p|^2/2 and the
+    per-axis wave speeds c_d = max_grid r_d (Sec. 2.5, Sec. 4.4)."""
+    Hh = 0.0
+    speeds = []
+    for dm, dp in ders:
+        r = np.maximum(np.abs(dm), np.abs(dp))
+        mean = 0.5 * (dm + dp)
+        Hh = Hh + 0.5 * mean * mean + r * 0.5 * (dm - dp)
+        speeds.append(float(r.max()))
+    return Hh, speeds
+
+
+def hj_dt(speeds, dxs, cfl):
+    """dt = CFL * min_d dx_d / c_d (Eq. "adaptive time rule"), capped at 10 dx."""
+    cands = [cfl * dx / c for dx, c in zip(dxs, speeds) if c > 0.0]
+    cap = 10.0 * min(dxs)
+    return min(cands + [cap])
+
+
+def hj_initial_speeds(u, dxs, cfl=1.5, beta=1.0, npts=5, weights="wenoz", weight_fn=None):
+    alpha = beta / (cfl * min(dxs))
+    _, speeds = hj_hamiltonian(hj_derivatives(u, alpha, dxs, npts, weights, weight_fn))
+    return speeds
+
+
+def hj_step(u, dxs, lagged_speeds, cfl=1.5, beta=1.0, npts=5, weights="wenoz", weight_fn=None):
+    """One forward-Euler step u^{n+1} = u^n - dt^n H^; returns
+    (u^{n+1}, dt^n, speeds of u^n) -- the speeds become the lagged speeds of
+    the next step (Algorithm 1)."""
+    alpha = beta / (cfl * min(dxs))
+    dt = hj_dt(lagged_speeds, dxs, cfl)
+    Hh, speeds = hj_hamiltonian(hj_derivatives(u, alpha, dxs, npts, weights, weight_fn))
+    return u - dt * Hh, dt, speeds

@@ -1,0 +1,96 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the bench.
+
+This module holds no arithmetic of the method: it only draws the initial
+states and problem lists of the five workloads, with numpy's PCG64 generator,
+so that the CUDA path and the FP64 oracle are fed identical arrays.
+
+Workloads (grid conventions: periodic axes store the N unique points
+x_i = lo + i*h, h = (hi-lo)/N; Dirichlet axes store all nodes including both
+boundary nodes, h = (hi-lo)/(n-1)):
+
+* ``heat_modes``   -- 2-D periodic [0,1]^2, u0 = sum of 8 Fourier modes
+                      a_m cos(2 pi (kx_m x + ky_m y)), (kx, ky) ~ U{1..8}^2,
+                      a_m ~ N(0,1).
+* ``wave_bumps``   -- 3-D [0,1]^3 Dirichlet, u0 = sum of 16 Gaussian bumps
+                      exp(-|x-x_k|^2 / (2 s_k^2)), x_k ~ U[0,1]^3,
+                      s_k ~ U[0.02, 0.1]; boundary nodes set to 0; u_t = 0.
+* ``batched_sides``-- 64 side lengths drawn uniformly from
+                      {128, 256, 512, 1024, 2048}.
+* ``hj_initial``   -- 2-D periodic [0,2pi]^2, u0 = -cos x - cos y plus iid
+                      1e-3 N(0,1) noise per node.
+"""
+import numpy as np
+
+SEED_HEAT = 1
+SEED_WAVE = 2
+SEED_BATCH = 3
+SEED_HJ = 4
+SEED_HJ_LARGE = 5
+
+
+def rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def heat_modes(n, seed=SEED_HEAT, nmodes=8, kmax=8):
+    g = rng(seed)
+    k = g.integers(1, kmax + 1, size=(nmodes, 2))
+    a = g.standard_normal(nmodes)
+    x = np.arange(n) / n
+    u = np.zeros((n, n))          # [y][x]
+    for m in range(nmodes):
+        u += a[m] * np.cos(2 * np.pi * (k[m, 0] * x[None, :] + k[m, 1] * x[:, None]))
+    return u
+
+
+def wave_bump_params(seed=SEED_WAVE, nbumps=16):
+    g = rng(seed)
+    centres = g.uniform(0.0, 1.0, size=(nbumps, 3))
+    widths = g.uniform(0.02, 0.1, size=nbumps)
+    return centres, widths
+
+
+def wave_bumps(n, seed=SEED_WAVE, nbumps=16, dtype=np.float64):
+    """[z][y][x] array of n^3 nodes on [0,1]^3 (h = 1/(n-1))."""
+    centres, widths = wave_bump_params(seed, nbumps)
+    x = np.arange(n) / (n - 1)
+    u = np.zeros((n, n, n), dtype=dtype)
+    for (cx, cy, cz), s in zip(centres, widths):
+        gx = np.exp(-(x - cx) ** 2 / (2 * s * s))
+        gy = np.exp(-(x - cy) ** 2 / (2 * s * s))
+        gz = np.exp(-(x - cz) ** 2 / (2 * s * s))
+        u += (gz[:, None, None] * gy[None, :, None]) * gx[None, None, :]
+    zero_boundary(u)
+    return u
+
+
+def zero_boundary(u):
+    for ax in range(u.ndim):
+        sl = [slice(None)] * u.ndim
+        sl[ax] = 0
+        u[tuple(sl)] = 0.0
+        sl[ax] = -1
+        u[tuple(sl)] = 0.0
+    return u
+
+
+def batched_sides(seed=SEED_BATCH, count=64):
+    g = rng(seed)
+    return [int(s) for s in g.choice([128, 256, 512, 1024, 2048], size=count)]
+
+
+def batched_heat(seed=SEED_BATCH, count=64, sides=None):
+    sides = sides if sides is not None else batched_sides(seed, count)
+    return [heat_modes(s, seed=3000 + i) for i, s in enumerate(sides)]
+
+
+def hj_initial(n, seed=SEED_HJ, noise=1e-3):
+    g = rng(seed)
+    x = 2 * np.pi * np.arange(n) / n
+    u = -np.cos(x)[None, :] - np.cos(x)[:, None]
+    return u + noise * g.standard_normal((n, n))
+
+
+def random_lines(shape, seed=0):
+    """Generic seeded test field, N(0,1) iid."""
+    return rng(seed).standard_normal(shape)
