@@ -1,0 +1,305 @@
+"""Benchmark: DOF updates/s of the method-of-lines-transpose wave step.
+
+Workload (one step = every sweep of the method's hot path over the grid):
+3-D linear wave u_tt = c^2 Lap u, c = 1, on [0,1]^3 with Dirichlet
+boundaries, 512^3 nodes, P = 2 successive-convolution terms, 6-point
+quadrature, dt = 2h, beta = 0.8, sweeps in FP32 with the boundary solve and
+the leapfrog update in FP64; u0 = 16 seeded Gaussian bumps (synthetic).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``value`` is device-timed (inputs resident in HBM),
+``e2e`` goes through the same C-ABI call with pinned host buffers copied in
+and the new state copied out every step.  ``--impl reference`` times the FP64
+CPU oracle (numpy) on a bounded sample of the same workload.  Under torchrun
+(N > 1) every rank advances its own replica (the path does not shard across
+GPUs: replicas only); rank 0 prints.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N = 512
+P = 2
+QUAD = 6
+BETA = 0.8
+METRIC = "DOF updates/sec (3-D wave, 512^3, P=2) on GB300"
+UNIT = "DOF/s"
+WORKLOAD = {
+    "workload": "wave3d_dirichlet_512^3_P2_quad6_beta0.8_dt2h",
+    "grid": [N, N, N],
+    "P": P,
+    "quad_points": QUAD,
+    "precision": "FP32 sweeps, FP64 boundary solve and leapfrog update",
+    "l2": "inputs larger than L2 (2 x 1.07 GB FP64 state + 0.5 GB FP32 copy)",
+}
+# algorithmic bytes per DOF of each pass (see DESIGN): x: read FP32 copy,
+# write FP32 accumulator; y: read copy + acc, write acc; z: read copy + acc +
+# u^n + u^{n-1} (FP64), write u^{n+1} (FP64) + its FP32 copy
+BYTES_PER_DOF = {"x": 8, "y": 12, "z": 36}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def cpu_oracle_sample(seconds_target=15.0, k=None):
+    """Times the FP64 oracle on a bounded sample: S_2 along x and y on k
+    complete z-planes of the 512^3 grid, S_2 along z on the same number of
+    complete z-lines, and the FP64 leapfrog update of those points.  Returns
+    (DOF/s, description, cores)."""
+    import numpy as np
+    from oracle import sweep
+    from paper_2007_03041_gb300 import workloads
+    h = 1.0 / (N - 1)
+    alpha = BETA / (2 * h)
+    g = workloads.rng(7)
+    if k is None:
+        k = 2
+    slab = g.standard_normal((k, N, N))
+    zl = g.standard_normal((N, k, N))
+    t0 = time.perf_counter()
+    sx = sweep.partial_sum(slab, 2, alpha, h, "0", "dirichlet", QUAD, P)
+    sy = sweep.partial_sum(slab, 1, alpha, h, "0", "dirichlet", QUAD, P)
+    sz = sweep.partial_sum(zl, 0, alpha, h, "0", "dirichlet", QUAD, P)
+    new = 2.0 * slab - slab - BETA * BETA * (sx + sy + np.moveaxis(sz, 0, 1).reshape(slab.shape))
+    el = time.perf_counter() - t0
+    del new
+    pts = k * N * N
+    return pts / el, "S_2 along x, y on %d complete 512^2 z-planes, along z on %d complete z-lines, and the update " \
+                     "(%d DOF of the 512^3 grid)" % (k, k * N, pts), 1, el
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_oracle_sample(k=1)
+    tot_pts, tot_t = 0, 0.0
+    desc = None
+    for _ in range(args.steps):
+        v, desc, cores, el = cpu_oracle_sample(k=1)
+        tot_pts += N * N
+        tot_t += el
+    value = tot_pts / tot_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(WORKLOAD, sample=desc),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    from paper_2007_03041_gb300 import molt as M
+    from paper_2007_03041_gb300 import workloads
+
+    ws, rank, local = dist_env()
+    dist = ws > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    h = 1.0 / (N - 1)
+    dt = 2 * h
+    d = M.make_desc((N, N, N), bc=[M.BC_DIRICHLET] * 3, P=P, quad_points=QUAD, beta=BETA, pde=M.PDE_WAVE,
+                    c=1.0, dt=dt, prec=M.PREC_F32_F64UPDATE)
+    stream = torch.cuda.current_stream(dev)
+    ctx = M.molt_create(d, stream)
+    # synthetic initial state (16 seeded bumps; generated on the device)
+    cen, wid = workloads.wave_bump_params()
+    x = torch.arange(N, device=dev, dtype=torch.float64) / (N - 1)
+    u = torch.zeros((N, N, N), device=dev, dtype=torch.float64)
+    for (cx, cy, cz), s in zip(cen, wid):
+        gx = torch.exp(-(x - cx) ** 2 / (2 * s * s))
+        gy = torch.exp(-(x - cy) ** 2 / (2 * s * s))
+        gz = torch.exp(-(x - cz) ** 2 / (2 * s * s))
+        u += gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+    for ax in range(3):
+        u.select(ax, 0).zero_()
+        u.select(ax, N - 1).zero_()
+    up = torch.empty_like(u)
+    t = M.molt_step(ctx, u, up, nsteps=1, t=[0.0])       # start from rest
+    t = M.molt_step(ctx, u, up, nsteps=args.warmup, t=t)  # warm-up
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    M.molt_set_option(ctx, M.OPT_PROFILE, 1)
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    t = M.molt_step(ctx, u, up, nsteps=args.steps, t=t)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    # launch events of the timed region (x pass; molt_profile_read clears all)
+    x_ms, x_cnt = M.molt_profile_read(ctx, M.KERNEL_ACC_SET)
+    M.molt_set_option(ctx, M.OPT_PROFILE, 0)
+    clk = clocks.stop()
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # per-kernel averages: x from the timed region, y and z from equal runs
+    per_kernel = {"x": x_ms / max(x_cnt, 1)}
+    for name, kind in (("y", M.KERNEL_ACC_ADD), ("z", M.KERNEL_WAVE_FINAL)):
+        M.molt_set_option(ctx, M.OPT_PROFILE, 1)
+        t = M.molt_step(ctx, u, up, nsteps=args.steps, t=t)
+        tot, cnt = M.molt_profile_read(ctx, kind)
+        M.molt_set_option(ctx, M.OPT_PROFILE, 0)
+        per_kernel[name] = tot / max(cnt, 1)
+
+    # end to end: pinned host buffers in, new state out, every step
+    e2e_steps = max(2, min(args.steps, 5))
+    hu = torch.empty_like(u, device="cpu").pin_memory()
+    hup = torch.empty_like(u, device="cpu").pin_memory()
+    hu.copy_(u)
+    hup.copy_(up)
+    barrier()
+    e0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        u.copy_(hu, non_blocking=True)
+        up.copy_(hup, non_blocking=True)
+        t = M.molt_step(ctx, u, up, nsteps=1, t=t)
+        hu.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - e0
+    M.molt_destroy(ctx)
+
+    dof = N ** 3
+    value = ws * dof * args.steps / (ms / 1e3)
+    e2e = {"value": ws * dof * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * dof,
+           "d2h_bytes_per_step": 8 * dof}
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    dom = "z"
+    achieved = BYTES_PER_DOF[dom] * dof / (per_kernel[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "sweep z-pass + leapfrog update (WAVE_FINAL)",
+                "peak_source": "measured" if peaks else "fallback",
+                "per_kernel_ms": per_kernel,
+                "algorithmic_bytes_per_dof": BYTES_PER_DOF}
+    if rank != 0:
+        return
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        # repeat the one-plane sample for about 10 s of CPU work
+        pts, el_tot, reps = 0, 0.0, 0
+        while el_tot < 10.0 or reps < 3:
+            v, desc, cores, el = cpu_oracle_sample(k=1)
+            pts += N * N
+            el_tot += el
+            reps += 1
+        cpu = {"value": pts / el_tot, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d repetitions of: %s" % (reps, desc)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": dict(WORKLOAD, parallelism="replicas" if ws > 1 else "1gpu"),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": 3 * args.steps + 1, "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * molt.h -- C ABI of the GB300 (sm_103a) library for the fast summation of
+ * the method-of-lines-transpose convolution operator and the successive-
+ * convolution partial sums it feeds (Christlieb, Guthrey, Sands,
+ * Thavappiragasm, "Parallel Algorithms for Successive Convolution",
+ * arXiv 2007.03041).
+ *
+ * The operators (Sec. 2.1, Eqs. "left/right-moving inverse op" and "second
+ * derivative inverse op"), for a line [a, b] and a parameter alpha:
+ *   L_R^{-1}[v](x) = alpha int_a^x e^{-alpha(x-s)} v(s) ds + A e^{-alpha(x-a)}
+ *   L_L^{-1}[v](x) = alpha int_x^b e^{-alpha(s-x)} v(s) ds + B e^{-alpha(b-x)}
+ *   L_0^{-1}[v](x) = alpha/2 int_a^b e^{-alpha|x-s|} v(s) ds
+ *                    + A e^{-alpha(x-a)} + B e^{-alpha(b-x)}
+ * D_* = I - L_*^{-1} (Eq. "D operators"), D^k = D(D^{k-1}) (Eq. "successive
+ * relation for D"), and the partial sums sum_{p=1}^P D^p that represent
+ * d_x^+ = -alpha sum D_L^p, d_x^- = alpha sum D_R^p, d_xx = -alpha^2 sum D_0^p
+ * (Sec. 2.2).  Discretisation: local integrals J_R/J_L by polynomial
+ * (optionally WENO-Z weighted) quadrature and the O(N) recurrences
+ * I_R(x_i) = e^{-alpha dx} I_R(x_{i-1}) + J_R(x_i) (Sec. 2.4), boundary
+ * constants A/B from periodicity (Sec. 2.3) or from the boundary values.
+ *
+ * Conventions shared by every entry point
+ *   - Arrays are C-ordered [z][y][x] (x fastest, contiguous); axis 0 is x,
+ *     axis 1 is y, axis 2 is z.  n[0], n[1], n[2] are the x, y, z sizes.
+ *   - Periodic axes store the N unique points x_i = lo + i*h, h = (hi-lo)/N.
+ *     Dirichlet axes store all nodes including both boundary nodes,
+ *     h = (hi-lo)/(n-1).
+ *   - All array pointers are DEVICE pointers, owned by the caller, dense and
+ *     16-byte aligned.  Element type: double, except under MOLT_PREC_F32
+ *     where it is float.
+ *   - Work is enqueued on the CUDA stream given to molt_create; calls return
+ *     before the GPU finishes, except where stated.
+ *   - Every entry point returns a molt_status; nothing throws across the ABI.
+ *     On failure, molt_last_error(ctx) describes the cause.  Unsupported
+ *     combinations return MOLT_EUNSUPPORTED; there is no CPU fallback.
+ */
+#ifndef MOLT_H
+#define MOLT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MOLT_OK = 0,
+  MOLT_EINVAL = 1,        /* bad argument or descriptor                       */
+  MOLT_ENOMEM = 2,        /* device allocation failed                         */
+  MOLT_ECUDA = 3,         /* a CUDA call failed                               */
+  MOLT_ETIMEOUT = 4,      /* a device-side wait gave up (kernel returned)     */
+  MOLT_ENONFINITE = 5,    /* a non-finite value reached the state             */
+  MOLT_EUNSUPPORTED = 6   /* valid but not implemented combination            */
+} molt_status;
+
+typedef enum { MOLT_BC_PERIODIC = 0, MOLT_BC_DIRICHLET = 1 } molt_bc;
+typedef enum { MOLT_OP_L = 0, MOLT_OP_R = 1, MOLT_OP_0 = 2 } molt_op;
+typedef enum {
+  MOLT_PREC_F64 = 0,            /* FP64 state, FP64 sweeps                         */
+  MOLT_PREC_F32_F64UPDATE = 1,  /* FP64 state, FP32 sweeps, FP64 A/B and update    */
+  MOLT_PREC_F32 = 2             /* FP32 state and sweeps, FP64 A/B                 */
+} molt_prec;
+typedef enum { MOLT_PDE_HEAT = 0, MOLT_PDE_WAVE = 1, MOLT_PDE_HJ = 2 } molt_pde;
+typedef enum { MOLT_W_LINEAR = 0, MOLT_W_WENOZ = 1, MOLT_W_LEARNED = 2 } molt_weights;
+
+/* One problem: a grid, its boundary types, the quadrature and the PDE whose
+ * time step molt_step advances.  Enumerations are stored as int. */
+typedef struct {
+  int ndim;              /* 1, 2 or 3                                            */
+  int64_t n[3];          /* points per axis (x, y, z); unused axes = 1           */
+  double lo[3], hi[3];   /* domain [lo, hi] per axis                             */
+  int bc[3];             /* molt_bc per axis                                     */
+  int P;                 /* terms of the partial sum, >= 1                       */
+  int quad_points;       /* 3, 5 or 6 (J_R stencils {-1..1}, {-3..1}, {-3..2})   */
+  int weights;           /* molt_weights; WENO-Z and learned need quad_points 5  */
+  double beta;           /* alpha parameter (Sec. 2.1)                           */
+  int pde;               /* molt_pde                                             */
+  double c;              /* wave speed (wave)                                    */
+  double diffusivity;    /* kappa (heat)                                         */
+  double cfl;            /* CFL number (Hamilton-Jacobi)                         */
+  double dt;             /* fixed time step; <= 0 selects the adaptive rule (HJ) */
+  int prec;              /* molt_prec                                            */
+} molt_desc;
+
+typedef struct molt_ctx molt_ctx;
+
+/* Create a context for `count` problems (count > 1: a batch advanced
+ * together by molt_step).  `cuda_stream` is a cudaStream_t (NULL = legacy
+ * default stream).  Validates every descriptor (n >= 1 per used axis,
+ * Dirichlet axes n >= 2, P >= 1, quad_points in {3,5,6}, ...), builds the
+ * quadrature tables (App. C weights by an independent moment series) and
+ * allocates the workspace.  Synchronous.  On success *out owns all of it. */
+molt_status molt_create(const molt_desc* descs, int count, void* cuda_stream, molt_ctx** out);
+
+/* out = sum_{p=1}^{P} D_op^p[in] along `axis` of problem `problem`
+ * (Eqs. "D operators", "successive relation for D", Sec. 2.2), with the
+ * given alpha (nu = alpha*h), the problem's boundary type on that axis and
+ * its quadrature/weights.  in and out: device arrays of the problem's full
+ * grid; in == out is allowed.  The element type follows the precision
+ * (double unless MOLT_PREC_F32); the sweeps run in FP32 unless MOLT_PREC_F64.
+ * Asynchronous. */
+molt_status molt_apply_D(molt_ctx* ctx, int problem, int axis, int op, int P, double alpha,
+                         const void* in, void* out);
+
+/* Advance every problem of the context by `nsteps` time steps.
+ *   u[i]       device state of problem i (updated in place).
+ *   u_prev[i]  wave: previous state u^{n-1} (updated to the state before the
+ *              final one); NULL for heat / Hamilton-Jacobi.
+ *   t_inout[i] time of problem i, host memory; advanced by the steps taken.
+ *              Wave: t_inout[i] == 0 starts from rest (u_t = 0) with a
+ *              second-order Taylor step and ignores u_prev[i] on entry.
+ * Heat: 3-stage SSP Runge-Kutta on dt*F = -beta^2 sum_d S_{P,d}, alpha =
+ * beta/sqrt(kappa dt).  Wave: u^{n+1} = 2u^n - u^{n-1} - beta^2 sum_d S_{P,d},
+ * alpha = beta/(c dt).  Hamilton-Jacobi (H = |grad u|^2/2, periodic):
+ * forward Euler with the local Lax-Friedrichs numerical Hamiltonian, one-
+ * sided derivatives alpha D_R, -alpha D_L, alpha = beta/(cfl h), dt from the
+ * wave speeds of the previous step (Algorithm 1; the speeds of u^0 on the
+ * first step).  Synchronous at the end (reads t and the device status). */
+molt_status molt_step(molt_ctx* ctx, void* const* u, void* const* u_prev, int nsteps, double* t_inout);
+
+/* Context options.
+ *   MOLT_OPT_TMA      1 (default): sweeps whose lines are an exact fit and
+ *                     whose arrays meet the tensor-copy alignment rules run
+ *                     the persistent TMA-fed kernel; 0: always the plain
+ *                     one-tile-per-CTA kernel.  Both compute the same values.
+ *   MOLT_OPT_PROFILE  1: record a CUDA event pair around every sweep launch
+ *                     (read back with molt_profile_read); 0 (default): off.
+ * Returns MOLT_EINVAL for an unknown option or value. */
+typedef enum { MOLT_OPT_TMA = 0, MOLT_OPT_PROFILE = 1 } molt_option;
+molt_status molt_set_option(molt_ctx* ctx, int option, int64_t value);
+
+/* Kinds of sweep launches, by the work their epilogue does. */
+typedef enum {
+  MOLT_KERNEL_STORE = 0,       /* molt_apply_D                                */
+  MOLT_KERNEL_ACC_SET = 1,     /* first axis of a step: acc = S               */
+  MOLT_KERNEL_ACC_ADD = 2,     /* middle axis: acc += S                       */
+  MOLT_KERNEL_HEAT_FINAL = 3,  /* last axis + Runge-Kutta stage update        */
+  MOLT_KERNEL_WAVE_FINAL = 4,  /* last axis + leapfrog update                 */
+  MOLT_KERNEL_HJ_X = 5,        /* Hamilton-Jacobi: first axes                 */
+  MOLT_KERNEL_HJ_Y = 6         /* Hamilton-Jacobi: last axis + update         */
+} molt_kernel_kind;
+
+/* With MOLT_OPT_PROFILE on: synchronises the stream, returns the summed
+ * device time (ms) and count of the recorded launches of `kind`, and clears
+ * every recorded launch.  Either output pointer may be NULL. */
+molt_status molt_profile_read(molt_ctx* ctx, int kind, double* total_ms, int64_t* launches);
+
+/* Release everything the context owns.  Synchronises its stream first. */
+molt_status molt_destroy(molt_ctx* ctx);
+
+/* Text of the last error recorded on ctx ("" if none); valid until the next
+ * call on ctx.  ctx may be NULL (then describes the last molt_create error). */
+const char* molt_last_error(const molt_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOLT_H */

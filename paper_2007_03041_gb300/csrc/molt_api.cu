@@ -1,0 +1,704 @@
+// C ABI of the library (include/molt.h): contexts, descriptor validation,
+// per-axis sweep planning and the time-step drivers.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "coeffs.h"
+#include "molt.h"
+#include "sweep_launch.h"
+
+using namespace molt;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Problem {
+  molt_desc d;
+  int64_t n[3];
+  double h[3];
+  int64_t total;
+  void* acc = nullptr;      // compute-type accumulator (total elements)
+  void* stage1 = nullptr;   // heat RK stages (state type)
+  void* stage2 = nullptr;
+  void* hx = nullptr;       // HJ H^_x (state type)
+  float* shadow = nullptr;  // FP32 copy of the state the sweeps read (mixed precision)
+  int64_t hj_steps = 0;     // HJ steps taken (rotates the speed slots)
+  bool hj_lag_ready = false;
+};
+
+}  // namespace
+
+struct molt_ctx {
+  cudaStream_t stream = nullptr;
+  std::vector<Problem> probs;
+  int* status_dev = nullptr;       // device status word
+  unsigned long long* speed_dev = nullptr;  // per problem: 2 speed slots (double bits)
+  double* t_dev = nullptr;         // per problem time (HJ)
+  bool no_tma = false;             // force the plain kernels (molt_set_option)
+  bool profile = false;
+  struct Rec { int kind; cudaEvent_t start, stop; };
+  std::vector<Rec> recs;
+  std::string err;
+};
+
+namespace {
+
+molt_status fail(molt_ctx* c, molt_status s, const std::string& m) {
+  if (c) c->err = m; else g_create_error = m;
+  return s;
+}
+
+molt_status cuda_fail(molt_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, MOLT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool is_f64_sweep(const molt_desc& d) { return d.prec == MOLT_PREC_F64; }
+bool is_f32_state(const molt_desc& d) { return d.prec == MOLT_PREC_F32; }
+bool is_mixed(const molt_desc& d) { return d.prec == MOLT_PREC_F32_F64UPDATE; }
+size_t state_bytes(const molt_desc& d) { return is_f32_state(d) ? 4 : 8; }
+size_t compute_bytes(const molt_desc& d) { return is_f64_sweep(d) ? 8 : 4; }
+
+std::string validate(const molt_desc& d) {
+  if (d.ndim < 1 || d.ndim > 3) return "ndim must be 1, 2 or 3";
+  for (int ax = 0; ax < 3; ++ax) {
+    if (ax < d.ndim) {
+      if (d.n[ax] < 1) return "n must be >= 1 on every used axis";
+      if (d.n[ax] > (1 << 20)) return "n above 2^20 points per axis";
+      if (d.bc[ax] != MOLT_BC_PERIODIC && d.bc[ax] != MOLT_BC_DIRICHLET) return "unknown boundary type";
+      if (d.bc[ax] == MOLT_BC_DIRICHLET && d.n[ax] < 2) return "Dirichlet axes need n >= 2";
+      if (!(d.hi[ax] > d.lo[ax])) return "hi must exceed lo";
+    } else if (d.n[ax] != 1 && d.n[ax] != 0) {
+      return "unused axes must have n = 1";
+    }
+  }
+  if (d.P < 1 || d.P > 64) return "P must be in 1..64";
+  if (d.quad_points != 3 && d.quad_points != 5 && d.quad_points != 6) return "quad_points must be 3, 5 or 6";
+  if (d.weights != MOLT_W_LINEAR && d.weights != MOLT_W_WENOZ && d.weights != MOLT_W_LEARNED)
+    return "unknown weights";
+  if (d.weights != MOLT_W_LINEAR && d.quad_points != 5) return "WENO weights need quad_points = 5";
+  if (d.prec < 0 || d.prec > 2) return "unknown precision";
+  if (d.pde < 0 || d.pde > 2) return "unknown pde";
+  if (!(d.beta > 0)) return "beta must be positive";
+  return "";
+}
+
+int64_t axis_n(const Problem& p, int ax) { return ax < p.d.ndim ? p.n[ax] : 1; }
+
+// Geometry of the lines along `ax` in a C-ordered [z][y][x] grid.
+LineGeom geom(const Problem& p, int ax) {
+  const int64_t nx = axis_n(p, 0), ny = axis_n(p, 1), nz = axis_n(p, 2);
+  LineGeom g{};
+  if (ax == 0) {
+    g.n = int(nx);
+    g.nlines = ny * nz;
+    g.nlo = ny;
+    g.s_lo = nx;
+    g.s_hi = nx * ny;
+    g.stride = 1;
+  } else if (ax == 1) {
+    g.n = int(ny);
+    g.nlines = nx * nz;
+    g.nlo = nx;
+    g.s_lo = 1;
+    g.s_hi = nx * ny;
+    g.stride = nx;
+  } else {
+    g.n = int(nz);
+    g.nlines = nx * ny;
+    g.nlo = nx;
+    g.s_lo = 1;
+    g.s_hi = nx;
+    g.stride = nx * ny;
+  }
+  return g;
+}
+
+struct Plan {
+  SweepArgs a;
+  int grid, block;
+  size_t smem;
+  int ax = 0;
+  bool use_tma = false;
+  TmaPlan tma;
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+int phys_host(int e) {
+  const int ee = e + kG;
+  return ee + (ee >> 4);
+}
+
+// Builds the kernel arguments for sum_{p<=P} D_mode^p along `ax` with alpha.
+molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, double alpha, Plan* out) {
+  SweepArgs& a = out->a;
+  std::memset(&a, 0, sizeof(a));
+  out->ax = ax;
+  out->use_tma = false;
+  a.g = geom(p, ax);
+  const int n = a.g.n;
+  a.bc = p.d.bc[ax];
+  a.mode = mode;
+  a.P = P;
+  a.contiguous = a.g.stride == 1;
+  a.alpha = alpha;
+  const double h = p.h[ax];
+  const double nu = alpha * h;
+  if (!(nu > 0) || !std::isfinite(nu)) return fail(c, MOLT_EINVAL, "alpha*h must be positive and finite");
+  QuadTable qt;
+  if (!build_quadrature(p.d.quad_points, nu, &qt)) return fail(c, MOLT_EINVAL, "quadrature table construction failed");
+  for (int i = 0; i < 6; ++i) a.c[i] = qt.c[i];
+  for (int r = 0; r < 3; ++r) {
+    for (int j = 0; j < 4; ++j) a.sub[r][j] = qt.sub[r][j];
+    a.d[r] = qt.d[r];
+  }
+  a.q = qt.q;
+  a.qE = std::exp(-nu * double(kE));
+  a.invq = std::exp(nu);
+  const int N = a.bc == MOLT_BC_PERIODIC ? n : n - 1;  // intervals
+  a.mu = std::exp(-nu * double(N));
+  a.inv1mmu = 1.0 / (-std::expm1(-nu * double(N)));
+  a.invdet = 1.0 / (-std::expm1(-2.0 * nu * double(N)));
+  // tile shape: nwl warps per line, W lines per CTA, <= kMaxThreads threads
+  const int nwl = (n + 32 * kE - 1) / (32 * kE);
+  if (nwl > kMaxThreads / 32) return fail(c, MOLT_EUNSUPPORTED, "line longer than 8192 points");
+  int W = (kMaxThreads / 32) / nwl;
+  int Wp = 1;
+  while (Wp * 2 <= W) Wp *= 2;
+  W = Wp;
+  while (W > 1 && (long long)W / 2 >= a.g.nlines) W /= 2;
+  const int cap = nwl * 32 * kE;
+  int LS = phys_host(cap + 3) + 1;
+  LS = (LS + 31) / 32 * 32 + (W < 32 ? 32 / W : 1);
+  a.W = W;
+  a.nwl = nwl;
+  a.LS = LS;
+  const size_t tb = compute_bytes(p.d);
+  size_t off = (size_t(4 * W) * 8 + size_t(W * nwl * 4) * tb + 15) & ~size_t(15);
+  out->smem = off + size_t(W) * LS * tb;
+  if (out->smem > 200 * 1024) return fail(c, MOLT_EUNSUPPORTED, "tile does not fit in shared memory");
+  out->block = 32 * nwl * W;
+  out->grid = int((a.g.nlines + W - 1) / W);
+  a.status = c->status_dev;
+  return MOLT_OK;
+}
+
+// Chooses the persistent TMA kernel when the line is an exact fit and the
+// array geometry meets the tensor-copy alignment rules (16-byte global
+// strides, a 16-byte multiple of bytes in the innermost box dimension, tiles
+// that do not straddle rows); otherwise the plain kernel runs.
+void plan_tma(const Problem& p, int ax, const void* in, size_t in_bytes, Plan* pl) {
+  pl->use_tma = false;
+  SweepArgs& a = pl->a;
+  if (!exact_fit(a)) return;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return;
+  if (reinterpret_cast<uintptr_t>(in) & 15) return;
+  const int64_t nx = axis_n(p, 0), ny = axis_n(p, 1), nz = axis_n(p, 2);
+  if ((nx * int64_t(in_bytes)) % 16 != 0) return;
+  const int n = a.g.n;
+  TmaGeom tg{};
+  tg.box_p = n < 256 ? n : 256;
+  if (n % tg.box_p != 0 || (tg.box_p & (tg.box_p - 1)) != 0) return;
+  tg.nbox = n / tg.box_p;
+  tg.nx = int(nx);
+  const int W = a.W;
+  CUtensorMap map;
+  const CUtensorMapDataType dt = in_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r;
+  if (ax == 0) {
+    tg.kind = 0;
+    cuuint64_t dims[2] = {cuuint64_t(nx), cuuint64_t(ny * nz)};
+    cuuint64_t strides[1] = {cuuint64_t(nx * in_bytes)};
+    cuuint32_t box[2] = {cuuint32_t(tg.box_p), cuuint32_t(W)};
+    r = enc(&map, dt, 2, const_cast<void*>(in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    if ((W * in_bytes) % 16 != 0 || nx % W != 0) return;
+    tg.kind = ax == 1 ? 1 : 2;
+    cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(ny), cuuint64_t(nz)};
+    cuuint64_t strides[2] = {cuuint64_t(nx * in_bytes), cuuint64_t(nx * ny * in_bytes)};
+    cuuint32_t box[3] = {cuuint32_t(W), ax == 1 ? cuuint32_t(tg.box_p) : 1u, ax == 2 ? cuuint32_t(tg.box_p) : 1u};
+    r = enc(&map, dt, 3, const_cast<void*>(in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (r != CUDA_SUCCESS) return;
+  tg.tx_bytes = unsigned(size_t(tg.nbox) * tg.box_p * W * in_bytes);
+  const size_t bar_off = (pl->smem + 15) & ~size_t(15);
+  const size_t stage_off = (bar_off + 16 + 127) & ~size_t(127);
+  const size_t total = stage_off + size_t(tg.tx_bytes);
+  if (total > 210 * 1024) return;
+  pl->tma.tg = tg;
+  pl->tma.map = map;
+  pl->tma.smem = total;
+  pl->use_tma = true;
+}
+
+#define TMA (pl.use_tma ? &pl.tma : nullptr)
+
+template <typename T, typename TIN, typename TST>
+cudaError_t dispatch_lin(int epi, const Plan& pl, cudaStream_t s) {
+  const SweepArgs& a = pl.a;
+  switch (epi) {
+    case EPI_STORE: return launch_sweep<T, TIN, TST, false, EPI_STORE>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    case EPI_ACC_SET: return launch_sweep<T, TIN, TST, false, EPI_ACC_SET>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    case EPI_ACC_ADD: return launch_sweep<T, TIN, TST, false, EPI_ACC_ADD>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    case EPI_HEAT_FINAL: return launch_sweep<T, TIN, TST, false, EPI_HEAT_FINAL>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    case EPI_WAVE_FINAL: return launch_sweep<T, TIN, TST, false, EPI_WAVE_FINAL>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+template <typename T>
+cudaError_t dispatch_same(bool weno, int epi, const Plan& pl, cudaStream_t s) {
+  const SweepArgs& a = pl.a;
+  if (weno) {
+    if (epi == EPI_STORE) return launch_sweep<T, T, T, true, EPI_STORE>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    if (epi == EPI_HJ_X) return launch_sweep<T, T, T, true, EPI_HJ_X>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    if (epi == EPI_HJ_Y) return launch_sweep<T, T, T, true, EPI_HJ_Y>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    return cudaErrorNotSupported;
+  }
+  if (epi == EPI_HJ_X) return launch_sweep<T, T, T, false, EPI_HJ_X>(a, TMA, pl.grid, pl.block, pl.smem, s);
+  if (epi == EPI_HJ_Y) return launch_sweep<T, T, T, false, EPI_HJ_Y>(a, TMA, pl.grid, pl.block, pl.smem, s);
+  return dispatch_lin<T, T, T>(epi, pl, s);
+}
+
+// apply_D in mixed precision reads the FP64 array directly; molt_step's
+// sweeps read the FP32 copy of the state.
+cudaError_t launch(const Problem& p, int epi, const Plan& pl, cudaStream_t s, bool from_state_copy) {
+  const bool weno = p.d.weights == MOLT_W_WENOZ;
+  if (is_f64_sweep(p.d)) return dispatch_same<double>(weno, epi, pl, s);
+  if (is_f32_state(p.d)) return dispatch_same<float>(weno, epi, pl, s);
+  if (!from_state_copy) {
+    if (epi != EPI_STORE) return cudaErrorNotSupported;
+    if (weno) return launch_sweep<float, double, double, true, EPI_STORE>(pl.a, TMA, pl.grid, pl.block, pl.smem, s);
+    return launch_sweep<float, double, double, false, EPI_STORE>(pl.a, TMA, pl.grid, pl.block, pl.smem, s);
+  }
+  if (weno) return cudaErrorNotSupported;
+  return dispatch_lin<float, float, double>(epi, pl, s);
+}
+
+molt_status run(molt_ctx* c, const Problem& p, int epi, Plan& pl, bool from_state_copy = true) {
+  // element size of the sweep input: FP64 except FP32 state or the FP32 copy
+  const size_t in_bytes = is_f32_state(p.d) || (is_mixed(p.d) && from_state_copy) ? 4 : 8;
+  if (!c->no_tma) plan_tma(p, pl.ax, pl.a.in, in_bytes, &pl);
+  molt_ctx::Rec rec{epi, nullptr, nullptr};
+  if (c->profile) {
+    cudaEventCreate(&rec.start);
+    cudaEventCreate(&rec.stop);
+    cudaEventRecord(rec.start, c->stream);
+  }
+  cudaError_t e = launch(p, epi, pl, c->stream, from_state_copy);
+  if (c->profile) {
+    cudaEventRecord(rec.stop, c->stream);
+    c->recs.push_back(rec);
+  }
+  if (e == cudaErrorNotSupported)
+    return fail(c, MOLT_EUNSUPPORTED, "no kernel for this precision/weights/epilogue combination");
+  if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
+  return MOLT_OK;
+}
+
+double step_alpha(const Problem& p) {
+  const molt_desc& d = p.d;
+  if (d.pde == MOLT_PDE_HEAT) return d.beta / std::sqrt(d.diffusivity * d.dt);
+  if (d.pde == MOLT_PDE_WAVE) return d.beta / (d.c * d.dt);
+  double hmin = p.h[0];
+  for (int ax = 1; ax < d.ndim; ++ax) hmin = std::min(hmin, p.h[ax]);
+  return d.beta / (d.cfl * hmin);
+}
+
+}  // namespace
+
+extern "C" {
+
+molt_status molt_create(const molt_desc* descs, int count, void* cuda_stream, molt_ctx** out) {
+  if (!descs || count < 1 || !out) return fail(nullptr, MOLT_EINVAL, "null descriptor/out or count < 1");
+  *out = nullptr;
+  molt_ctx* c = new molt_ctx();
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  for (int i = 0; i < count; ++i) {
+    const std::string v = validate(descs[i]);
+    if (!v.empty()) {
+      delete c;
+      return fail(nullptr, MOLT_EINVAL, "problem " + std::to_string(i) + ": " + v);
+    }
+    Problem p;
+    p.d = descs[i];
+    p.total = 1;
+    for (int ax = 0; ax < 3; ++ax) {
+      p.n[ax] = ax < p.d.ndim ? p.d.n[ax] : 1;
+      p.total *= p.n[ax];
+      if (ax < p.d.ndim) {
+        const int64_t N = p.d.bc[ax] == MOLT_BC_PERIODIC ? p.n[ax] : p.n[ax] - 1;
+        p.h[ax] = (p.d.hi[ax] - p.d.lo[ax]) / double(N);
+      } else {
+        p.h[ax] = 1.0;
+      }
+    }
+    if (p.d.pde == MOLT_PDE_HJ) {
+      for (int ax = 0; ax < p.d.ndim; ++ax)
+        if (p.d.bc[ax] != MOLT_BC_PERIODIC) {
+          delete c;
+          return fail(nullptr, MOLT_EUNSUPPORTED, "Hamilton-Jacobi needs periodic axes");
+        }
+      if (p.d.prec == MOLT_PREC_F32_F64UPDATE) {
+        delete c;
+        return fail(nullptr, MOLT_EUNSUPPORTED, "Hamilton-Jacobi runs in MOLT_PREC_F32 or MOLT_PREC_F64");
+      }
+      if (!(p.d.cfl > 0)) {
+        delete c;
+        return fail(nullptr, MOLT_EINVAL, "cfl must be positive");
+      }
+    }
+    if (p.d.weights == MOLT_W_LEARNED) {
+      delete c;
+      return fail(nullptr, MOLT_EUNSUPPORTED, "learned weights are not available in this build");
+    }
+    c->probs.push_back(p);
+  }
+  cudaError_t e;
+  if ((e = cudaMalloc(&c->status_dev, sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&c->speed_dev, sizeof(unsigned long long) * 2 * count)) != cudaSuccess ||
+      (e = cudaMalloc(&c->t_dev, sizeof(double) * count)) != cudaSuccess) {
+    molt_destroy(c);
+    return fail(nullptr, MOLT_ENOMEM, std::string("workspace: ") + cudaGetErrorString(e));
+  }
+  cudaMemset(c->status_dev, 0, sizeof(int));
+  cudaMemset(c->speed_dev, 0, sizeof(unsigned long long) * 2 * count);
+  for (auto& p : c->probs) {
+    const size_t cb = compute_bytes(p.d), sb = state_bytes(p.d);
+    const size_t tot = size_t(p.total);
+    bool ok = true;
+    if (p.d.ndim > 1 && p.d.pde != MOLT_PDE_HJ) ok = ok && cudaMalloc(&p.acc, cb * tot) == cudaSuccess;
+    if (p.d.pde == MOLT_PDE_HEAT) {
+      ok = ok && cudaMalloc(&p.stage1, sb * tot) == cudaSuccess;
+      ok = ok && cudaMalloc(&p.stage2, sb * tot) == cudaSuccess;
+    }
+    if (p.d.pde == MOLT_PDE_HJ && p.d.ndim > 1) ok = ok && cudaMalloc(&p.hx, sb * tot) == cudaSuccess;
+    if (is_mixed(p.d) && p.d.pde != MOLT_PDE_HJ) ok = ok && cudaMalloc(&p.shadow, 4 * tot) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      molt_destroy(c);
+      return fail(nullptr, MOLT_ENOMEM, "workspace allocation failed");
+    }
+  }
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+    molt_destroy(c);
+    return fail(nullptr, MOLT_ECUDA, std::string("create: ") + cudaGetErrorString(e));
+  }
+  *out = c;
+  return MOLT_OK;
+}
+
+molt_status molt_apply_D(molt_ctx* c, int problem, int axis, int op, int P, double alpha, const void* in,
+                         void* out) {
+  if (!c) return fail(nullptr, MOLT_EINVAL, "null context");
+  if (problem < 0 || problem >= int(c->probs.size())) return fail(c, MOLT_EINVAL, "problem index out of range");
+  const Problem& p = c->probs[problem];
+  if (axis < 0 || axis >= p.d.ndim) return fail(c, MOLT_EINVAL, "axis out of range");
+  if (op != MOLT_OP_L && op != MOLT_OP_R && op != MOLT_OP_0) return fail(c, MOLT_EINVAL, "unknown op");
+  if (P < 1 || P > 64) return fail(c, MOLT_EINVAL, "P must be in 1..64");
+  if (!in || !out) return fail(c, MOLT_EINVAL, "null array");
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15)
+    return fail(c, MOLT_EINVAL, "arrays must be 16-byte aligned");
+  const int mode = op == MOLT_OP_L ? MODE_L : (op == MOLT_OP_R ? MODE_R : MODE_0);
+  Plan pl;
+  molt_status st = plan_axis(c, p, axis, mode, P, alpha, &pl);
+  if (st != MOLT_OK) return st;
+  // in == out is safe: every CTA reads its whole lines before writing them
+  pl.a.in = in;
+  pl.a.out = out;
+  return run(c, p, EPI_STORE, pl, false);
+}
+
+}  // extern "C"
+
+namespace {
+
+// FP32 copy of an FP64 state (integer-pattern conversion, grid-stride).
+__global__ void shadow_kernel(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = d2f(in[i]);
+}
+
+molt_status refresh_shadow(molt_ctx* c, Problem& p, const void* u) {
+  if (!p.shadow) return MOLT_OK;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long n = p.total;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 8LL * sms) blocks = 8LL * sms;
+  shadow_kernel<<<int(blocks), 256, 0, c->stream>>>(static_cast<const double*>(u), p.shadow, n);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MOLT_OK : cuda_fail(c, e, "state copy");
+}
+
+// Sweep input of molt_step: the FP32 copy in mixed precision, else the state.
+const void* sweep_input(const Problem& p, const void* state) { return p.shadow ? p.shadow : state; }
+
+molt_status heat_step(molt_ctx* c, Problem& p, void* u) {
+  const double alpha = step_alpha(p);
+  const double coefS = -p.d.beta * p.d.beta;
+  static const double rk[3][2] = {{0.0, 1.0}, {0.75, 0.25}, {1.0 / 3.0, 2.0 / 3.0}};
+  void* ins[3] = {u, p.stage1, p.stage2};
+  void* dsts[3] = {p.stage1, p.stage2, u};
+  for (int s = 0; s < 3; ++s) {
+    for (int ax = 0; ax < p.d.ndim; ++ax) {
+      Plan pl;
+      molt_status st = plan_axis(c, p, ax, MODE_0, p.d.P, alpha, &pl);
+      if (st != MOLT_OK) return st;
+      pl.a.in = sweep_input(p, ins[s]);
+      pl.a.acc = p.acc;
+      int epi;
+      if (ax + 1 < p.d.ndim) {
+        epi = ax == 0 ? EPI_ACC_SET : EPI_ACC_ADD;
+      } else {
+        epi = EPI_HEAT_FINAL;
+        if (p.d.ndim == 1) pl.a.acc = nullptr;
+        pl.a.un = u;
+        pl.a.us = ins[s];
+        pl.a.dst = dsts[s];
+        pl.a.shadow = p.shadow;
+        pl.a.a0 = rk[s][0];
+        pl.a.a1 = rk[s][1];
+        pl.a.coefS = coefS;
+      }
+      if ((st = run(c, p, epi, pl)) != MOLT_OK) return st;
+    }
+  }
+  return MOLT_OK;
+}
+
+molt_status wave_step(molt_ctx* c, Problem& p, void* cur, void* prev, bool from_rest, bool in_place_variant) {
+  const double alpha = step_alpha(p);
+  for (int ax = 0; ax < p.d.ndim; ++ax) {
+    Plan pl;
+    molt_status st = plan_axis(c, p, ax, MODE_0, p.d.P, alpha, &pl);
+    if (st != MOLT_OK) return st;
+    pl.a.in = sweep_input(p, cur);
+    pl.a.acc = p.acc;
+    int epi;
+    if (ax + 1 < p.d.ndim) {
+      epi = ax == 0 ? EPI_ACC_SET : EPI_ACC_ADD;
+    } else {
+      epi = EPI_WAVE_FINAL;
+      if (p.d.ndim == 1) pl.a.acc = nullptr;
+      pl.a.un = cur;
+      pl.a.us = prev;
+      pl.a.coefS = -p.d.beta * p.d.beta;
+      pl.a.from_rest = from_rest ? 1 : 0;
+      pl.a.shadow = p.shadow;
+      if (in_place_variant) {
+        pl.a.dst = cur;
+        pl.a.dst2 = prev;
+      } else {
+        pl.a.dst = prev;
+      }
+    }
+    if ((st = run(c, p, epi, pl)) != MOLT_OK) return st;
+  }
+  return MOLT_OK;
+}
+
+molt_status hj_pass(molt_ctx* c, Problem& p, int idx, void* u, int ax, int epi, unsigned long long* speed,
+                    const unsigned long long* lag, void* hx) {
+  Plan pl;
+  molt_status st = plan_axis(c, p, ax, MODE_RL, 1, step_alpha(p), &pl);
+  if (st != MOLT_OK) return st;
+  double hmin = p.h[0];
+  for (int a = 1; a < p.d.ndim; ++a) hmin = std::min(hmin, p.h[a]);
+  pl.a.in = u;
+  pl.a.un = u;
+  pl.a.out = hx;
+  pl.a.dst = u;
+  pl.a.speed = speed;
+  pl.a.lag = lag;
+  pl.a.cfl_h = p.d.cfl * hmin;
+  pl.a.dt_max = 10.0 * hmin;
+  pl.a.t_dev = c->t_dev + idx;
+  return run(c, p, epi, pl);
+}
+
+molt_status hj_step(molt_ctx* c, Problem& p, int idx, void* u) {
+  unsigned long long* slots = c->speed_dev + 2 * idx;
+  cudaError_t e;
+  if (!p.hj_lag_ready) {
+    // speeds of u^0 serve as the lagged speeds of the first step (Algorithm 1)
+    if ((e = cudaMemsetAsync(slots + 1, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "memset");
+    for (int ax = 0; ax < p.d.ndim; ++ax) {
+      molt_status st = hj_pass(c, p, idx, u, ax, EPI_HJ_X, slots + 1, nullptr, nullptr);
+      if (st != MOLT_OK) return st;
+    }
+    p.hj_lag_ready = true;
+    p.hj_steps = 0;
+  }
+  const int cur = int(p.hj_steps & 1);
+  unsigned long long* slot = slots + cur;
+  const unsigned long long* lag = slots + (cur ^ 1);
+  if ((e = cudaMemsetAsync(slot, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "memset");
+  for (int ax = 0; ax < p.d.ndim; ++ax) {
+    const bool last = ax + 1 == p.d.ndim;
+    const int epi = last ? EPI_HJ_Y : EPI_HJ_X;
+    molt_status st = hj_pass(c, p, idx, u, ax, epi, slot, lag, p.d.ndim > 1 ? p.hx : nullptr);
+    if (st != MOLT_OK) return st;
+  }
+  p.hj_steps++;
+  return MOLT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+molt_status molt_step(molt_ctx* c, void* const* u, void* const* u_prev, int nsteps, double* t_inout) {
+  if (!c) return fail(nullptr, MOLT_EINVAL, "null context");
+  if (!u || !t_inout || nsteps < 0) return fail(c, MOLT_EINVAL, "null u/t_inout or negative nsteps");
+  const int np = int(c->probs.size());
+  for (int i = 0; i < np; ++i) {
+    if (!u[i]) return fail(c, MOLT_EINVAL, "null state pointer");
+    if (c->probs[i].d.pde == MOLT_PDE_WAVE && (!u_prev || !u_prev[i]))
+      return fail(c, MOLT_EINVAL, "wave problems need u_prev");
+    if (c->probs[i].d.pde != MOLT_PDE_HJ && !(c->probs[i].d.dt > 0))
+      return fail(c, MOLT_EINVAL, "heat and wave steps need dt > 0");
+  }
+  cudaError_t e;
+  std::vector<double> t0(np);
+  for (int i = 0; i < np; ++i) t0[i] = t_inout[i];
+  if ((e = cudaMemcpyAsync(c->t_dev, t0.data(), sizeof(double) * np, cudaMemcpyHostToDevice, c->stream)) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "t upload");
+  for (int i = 0; i < np && nsteps > 0; ++i) {
+    molt_status st = refresh_shadow(c, c->probs[i], u[i]);
+    if (st != MOLT_OK) return st;
+  }
+  for (int k = 0; k < nsteps; ++k) {
+    for (int i = 0; i < np; ++i) {
+      Problem& p = c->probs[i];
+      molt_status st = MOLT_OK;
+      if (p.d.pde == MOLT_PDE_HEAT) {
+        st = heat_step(c, p, u[i]);
+        t_inout[i] += p.d.dt;
+      } else if (p.d.pde == MOLT_PDE_WAVE) {
+        const bool from_rest = (k == 0 && t0[i] == 0.0);
+        const bool even = (k % 2) == 0;
+        void* cur = even ? u[i] : u_prev[i];
+        void* prev = even ? u_prev[i] : u[i];
+        const bool variant = (k == nsteps - 1) && even;   // keep u = newest on return
+        st = wave_step(c, p, cur, prev, from_rest, variant);
+        t_inout[i] += p.d.dt;
+      } else {
+        st = hj_step(c, p, i, u[i]);
+      }
+      if (st != MOLT_OK) return st;
+    }
+  }
+  int status = 0;
+  std::vector<double> tdev(np);
+  if ((e = cudaMemcpyAsync(&status, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "status read");
+  if ((e = cudaMemcpyAsync(tdev.data(), c->t_dev, sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream)) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "t read");
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "step");
+  for (int i = 0; i < np; ++i)
+    if (c->probs[i].d.pde == MOLT_PDE_HJ) t_inout[i] = tdev[i];
+  if (status & ST_NONFINITE) {
+    cudaMemsetAsync(c->status_dev, 0, sizeof(int), c->stream);
+    return fail(c, MOLT_ENONFINITE, "a non-finite value reached the state");
+  }
+  if (status & ST_TIMEOUT) {
+    cudaMemsetAsync(c->status_dev, 0, sizeof(int), c->stream);
+    return fail(c, MOLT_ETIMEOUT, "a device-side wait timed out");
+  }
+  return MOLT_OK;
+}
+
+molt_status molt_set_option(molt_ctx* c, int option, int64_t value) {
+  if (!c) return fail(nullptr, MOLT_EINVAL, "null context");
+  if (value != 0 && value != 1) return fail(c, MOLT_EINVAL, "option value must be 0 or 1");
+  if (option == MOLT_OPT_TMA) c->no_tma = value == 0;
+  else if (option == MOLT_OPT_PROFILE) c->profile = value == 1;
+  else return fail(c, MOLT_EINVAL, "unknown option");
+  return MOLT_OK;
+}
+
+static void clear_records(molt_ctx* c) {
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.start);
+    cudaEventDestroy(r.stop);
+  }
+  c->recs.clear();
+}
+
+molt_status molt_profile_read(molt_ctx* c, int kind, double* total_ms, int64_t* launches) {
+  if (!c) return fail(nullptr, MOLT_EINVAL, "null context");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
+  double tot = 0.0;
+  int64_t cnt = 0;
+  for (auto& r : c->recs) {
+    if (r.kind != kind) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.start, r.stop) == cudaSuccess) {
+      tot += ms;
+      ++cnt;
+    }
+  }
+  clear_records(c);
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = cnt;
+  return MOLT_OK;
+}
+
+molt_status molt_destroy(molt_ctx* c) {
+  if (!c) return MOLT_OK;
+  cudaStreamSynchronize(c->stream);
+  clear_records(c);
+  for (auto& p : c->probs) {
+    cudaFree(p.acc);
+    cudaFree(p.stage1);
+    cudaFree(p.stage2);
+    cudaFree(p.hx);
+    cudaFree(p.shadow);
+  }
+  cudaFree(c->status_dev);
+  cudaFree(c->speed_dev);
+  cudaFree(c->t_dev);
+  delete c;
+  return MOLT_OK;
+}
+
+const char* molt_last_error(const molt_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+}  // extern "C"

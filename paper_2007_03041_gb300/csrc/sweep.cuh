@@ -1,0 +1,671 @@
+// Line-sweep kernel: the O(N) fast summation of L^{-1} and the successive-
+// convolution partial sums S_P = sum_{p=1}^P D^p along one axis of a grid
+// (arXiv 2007.03041, Sec. 2.1-2.4), with a fused epilogue that consumes S_P
+// (store, accumulate, or the time-integrator update).
+//
+// Mapping.  A CTA owns W lines of one axis.  The lines are staged in shared
+// memory (converted to the compute type T) with ghost cells on both ends;
+// each line is processed by `nwl` warps and every lane owns kE consecutive
+// points of it in registers.  Per application of D:
+//   1. local integrals J_R(x_e) = sum_l c_l v_{e+l} and J_L(x_e) =
+//      sum_l c_l v_{e-l} (Sec. 2.4 / App. C, optionally WENO-Z weighted) from
+//      a register window of the lane's points plus 3 neighbours per side;
+//   2. the recurrences I_R(x_i) = q I_R(x_{i-1}) + J_R(x_i) and
+//      I_L(x_i) = q I_L(x_{i+1}) + J_L(x_i) (Sec. 2.4) as affine scans:
+//      a serial fold per lane, a shuffle scan across the warp, a shared-
+//      memory scan across the warps of a line (the exact block split of the
+//      convolution sums, Sec. 3, without any truncation);
+//   3. the boundary constants from the line totals in FP64 (Sec. 2.3:
+//      periodic A = I(b)/(1-mu), B = I(a)/(1-mu); Dirichlet: the 2x2 system
+//      with determinant 1-mu^2, Sec. 3.3), folded into the scans as their
+//      initial values so that A e^{-alpha(x-a)} needs no pow();
+//   4. a fix-up pass giving L^{-1} (in FP32 the recurrence is accumulated
+//      with a compensation term: exact product error by FMA, TwoSum for the
+//      addition), then D = v - L^{-1}.
+// D is written back to shared memory for the next power.  The epilogue runs
+// in the coalesced load mapping.
+//
+// Precision plumbing.  GB300 executes FP64 arithmetic and FP64<->FP32
+// conversions at a small fraction of the FP32 rate, so per-point FP64 work is
+// kept to the update itself: sweeps read an FP32 copy of the state (written
+// by the previous update), conversions are done with integer bit operations,
+// and only the state update uses FP64 fused multiply-adds.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace molt {
+
+constexpr int kE = 16;   // points per lane
+constexpr int kG = 16;   // ghost slots per side in shared memory (3 used)
+#ifndef MOLT_MAX_THREADS
+#define MOLT_MAX_THREADS 512
+#endif
+constexpr int kMaxThreads = MOLT_MAX_THREADS;
+
+enum Epi {
+  EPI_STORE = 0,       // out = S
+  EPI_ACC_SET = 1,     // acc = S
+  EPI_ACC_ADD = 2,     // acc += S
+  EPI_HEAT_FINAL = 3,  // dst = a0*un + a1*(us + coefS*(acc + S))
+  EPI_WAVE_FINAL = 4,  // dst = 2u - uprev + coefS*(acc+S)  (or from rest)
+  EPI_HJ_X = 5,        // hx = H^_x(D_R, D_L); speed max
+  EPI_HJ_Y = 6         // u -= dt*(hx + H^_y); speed max
+};
+enum Mode { MODE_L = 0, MODE_R = 1, MODE_0 = 2, MODE_RL = 3 };
+enum StatusBits { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
+
+struct LineGeom {
+  int n;              // stored points per line
+  long long nlines;   // lines in this pass
+  long long nlo;      // line l = hi*nlo + lo
+  long long s_lo, s_hi;
+  long long stride;   // element stride along the line
+};
+
+struct SweepArgs {
+  LineGeom g;
+  int W, nwl, LS;     // lines per CTA, warps per line, shared line stride (elements)
+  int bc;             // 0 periodic, 1 Dirichlet
+  int mode;           // Mode
+  int P;
+  int contiguous;     // stride == 1
+  double c[6];        // J_R weights on offsets -3..2
+  double sub[3][4];   // WENO substencil weights (5-point rule)
+  double d[3];        // linear weights
+  double q;           // e^{-nu}
+  double qE;          // e^{-nu kE}
+  double invq;        // e^{+nu}
+  double inv1mmu;     // 1/(1-mu)
+  double mu;          // e^{-alpha(b-a)}
+  double invdet;      // 1/(1-mu^2)
+  double alpha;
+  // epilogue operands
+  const void* in;     // sweep input (TIN)
+  void* out;          // EPI_STORE destination / HJ: H^_x buffer (state type)
+  void* acc;          // accumulator (compute type)
+  const void* un;     // heat: u^n; wave: u^n; HJ: u (state type)
+  const void* us;     // heat: stage state; wave: u^{n-1}
+  void* dst;          // final destination (state type)
+  void* dst2;         // wave: receives u^n (old state) when non-null
+  float* shadow;      // FP32 copy of dst written by final epilogues (or null)
+  double a0, a1, coefS;
+  int from_rest;      // wave Taylor start
+  // Hamilton-Jacobi
+  const unsigned long long* lag;  // lagged speed (double bits)
+  unsigned long long* speed;      // this pass's speed slot (double bits)
+  double cfl_h, dt_max;
+  double* t_dev;            // time accumulator (HJ_Y, block 0)
+  int* status;
+};
+
+__device__ __forceinline__ int phys(int e) {
+  const int ee = e + kG;
+  return ee + (ee >> 4);
+}
+
+__device__ __forceinline__ long long line_base(const LineGeom& g, long long l) {
+  const long long hi = l / g.nlo;
+  const long long lo = l - hi * g.nlo;
+  return hi * g.s_hi + lo * g.s_lo;
+}
+
+// ------------------------------------------------------------ conversions
+// double -> float, round to nearest even, by integer operations on the bit
+// pattern (normal results); zeros, subnormal results, overflow, inf and NaN
+// take the hardware conversion.
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned int hi = __double2hiint(x);
+  const unsigned int lo = __double2loint(x);
+  const unsigned int e11 = (hi >> 20) & 0x7FFu;
+  if (e11 < 897u || e11 > 1150u) return __double2float_rn(x);
+  const unsigned int mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const unsigned int rest = lo & 0x1FFFFFFFu;           // 29 dropped bits
+  const unsigned int half = 0x10000000u;
+  const unsigned int up = (rest > half) | ((rest == half) & (mant & 1u));
+  const unsigned int bits = (hi & 0x80000000u) | (((e11 - 896u) << 23) + mant + up);
+  return __uint_as_float(bits);
+}
+
+// float -> double (exact) by integer operations; zero/subnormal/inf/NaN take
+// the hardware conversion.
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned int u = __float_as_uint(x);
+  const unsigned int e8 = (u >> 23) & 0xFFu;
+  if (e8 == 0u || e8 == 255u) return double(x);
+  const unsigned int hi = (u & 0x80000000u) | ((e8 + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  const unsigned int lo = u << 29;
+  return __hiloint2double(int(hi), int(lo));
+}
+
+// Non-finite test on the exponent bits (no floating-point instruction).
+__device__ __forceinline__ bool nonfinite(double x) { return (__double2hiint(x) & 0x7FF00000) == 0x7FF00000; }
+__device__ __forceinline__ bool nonfinite(float x) { return (__float_as_uint(x) & 0x7F800000u) == 0x7F800000u; }
+
+template <typename TO, typename FROM>
+__device__ __forceinline__ TO cvt(FROM x) {
+  if constexpr (sizeof(TO) == 4 && sizeof(FROM) == 8) return d2f(x);
+  else if constexpr (sizeof(TO) == 8 && sizeof(FROM) == 4) return f2d(x);
+  else return TO(x);
+}
+
+// ---------------------------------------------------------------- arithmetic
+// y <- a*y + b on y = hi + lo.  FP32: compensated (exact product error by FMA,
+// TwoSum for the addition).  FP64: plain FMA.
+template <typename T>
+struct Acc {
+  T hi, lo;
+  __device__ __forceinline__ void step(T a, T b) {
+    if constexpr (sizeof(T) == 4) {
+      const T p = a * hi;
+      const T pe = fmaf(a, hi, -p);
+      const T s = p + b;
+      const T bb = s - p;
+      const T se = (p - (s - bb)) + (b - bb);
+      lo = fmaf(a, lo, pe + se);
+      hi = s;
+    } else {
+      hi = fma(a, hi, b);
+    }
+  }
+  __device__ __forceinline__ T value() const {
+    if constexpr (sizeof(T) == 4) return hi + lo; else return hi;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+template <typename T>
+__device__ __forceinline__ T shfl_down(T v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+
+// WENO-Z weighted local integral from the 5 values w[0..4] = v at offsets
+// -3..1 relative to the target node, in the orientation of J_R (J_L passes
+// the mirrored values).  Smoothness indicators: beta_r = int_{-1}^0
+// (p_r')^2 + (p_r'')^2 dt for the quadratic through substencil r, worked out
+// in closed form with s1 = (c-a)/2, s2 = a-2b+c:
+//   beta_0 = s1^2 + 3 s1 s2 + 10/3 s2^2,  beta_1 = s1^2 + s1 s2 + 4/3 s2^2,
+//   beta_2 = s1^2 - s1 s2 + 4/3 s2^2.
+// WENO-Z (Sec. 2.4): w~_r = d_r (1 + tau/(eps+beta_r)), tau = |beta_0-beta_2|.
+template <typename T>
+__device__ __forceinline__ T wenoz_integral(const T* w, const T (&sub)[3][3], const T (&d)[3]) {
+  T J[3], beta[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const T a = w[r], b = w[r + 1], c = w[r + 2];
+    J[r] = sub[r][0] * a + sub[r][1] * b + sub[r][2] * c;
+    const T s1 = T(0.5) * (c - a);
+    const T s2 = a - T(2) * b + c;
+    const T k = r == 0 ? T(3) : (r == 1 ? T(1) : T(-1));
+    const T m = r == 0 ? T(10.0 / 3.0) : T(4.0 / 3.0);
+    beta[r] = s1 * s1 + k * s1 * s2 + m * s2 * s2;
+  }
+  const T tau = fabs(beta[0] - beta[2]);
+  const T eps = T(1e-6);
+  T wt[3], sum = T(0);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    wt[r] = d[r] * (T(1) + tau / (eps + beta[r]));
+    sum += wt[r];
+  }
+  return (wt[0] * J[0] + wt[1] * J[1] + wt[2] * J[2]) / sum;
+}
+
+// -------------------------------------------------------------- tile staging
+// Contiguous lines: the nwl warps of line lw read it with consecutive lanes.
+// Strided lines: thread (p, w) with w fastest, so a warp reads whole rows of
+// W neighbouring lines.
+template <typename T, typename TIN>
+__device__ __forceinline__ void load_tile(const SweepArgs& a, const TIN* in, T* lines, long long line0,
+                                          int lw, int tl) {
+  const int W = a.W, n = a.g.n;
+  if (a.contiguous) {
+    const long long gl = line0 + lw;
+    if (gl >= a.g.nlines) return;
+    const TIN* src = in + line_base(a.g, gl);
+    T* dstl = lines + lw * a.LS;
+    const int step = a.nwl * 32;
+#pragma unroll 4
+    for (int p = tl; p < n; p += step) dstl[phys(p)] = cvt<T>(src[p]);
+  } else {
+    // prow = blockDim/W is a multiple of 16, so phys() advances by a constant
+    const int w = threadIdx.x % W;
+    const int prow = blockDim.x / W;
+    const long long gl = line0 + w;
+    if (gl >= a.g.nlines) return;
+    const long long st = a.g.stride;
+    int p = threadIdx.x / W;
+    const TIN* src = in + line_base(a.g, gl) + p * st;
+    const long long sstep = prow * st;
+    T* dst = lines + w * a.LS + phys(p);
+    const int dstep = prow + (prow >> 4);
+#pragma unroll 8
+    for (; p < n; p += prow) {
+      *dst = cvt<T>(*src);
+      src += sstep;
+      dst += dstep;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void fill_ghosts(const SweepArgs& a, T* lines) {
+  const int n = a.g.n;
+  for (int t = threadIdx.x; t < a.W * 6; t += blockDim.x) {
+    const int w = t / 6, g = t - w * 6;
+    T* b = lines + w * a.LS;
+    if (g < 3) {
+      const int j = g + 1;  // ghost e = -j
+      T val;
+      if (a.bc == 0) {
+        int s = (-j) % n;
+        if (s < 0) s += n;
+        val = b[phys(s)];
+      } else {
+        const int m = j < n - 1 ? j : n - 1;
+        val = T(2) * b[phys(0)] - b[phys(m)];
+      }
+      b[phys(-j)] = val;
+    } else {
+      const int j = g - 2;  // ghost e = n-1+j
+      T val;
+      if (a.bc == 0) {
+        val = b[phys((n - 1 + j) % n)];
+      } else {
+        const int m = n - 1 - j > 0 ? n - 1 - j : 0;
+        val = T(2) * b[phys(n - 1)] - b[phys(m)];
+      }
+      b[phys(n - 1 + j)] = val;
+    }
+  }
+}
+
+// ------------------------------------------------------------------- kernels
+// T: compute type; TIN: sweep input element type; TST: state type of the
+// epilogue operands.
+
+struct TileSmem {
+  double* carries;   // [W][4] compute-type (hi, lo) carry pairs (room for FP64)
+  void* totals;      // [W][nwl][4] of T
+  void* lines;       // [W][LS] of T
+};
+
+template <typename T>
+__device__ __forceinline__ TileSmem carve(unsigned char* smem, const SweepArgs& a, size_t* used) {
+  TileSmem t;
+  t.carries = reinterpret_cast<double*>(smem);
+  t.totals = reinterpret_cast<T*>(t.carries + 4 * a.W);
+  const size_t off = (size_t(4 * a.W) * sizeof(double) + size_t(a.W * a.nwl * 4) * sizeof(T) + 15) & ~size_t(15);
+  t.lines = smem + off;
+  *used = off + size_t(a.W) * a.LS * sizeof(T);
+  return t;
+}
+
+// Fills the ghosts of the staged lines, applies D P times (the whole method
+// step of the header comment) and leaves S_P (or, for MODE_RL, the per-axis
+// Lax-Friedrichs Hamiltonian) in the line buffers.  Returns the thread's
+// largest one-sided derivative magnitude (MODE_RL).  Ends synchronised.
+template <typename T, bool WENO, bool RAGGED>
+__device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSmem& sm, bool line_ok) {
+  const int nwl = a.nwl, n = a.g.n;
+  double* carries = sm.carries;
+  T* totals = static_cast<T*>(sm.totals);
+  T* lines = static_cast<T*>(sm.lines);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int lw = warp / nwl, part = warp - lw * nwl;
+  const int tl = part * 32 + lane;
+  T* buf = lines + lw * a.LS;
+  const int e0 = tl * kE;
+
+  const T q = T(a.q);
+  const T qE = T(a.qE);
+  T c[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) c[i] = T(a.c[i]);
+  T sub[3][3], dw[3];
+  if constexpr (WENO) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      dw[r] = T(a.d[r]);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) sub[r][j] = T(a.sub[r][j]);
+    }
+  }
+  fill_ghosts(a, lines);
+  __syncthreads();
+
+  // element maps: (q, J) for points with a local integral, identity for
+  // points past the end of the line and for the Dirichlet end nodes where the
+  // recurrences start (I_R(x_0) = 0, I_L(x_N) = 0).  RAGGED kernels mask per
+  // point.  Exact-fit kernels (n = nwl*32*kE) have no points past the end;
+  // their Dirichlet end nodes keep the map (q, 0) and the line's initial
+  // value is divided by q, which yields the same values (x_0: q*(C/q) + 0 = C).
+  const int eR0 = (a.bc == 1) ? 1 : 0;          // first R point with a J
+  const int eL1 = (a.bc == 1) ? n - 2 : n - 1;  // last L point with a J
+  const bool zeroR0 = !RAGGED && a.bc == 1 && e0 == 0;
+  const bool zeroLN = !RAGGED && a.bc == 1 && e0 + kE == n;
+
+  T v[kE], S[kE], JR[kE], JL[kE];
+#pragma unroll
+  for (int k = 0; k < kE; ++k) S[k] = T(0);
+  T rmax = T(0);
+
+  for (int p = 0; p < a.P; ++p) {
+    // ---- 1. local integrals from a window of kE + 6 points
+    {
+      T win[kE + 6];
+#pragma unroll
+      for (int k = 0; k < kE + 6; ++k) win[k] = buf[phys(e0 - 3 + k)];
+#pragma unroll
+      for (int k = 0; k < kE; ++k) {
+        v[k] = win[k + 3];
+        if constexpr (WENO) {
+          T wr[5], wl[5];
+#pragma unroll
+          for (int j = 0; j < 5; ++j) {
+            wr[j] = win[k + j];        // offsets -3..1
+            wl[j] = win[k + 6 - j];    // mirrored: v_{e+3} .. v_{e-1}
+          }
+          JR[k] = wenoz_integral<T>(wr, sub, dw);
+          JL[k] = wenoz_integral<T>(wl, sub, dw);
+        } else {
+          T r = T(0), l = T(0);
+#pragma unroll
+          for (int j = 0; j < 6; ++j) {
+            r = fma(c[j], win[k + j], r);       // v_{e + (j-3)}
+            l = fma(c[j], win[k + 6 - j], l);   // v_{e - (j-3)}
+          }
+          JR[k] = r;
+          JL[k] = l;
+        }
+      }
+    }
+    if (zeroR0) JR[0] = T(0);
+    if (zeroLN) JL[kE - 1] = T(0);
+    // ---- 2a. lane folds (R ascending, L descending, interleaved)
+    T aR, aL, bR, bL;
+    if constexpr (!RAGGED) {
+      T r = T(0), l = T(0);
+#pragma unroll
+      for (int k = 0; k < kE; ++k) {
+        r = fma(q, r, JR[k]);
+        l = fma(q, l, JL[kE - 1 - k]);
+      }
+      aR = qE;
+      aL = qE;
+      bR = r;
+      bL = l;
+    } else {
+      T r = T(0), l = T(0);
+      aR = T(1);
+      aL = T(1);
+#pragma unroll
+      for (int k = 0; k < kE; ++k) {
+        const int e = e0 + k;
+        if (e >= eR0 && e < n) { r = fma(q, r, JR[k]); aR *= q; }
+        const int eL = e0 + kE - 1 - k;
+        if (eL <= eL1) { l = fma(q, l, JL[kE - 1 - k]); aL *= q; }
+      }
+      bR = r;
+      bL = l;
+    }
+    // ---- 2b. warp scans (R ascending, L descending)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T ap = shfl_up(aR, o), bp = shfl_up(bR, o);
+      const T an = shfl_down(aL, o), bn = shfl_down(bL, o);
+      if (lane >= o) { bR = fma(aR, bp, bR); aR *= ap; }
+      if (lane + o < 32) { bL = fma(aL, bn, bL); aL *= an; }
+    }
+    T exaR = shfl_up(aR, 1), exbR = shfl_up(bR, 1);
+    T exaL = shfl_down(aL, 1), exbL = shfl_down(bL, 1);
+    if (lane == 0) { exaR = T(1); exbR = T(0); }
+    if (lane == 31) { exaL = T(1); exbL = T(0); }
+    T* tot = totals + (lw * nwl) * 4;
+    if (lane == 31) { tot[part * 4 + 0] = aR; tot[part * 4 + 1] = bR; }
+    if (lane == 0) { tot[part * 4 + 2] = aL; tot[part * 4 + 3] = bL; }
+    __syncthreads();
+    // ---- 2c. across the warps of the line
+    T paR = T(1), pbR = T(0), paL = T(1), pbL = T(0);
+    for (int j = 0; j < part; ++j) {
+      const T A = tot[j * 4 + 0], B = tot[j * 4 + 1];
+      pbR = fma(A, pbR, B);
+      paR *= A;
+    }
+    for (int j = nwl - 1; j > part; --j) {
+      const T A = tot[j * 4 + 2], B = tot[j * 4 + 3];
+      pbL = fma(A, pbL, B);
+      paL *= A;
+    }
+    // ---- 3. boundary constants in FP64, vectorised over the CTA's lines:
+    //         lane w of warp 0 solves line w (GB300's FP64 pipe is narrow, so
+    //         one warp instruction for all lines instead of one per line).
+    if (warp == 0 && lane < a.W) {
+      const T* tw = totals + (lane * nwl) * 4;
+      T tbR = T(0), tbL = T(0);
+      for (int j = 0; j < nwl; ++j) tbR = fma(tw[j * 4 + 0], tbR, tw[j * 4 + 1]);
+      for (int j = nwl - 1; j >= 0; --j) tbL = fma(tw[j * 4 + 2], tbL, tw[j * 4 + 3]);
+      const double IRb = cvt<double>(tbR);   // I_R(b): R recurrence total from 0
+      const double ILa = cvt<double>(tbL);   // I_L(a)
+      double CR = 0.0, CL = 0.0;
+      if (a.bc == 0) {
+        // periodic: the cyclic recurrence's value before the first element
+        CR = IRb * a.inv1mmu;
+        CL = ILa * a.inv1mmu;
+      } else {
+        const T* bw = lines + lane * a.LS;
+        const double v0 = cvt<double>(bw[phys(0)]), vN = cvt<double>(bw[phys(n - 1)]);
+        if (a.mode == MODE_0) {
+          const double r0 = fma(-0.5, ILa, v0), r1 = fma(-0.5, IRb, vN);
+          // (A, B) = (1 - mu^2)^{-1} [[1, -mu], [-mu, 1]] (r0, r1); the
+          // carries are 2A and 2B (initial values of the R and L scans)
+          CR = 2.0 * fma(-a.mu, r1, r0) * a.invdet;
+          CL = 2.0 * fma(-a.mu, r0, r1) * a.invdet;
+        } else {
+          CR = v0;   // L_R^{-1}(a) = v(a)
+          CL = vN;   // L_L^{-1}(b) = v(b)
+        }
+        if (!RAGGED) {
+          CR *= a.invq;
+          CL *= a.invq;
+        }
+      }
+      // split into compute-type (hi, lo) pairs
+      T* cw = reinterpret_cast<T*>(carries) + lane * 4;
+      const T rh = cvt<T>(CR), lh = cvt<T>(CL);
+      cw[0] = rh;
+      cw[1] = cvt<T>(CR - cvt<double>(rh));
+      cw[2] = lh;
+      cw[3] = cvt<T>(CL - cvt<double>(lh));
+    }
+    __syncthreads();
+    // ---- 4. carries into the lane and the fix-up passes
+    {
+      const T* cw = reinterpret_cast<const T*>(carries) + lw * 4;
+      const T cRh = cw[0], cRl = cw[1], cLh = cw[2], cLl = cw[3];
+      const T laR = exaR * paR, lbR = fma(exaR, pbR, exbR);
+      const T laL = exaL * paL, lbL = fma(exaL, pbL, exbL);
+      Acc<T> yR{fma(laR, cRh, lbR), laR * cRl};
+      Acc<T> yL{fma(laL, cLh, lbL), laL * cLl};
+      if constexpr (!RAGGED) {
+#pragma unroll
+        for (int k = 0; k < kE; ++k) {
+          yR.step(q, JR[k]);
+          JR[k] = yR.value();
+          yL.step(q, JL[kE - 1 - k]);
+          JL[kE - 1 - k] = yL.value();
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < kE; ++k) {
+          const int e = e0 + k;
+          if (e >= eR0 && e < n) yR.step(q, JR[k]);
+          JR[k] = yR.value();
+          const int kl = kE - 1 - k;
+          if (e0 + kl <= eL1) yL.step(q, JL[kl]);
+          JL[kl] = yL.value();
+        }
+      }
+    }
+    // ---- 5. D = v - L^{-1}, accumulate, write back for the next power
+    if (a.mode == MODE_RL) {
+      // one-sided derivatives v^- = alpha D_R, v^+ = -alpha D_L and the
+      // per-axis part of the Lax-Friedrichs Hamiltonian (Sec. 2.5)
+      const T al = T(a.alpha);
+#pragma unroll
+      for (int k = 0; k < kE; ++k) {
+        const T vm = al * (v[k] - JR[k]);
+        const T vp = -al * (v[k] - JL[k]);
+        const T r = fmax(fabs(vm), fabs(vp));
+        const T mean = T(0.5) * (vm + vp);
+        S[k] = T(0.5) * mean * mean + r * T(0.5) * (vm - vp);
+        if (line_ok && e0 + k < n) rmax = fmax(rmax, r);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kE; ++k) {
+        T linv;
+        if (a.mode == MODE_0) linv = T(0.5) * (JR[k] + JL[k]);
+        else if (a.mode == MODE_R) linv = JR[k];
+        else linv = JL[k];
+        v[k] = v[k] - linv;
+        S[k] += v[k];
+      }
+    }
+    if (p + 1 < a.P) {
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < kE; ++k)
+        if (e0 + k < n) buf[phys(e0 + k)] = v[k];
+      __syncthreads();
+      fill_ghosts(a, lines);
+      __syncthreads();
+    }
+  }
+
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kE; ++k)
+    if (e0 + k < n) buf[phys(e0 + k)] = S[k];
+  __syncthreads();
+  return cvt<double>(rmax);
+}
+
+template <typename T, typename TST, int EPI>
+struct Epilogue {
+  const SweepArgs& a;
+  double dt;
+  __device__ __forceinline__ void operator()(long long gidx, T s) const {
+    if constexpr (EPI == EPI_STORE) {
+      static_cast<TST*>(a.out)[gidx] = cvt<TST>(s);
+    } else if constexpr (EPI == EPI_ACC_SET) {
+      static_cast<T*>(a.acc)[gidx] = s;
+    } else if constexpr (EPI == EPI_ACC_ADD) {
+      static_cast<T*>(a.acc)[gidx] += s;
+    } else if constexpr (EPI == EPI_HEAT_FINAL) {
+      const T tot = (a.acc ? static_cast<const T*>(a.acc)[gidx] : T(0)) + s;
+      const TST un = static_cast<const TST*>(a.un)[gidx];
+      const TST us = static_cast<const TST*>(a.us)[gidx];
+      const TST r = fma(TST(a.a0), un, TST(a.a1) * fma(TST(a.coefS), cvt<TST>(tot), us));
+      static_cast<TST*>(a.dst)[gidx] = r;
+      if (a.shadow) a.shadow[gidx] = cvt<float>(r);
+      if (nonfinite(r)) atomicOr(a.status, ST_NONFINITE);
+    } else if constexpr (EPI == EPI_WAVE_FINAL) {
+      const T tot = (a.acc ? static_cast<const T*>(a.acc)[gidx] : T(0)) + s;
+      const TST u = static_cast<const TST*>(a.un)[gidx];
+      TST r;
+      if (a.from_rest) r = fma(TST(0.5 * a.coefS), cvt<TST>(tot), u);
+      else r = fma(TST(a.coefS), cvt<TST>(tot), fma(TST(2), u, -static_cast<const TST*>(a.us)[gidx]));
+      if (a.dst2) static_cast<TST*>(a.dst2)[gidx] = u;
+      static_cast<TST*>(a.dst)[gidx] = r;
+      if (a.shadow) a.shadow[gidx] = cvt<float>(r);
+      if (nonfinite(r)) atomicOr(a.status, ST_NONFINITE);
+    } else if constexpr (EPI == EPI_HJ_X) {
+      if (a.out) static_cast<TST*>(a.out)[gidx] = TST(s);
+    } else if constexpr (EPI == EPI_HJ_Y) {
+      const TST u = static_cast<const TST*>(a.un)[gidx];
+      const TST hx = a.out ? static_cast<const TST*>(a.out)[gidx] : TST(0);
+      const TST r = u - TST(dt) * (hx + TST(s));
+      static_cast<TST*>(a.dst)[gidx] = r;
+      if (nonfinite(r)) atomicOr(a.status, ST_NONFINITE);
+    }
+  }
+
+};
+
+// Applies the epilogue to the tile's W lines in the coalesced mapping.
+template <typename T, typename TST, int EPI>
+__device__ __forceinline__ void epilogue_tile(const SweepArgs& a, const T* lines, long long line0, double dt) {
+  const Epilogue<T, TST, EPI> apply{a, dt};
+  const int W = a.W, n = a.g.n, nwl = a.nwl;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (a.contiguous) {
+    const int lw = warp / nwl, tl = (warp - lw * nwl) * 32 + lane;
+    if (line0 + lw < a.g.nlines) {
+      const long long base = line_base(a.g, line0 + lw);
+      const T* buf = lines + lw * a.LS;
+      const int step = nwl * 32;
+      for (int p = tl; p < n; p += step) apply(base + p, buf[phys(p)]);
+    }
+  } else {
+    const int w = tid % W;
+    const int prow = blockDim.x / W;
+    const long long gl = line0 + w;
+    if (gl < a.g.nlines) {
+      const long long st = a.g.stride;
+      int p = tid / W;
+      long long g = line_base(a.g, gl) + p * st;
+      const long long gstep = prow * st;
+      const T* src = lines + w * a.LS + phys(p);
+      const int sstep = prow + (prow >> 4);
+#pragma unroll 4
+      for (; p < n; p += prow) {
+        apply(g, *src);
+        g += gstep;
+        src += sstep;
+      }
+    }
+  }
+}
+
+template <int EPI>
+__device__ __forceinline__ double hj_dt(const SweepArgs& a) {
+  double dt = 0.0;
+  if constexpr (EPI == EPI_HJ_Y) {
+    const double cl = __longlong_as_double((long long)a.lag[0]);
+    dt = a.dt_max;
+    if (cl > 0.0 && a.cfl_h / cl < dt) dt = a.cfl_h / cl;
+  }
+  return dt;
+}
+
+template <int EPI>
+__device__ __forceinline__ void publish_speed(const SweepArgs& a, double rmax) {
+  if constexpr (EPI == EPI_HJ_X || EPI == EPI_HJ_Y) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    if ((threadIdx.x & 31) == 0 && rmax > 0.0 && a.speed)
+      atomicMax(a.speed, (unsigned long long)__double_as_longlong(rmax));
+  }
+}
+
+// One tile per CTA, plain coalesced loads (any size / alignment).
+template <typename T, typename TIN, typename TST, bool WENO, int EPI, bool RAGGED>
+__global__ void __launch_bounds__(kMaxThreads, 1) sweep_kernel(const SweepArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  size_t used;
+  const TileSmem sm = carve<T>(smem_raw, a, &used);
+  T* lines = static_cast<T*>(sm.lines);
+  const long long line0 = (long long)blockIdx.x * a.W;
+  const int warp = threadIdx.x >> 5, lw = warp / a.nwl;
+  const int tl = (warp - lw * a.nwl) * 32 + (threadIdx.x & 31);
+  load_tile<T, TIN>(a, static_cast<const TIN*>(a.in), lines, line0, lw, tl);
+  __syncthreads();
+  const double rmax = compute_lines<T, WENO, RAGGED>(a, sm, line0 + lw < a.g.nlines);
+  publish_speed<EPI>(a, rmax);
+  const double dt = hj_dt<EPI>(a);
+  if (EPI == EPI_HJ_Y && blockIdx.x == 0 && threadIdx.x == 0 && a.t_dev) *a.t_dev += dt;
+  epilogue_tile<T, TST, EPI>(a, lines, line0, dt);
+}
+
+}  // namespace molt

@@ -1,0 +1,71 @@
+// Launch entry points of the sweep kernel instantiations (one translation
+// unit per precision family, compiled in parallel).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "sweep.cuh"
+#include "sweep_tma.cuh"
+
+namespace molt {
+
+// TMA-fed persistent launch: staging geometry, tensor map, shared bytes.
+struct TmaPlan {
+  TmaGeom tg;
+  CUtensorMap map;
+  size_t smem;
+};
+
+// tma == nullptr: one tile per CTA with plain loads (grid/block/smem given);
+// otherwise the persistent TMA kernel on at most `grid` CTAs.
+template <typename T, typename TIN, typename TST, bool WENO, int EPI>
+cudaError_t launch_sweep(const SweepArgs& a, const TmaPlan* tma, int grid, int block, size_t smem,
+                         cudaStream_t s);
+
+// Exact-fit lines (n a multiple of 32*kE*nwl) run the unmasked kernels.
+inline bool exact_fit(const SweepArgs& a) { return a.g.n == a.nwl * 32 * kE; }
+
+#define MOLT_DEFINE_LAUNCH                                                                       \
+  template <typename T, typename TIN, typename TST, bool WENO, int EPI>                          \
+  cudaError_t launch_sweep(const SweepArgs& a, const TmaPlan* tma, int grid, int block,          \
+                           size_t smem, cudaStream_t s) {                                        \
+    if (tma) {                                                                                   \
+      auto k = &sweep_tma_kernel<T, TIN, TST, WENO, EPI>;                                        \
+      static bool configured = false;                                                            \
+      if (!configured) {                                                                         \
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                             210 * 1024);                                        \
+        if (e != cudaSuccess) return e;                                                          \
+        configured = true;                                                                       \
+      }                                                                                          \
+      int per_sm = 0, dev = 0, sms = 0;                                                          \
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, tma->smem); \
+      if (e != cudaSuccess) return e;                                                            \
+      cudaGetDevice(&dev);                                                                       \
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);                         \
+      long long ntiles = (a.g.nlines + a.W - 1) / a.W;                                           \
+      long long g = (long long)sms * (per_sm > 0 ? per_sm : 1);                                  \
+      if (g > ntiles) g = ntiles;                                                                \
+      k<<<int(g), block, tma->smem, s>>>(a, tma->tg, tma->map);                                  \
+      return cudaGetLastError();                                                                 \
+    }                                                                                            \
+    const bool fit = exact_fit(a);                                                               \
+    auto k = fit ? &sweep_kernel<T, TIN, TST, WENO, EPI, false>                                  \
+                 : &sweep_kernel<T, TIN, TST, WENO, EPI, true>;                                  \
+    static bool configured[2] = {false, false};                                                  \
+    if (!configured[fit]) {                                                                      \
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                           200 * 1024);                                          \
+      if (e != cudaSuccess) return e;                                                            \
+      configured[fit] = true;                                                                    \
+    }                                                                                            \
+    k<<<grid, block, smem, s>>>(a);                                                              \
+    return cudaGetLastError();                                                                   \
+  }
+
+#define MOLT_INST(T, TIN, TST, WENO, EPI)                                                        \
+  template cudaError_t launch_sweep<T, TIN, TST, WENO, EPI>(const SweepArgs&, const TmaPlan*, int, \
+                                                            int, size_t, cudaStream_t);
+
+}  // namespace molt

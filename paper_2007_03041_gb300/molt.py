@@ -1,0 +1,166 @@
+"""Thin ctypes binding of the C ABI in include/molt.h (argument marshalling only).
+
+Every computation runs in the CUDA kernels of ``libmolt.so``; there is no
+fallback: if the library is missing or no GPU is present, the calls raise.
+Arrays are torch CUDA tensors (dense, C-ordered [z][y][x]); ``axis`` follows
+the C ABI (0 = x, the contiguous axis).
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmolt.so")
+
+MOLT_OK, MOLT_EINVAL, MOLT_ENOMEM, MOLT_ECUDA, MOLT_ETIMEOUT, MOLT_ENONFINITE, MOLT_EUNSUPPORTED = range(7)
+BC_PERIODIC, BC_DIRICHLET = 0, 1
+OP_L, OP_R, OP_0 = 0, 1, 2
+PREC_F64, PREC_F32_F64UPDATE, PREC_F32 = 0, 1, 2
+PDE_HEAT, PDE_WAVE, PDE_HJ = 0, 1, 2
+W_LINEAR, W_WENOZ, W_LEARNED = 0, 1, 2
+
+EXPORTS = ("molt_create", "molt_apply_D", "molt_step", "molt_set_option", "molt_profile_read", "molt_destroy",
+           "molt_last_error")
+OPT_TMA, OPT_PROFILE = 0, 1
+KERNEL_STORE, KERNEL_ACC_SET, KERNEL_ACC_ADD, KERNEL_HEAT_FINAL, KERNEL_WAVE_FINAL, KERNEL_HJ_X, KERNEL_HJ_Y = range(7)
+
+
+class molt_desc(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int),
+        ("n", ctypes.c_int64 * 3),
+        ("lo", ctypes.c_double * 3),
+        ("hi", ctypes.c_double * 3),
+        ("bc", ctypes.c_int * 3),
+        ("P", ctypes.c_int),
+        ("quad_points", ctypes.c_int),
+        ("weights", ctypes.c_int),
+        ("beta", ctypes.c_double),
+        ("pde", ctypes.c_int),
+        ("c", ctypes.c_double),
+        ("diffusivity", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("prec", ctypes.c_int),
+    ]
+
+
+class MoltError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("molt status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libmolt.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libmolt.so not built: run __graft_entry__.build() (needs nvcc)")
+        lib = ctypes.CDLL(path)
+        lib.molt_create.argtypes = [ctypes.POINTER(molt_desc), ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.POINTER(ctypes.c_void_p)]
+        lib.molt_apply_D.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+        lib.molt_step.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                  ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        lib.molt_set_option.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]
+        lib.molt_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int64)]
+        lib.molt_destroy.argtypes = [ctypes.c_void_p]
+        lib.molt_last_error.argtypes = [ctypes.c_void_p]
+        lib.molt_last_error.restype = ctypes.c_char_p
+        for f in ("molt_create", "molt_apply_D", "molt_step", "molt_set_option", "molt_profile_read", "molt_destroy"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def make_desc(shape_xyz, lo=None, hi=None, bc=None, P=1, quad_points=6, weights=W_LINEAR, beta=1.0,
+              pde=PDE_HEAT, c=1.0, diffusivity=1.0, cfl=1.0, dt=0.0, prec=PREC_F64):
+    """Descriptor for a grid whose sizes are given x first (n_x, n_y, n_z)."""
+    nd = len(shape_xyz)
+    d = molt_desc()
+    d.ndim = nd
+    for i in range(3):
+        d.n[i] = int(shape_xyz[i]) if i < nd else 1
+        d.lo[i] = (lo[i] if lo is not None and i < nd else 0.0)
+        d.hi[i] = (hi[i] if hi is not None and i < nd else 1.0)
+        d.bc[i] = (bc[i] if bc is not None and i < nd else BC_PERIODIC)
+    d.P, d.quad_points, d.weights, d.beta = P, quad_points, weights, beta
+    d.pde, d.c, d.diffusivity, d.cfl, d.dt, d.prec = pde, c, diffusivity, cfl, dt, prec
+    return d
+
+
+def _check(lib, ctx, st):
+    if st != MOLT_OK:
+        msg = lib.molt_last_error(ctx)
+        raise MoltError(st, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    if not t.is_cuda:
+        raise ValueError("molt arrays must be CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("molt arrays must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def molt_create(descs, stream=None):
+    """Create a context; ``stream`` is a torch.cuda.Stream (default: current)."""
+    import torch
+    lib = load_library()
+    if isinstance(descs, molt_desc):
+        descs = [descs]
+    arr = (molt_desc * len(descs))(*descs)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    ctx = ctypes.c_void_p()
+    st = lib.molt_create(arr, len(descs), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(ctx))
+    _check(lib, None, st)
+    return ctx
+
+
+def molt_apply_D(ctx, problem, axis, op, P, alpha, inp, out):
+    lib = load_library()
+    _check(lib, ctx, lib.molt_apply_D(ctx, problem, axis, op, P, float(alpha), _ptr(inp), _ptr(out)))
+
+
+def molt_step(ctx, u, u_prev=None, nsteps=1, t=None):
+    """Advance all problems; ``u``/``u_prev`` are lists of tensors (or one
+    tensor); returns the list of times."""
+    lib = load_library()
+    if not isinstance(u, (list, tuple)):
+        u = [u]
+        if u_prev is not None:
+            u_prev = [u_prev]
+    n = len(u)
+    up = (ctypes.c_void_p * n)(*[_ptr(x) for x in u])
+    pp = None
+    if u_prev is not None:
+        pp = (ctypes.c_void_p * n)(*[(_ptr(x) if x is not None else None) for x in u_prev])
+    tt = (ctypes.c_double * n)(*([0.0] * n if t is None else list(t)))
+    _check(lib, ctx, lib.molt_step(ctx, up, pp, int(nsteps), tt))
+    return list(tt)
+
+
+def molt_set_option(ctx, option, value):
+    lib = load_library()
+    _check(lib, ctx, lib.molt_set_option(ctx, int(option), int(value)))
+
+
+def molt_profile_read(ctx, kind):
+    """(total device ms, launches) of the recorded sweeps of ``kind``; clears
+    the records."""
+    lib = load_library()
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(lib, ctx, lib.molt_profile_read(ctx, int(kind), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def molt_destroy(ctx):
+    lib = load_library()
+    _check(lib, ctx, lib.molt_destroy(ctx))

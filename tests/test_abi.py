@@ -1,0 +1,41 @@
+"""The C-ABI library loads and exports every function include/molt.h declares
+(no GPU needed: nothing here calls into CUDA)."""
+import ctypes
+import os
+import re
+
+from tests.conftest import ROOT
+
+
+def declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            src = open(os.path.join(inc, f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(molt_\w+)\s*\(", src, flags=re.M)
+    return names
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for f in ("molt_create", "molt_apply_D", "molt_step", "molt_destroy", "molt_last_error"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2007_03041_gb300 import molt as M
+    if not os.path.exists(M.LIB_PATH):
+        from paper_2007_03041_gb300 import build
+        build.build()
+    lib = ctypes.CDLL(M.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_the_header():
+    from paper_2007_03041_gb300 import molt as M
+    for name in declared_functions():
+        if name != "molt_last_error":
+            assert callable(getattr(M, name)), name

@@ -1,0 +1,136 @@
+"""GPU parity of molt_step (the fused multi-axis passes and the time-integrator
+epilogues) against the oracle's schemes, for every problem family."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import schemes
+from paper_2007_03041_gb300 import molt as M
+from paper_2007_03041_gb300 import workloads
+from tests.gpu_util import need_gpu, rel_l2, to_dev, tol_for, state_dtype
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", [M.PREC_F64, M.PREC_F32_F64UPDATE])
+@pytest.mark.parametrize("n", [64, 100])
+def test_heat_rk3_2d(prec, n):
+    need_gpu()
+    import torch
+    h = 1.0 / n
+    dt = h / 2
+    u0 = workloads.heat_modes(n)
+    d = M.make_desc((n, n), P=3, quad_points=3, beta=0.6, pde=M.PDE_HEAT, diffusivity=1.0, dt=dt, prec=prec)
+    ctx = M.molt_create(d)
+    try:
+        u = to_dev(u0, torch.float64)
+        t = M.molt_step(ctx, u, None, nsteps=3, t=[0.0])
+        got = u.cpu().numpy()
+    finally:
+        M.molt_destroy(ctx)
+    want = u0
+    for _ in range(3):
+        want = schemes.heat_step(want, [h, h], dt, 1.0, 0.6, None, 3, 3)
+    assert rel_l2(got, want) < tol_for(prec)
+    assert abs(t[0] - 3 * dt) < 1e-15
+
+
+@pytest.mark.parametrize("nsteps", [1, 2, 3])
+def test_wave_leapfrog_3d_dirichlet(nsteps):
+    need_gpu()
+    import torch
+    n = 33
+    h = 1.0 / (n - 1)
+    dt = 2 * h
+    u0 = workloads.wave_bumps(n)
+    d = M.make_desc((n, n, n), bc=[M.BC_DIRICHLET] * 3, P=2, quad_points=6, beta=0.8, pde=M.PDE_WAVE,
+                    c=1.0, dt=dt, prec=M.PREC_F32_F64UPDATE)
+    ctx = M.molt_create(d)
+    try:
+        u = to_dev(u0, torch.float64)
+        up = torch.full_like(u, float("nan"))   # ignored when starting from rest
+        M.molt_step(ctx, u, up, nsteps=nsteps, t=[0.0])
+        got, gotp = u.cpu().numpy(), up.cpu().numpy()
+    finally:
+        M.molt_destroy(ctx)
+    bc = ["dirichlet"] * 3
+    prev, cur = None, u0
+    for k in range(nsteps):
+        nxt = schemes.wave_step(cur, prev, [h] * 3, dt, 1.0, 0.8, bc, 6, 2, from_rest=(k == 0))
+        prev, cur = cur, nxt
+    assert rel_l2(got, cur) < 1e-5
+    assert rel_l2(gotp, prev) < 1e-5
+
+
+def test_wave_continues_across_calls_and_fp64():
+    need_gpu()
+    import torch
+    n = 21
+    h = 1.0 / (n - 1)
+    dt = 2 * h
+    u0 = workloads.wave_bumps(n)
+    for prec, tol in ((M.PREC_F64, 1e-12), (M.PREC_F32_F64UPDATE, 1e-5)):
+        d = M.make_desc((n, n, n), bc=[M.BC_DIRICHLET] * 3, P=2, quad_points=6, beta=0.8, pde=M.PDE_WAVE,
+                        c=1.0, dt=dt, prec=prec)
+        ctx = M.molt_create(d)
+        try:
+            u = to_dev(u0, torch.float64)
+            up = torch.zeros_like(u)
+            t = M.molt_step(ctx, u, up, nsteps=1, t=[0.0])
+            t = M.molt_step(ctx, u, up, nsteps=2, t=t)
+            got = u.cpu().numpy()
+        finally:
+            M.molt_destroy(ctx)
+        prev, cur = None, u0
+        for k in range(3):
+            nxt = schemes.wave_step(cur, prev, [h] * 3, dt, 1.0, 0.8, ["dirichlet"] * 3, 6, 2, from_rest=(k == 0))
+            prev, cur = cur, nxt
+        assert rel_l2(got, cur) < tol
+        assert abs(t[0] - 3 * dt) < 1e-14
+
+
+@pytest.mark.parametrize("prec,weights", [(M.PREC_F32, M.W_WENOZ), (M.PREC_F64, M.W_WENOZ),
+                                          (M.PREC_F32, M.W_LINEAR)])
+def test_hj_lagged_adaptive_2d(prec, weights):
+    need_gpu()
+    import torch
+    n = 128
+    h = 2 * np.pi / n
+    u0 = workloads.hj_initial(n)
+    d = M.make_desc((n, n), lo=[0, 0], hi=[2 * np.pi] * 2, P=1, quad_points=5, weights=weights, beta=1.0,
+                    pde=M.PDE_HJ, cfl=1.5, dt=0.0, prec=prec)
+    ctx = M.molt_create(d)
+    try:
+        u = to_dev(u0, state_dtype(prec))
+        t = M.molt_step(ctx, u, None, nsteps=2, t=[0.0])
+        t = M.molt_step(ctx, u, None, nsteps=2, t=t)
+        got = u.double().cpu().numpy()
+    finally:
+        M.molt_destroy(ctx)
+    wname = "wenoz" if weights == M.W_WENOZ else "linear"
+    uu = u0.astype(np.float32).astype(np.float64) if prec == M.PREC_F32 else u0
+    speeds = schemes.hj_initial_speeds(uu, [h, h], 1.5, 1.0, 5, wname)
+    tt = 0.0
+    for _ in range(4):
+        uu, dt, speeds = schemes.hj_step(uu, [h, h], speeds, 1.5, 1.0, 5, wname)
+        tt += dt
+    assert rel_l2(got, uu) < tol_for(prec)
+    assert abs(t[0] - tt) < (1e-12 if prec == M.PREC_F64 else 1e-4) * tt
+
+
+def test_nonfinite_state_is_reported():
+    need_gpu()
+    import torch
+    n = 32
+    u0 = workloads.heat_modes(n)
+    u0[3, 4] = np.inf
+    d = M.make_desc((n, n), P=1, quad_points=3, beta=0.6, pde=M.PDE_HEAT, dt=0.5 / n, prec=M.PREC_F64)
+    ctx = M.molt_create(d)
+    try:
+        u = to_dev(u0, torch.float64)
+        with pytest.raises(M.MoltError) as ei:
+            M.molt_step(ctx, u, None, nsteps=1, t=[0.0])
+        assert ei.value.status == M.MOLT_ENONFINITE
+    finally:
+        M.molt_destroy(ctx)
