@@ -146,6 +146,34 @@ typedef enum {
  * every recorded launch.  Either output pointer may be NULL. */
 molt_status molt_profile_read(molt_ctx* ctx, int kind, double* total_ms, int64_t* launches);
 
+/* One wave time step that allocates no device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code under a fixed device-memory budget, code inside a
+ * framework whose caching allocator owns all of the device's memory, and
+ * latency-critical code that cannot afford a first-use allocation.
+ *   desc      one problem with pde = MOLT_PDE_WAVE, prec =
+ *             MOLT_PREC_F32_F64UPDATE, linear weights, every used axis
+ *             2..8192 points, at most 1,048,576 grid points in total;
+ *             larger grids return MOLT_EINVAL, other PDEs/precisions
+ *             MOLT_EUNSUPPORTED.
+ *   u, u_prev u^n and u^{n-1}: device arrays of doubles (u_prev unused and
+ *             may be NULL when from_rest != 0).
+ *   u_next    receives u^{n+1} = 2u^n - u^{n-1} - beta^2 sum_d S_{P,d}[u^n]
+ *             (from_rest: u^n - beta^2/2 sum_d S_{P,d}[u^n]); must not alias
+ *             u or u_prev.  All three 16-byte aligned.
+ *   cuda_stream  cudaStream_t the work is enqueued on.
+ * Scratch (the FP32 copy of u^n, the FP32 axis accumulator and a status
+ * word, 8 MiB + 256 bytes) is a file-scope device array that every GPU
+ * loading the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.
+ * Every call on a device shares the array and clears the status word, so
+ * calls that overlap on the GPU (other streams, other host threads) race.
+ * Synchronous: returns after the step finished (MOLT_ENONFINITE if a
+ * non-finite value reached u_next).  Allocates nothing, host or device. */
+molt_status molt_wave_step_noalloc(const molt_desc* desc, const double* u, const double* u_prev, double* u_next,
+                                   int from_rest, void* cuda_stream);
+
 /* Release everything the context owns.  Synchronises its stream first. */
 molt_status molt_destroy(molt_ctx* ctx);
 

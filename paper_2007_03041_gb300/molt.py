@@ -19,7 +19,7 @@ PDE_HEAT, PDE_WAVE, PDE_HJ = 0, 1, 2
 W_LINEAR, W_WENOZ, W_LEARNED = 0, 1, 2
 
 EXPORTS = ("molt_create", "molt_apply_D", "molt_step", "molt_set_option", "molt_profile_read", "molt_destroy",
-           "molt_last_error")
+           "molt_last_error", "molt_wave_step_noalloc")
 OPT_TMA, OPT_PROFILE = 0, 1
 KERNEL_STORE, KERNEL_ACC_SET, KERNEL_ACC_ADD, KERNEL_HEAT_FINAL, KERNEL_WAVE_FINAL, KERNEL_HJ_X, KERNEL_HJ_Y = range(7)
 
@@ -70,6 +70,9 @@ def load_library(path=LIB_PATH):
         lib.molt_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64)]
         lib.molt_destroy.argtypes = [ctypes.c_void_p]
+        lib.molt_wave_step_noalloc.argtypes = [ctypes.POINTER(molt_desc), ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+        lib.molt_wave_step_noalloc.restype = ctypes.c_int
         lib.molt_last_error.argtypes = [ctypes.c_void_p]
         lib.molt_last_error.restype = ctypes.c_char_p
         for f in ("molt_create", "molt_apply_D", "molt_step", "molt_set_option", "molt_profile_read", "molt_destroy"):
@@ -159,6 +162,20 @@ def molt_profile_read(ctx, kind):
     n = ctypes.c_int64()
     _check(lib, ctx, lib.molt_profile_read(ctx, int(kind), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def molt_wave_step_noalloc(desc, u, u_prev, u_next, from_rest, stream=None):
+    """One wave step with no device allocation (scratch in a static device
+    array of the library); raises MoltError on a non-zero status."""
+    import torch
+    lib = load_library()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    prev = _ptr(u_prev) if u_prev is not None else None
+    st = lib.molt_wave_step_noalloc(ctypes.byref(desc), _ptr(u), prev, _ptr(u_next), int(from_rest),
+                                    ctypes.c_void_p(stream.cuda_stream))
+    if st != MOLT_OK:
+        raise MoltError(st, "molt_wave_step_noalloc")
 
 
 def molt_destroy(ctx):
