@@ -178,6 +178,15 @@ molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, do
   a.q = qt.q;
   a.qE = std::exp(-nu * double(kE));
   a.invq = std::exp(nu);
+  for (int i = 0; i < 6; ++i) a.cf[i] = float(a.c[i]);
+  for (int r = 0; r < 3; ++r) {
+    for (int j = 0; j < 3; ++j) a.subf[r][j] = float(a.sub[r][j]);
+    a.df[r] = float(a.d[r]);
+  }
+  a.qf = float(a.q);
+  a.qEf = float(a.qE);
+  a.alphaf = float(a.alpha);
+  if (a.g.nlines >= (1LL << 31)) return fail(c, MOLT_EUNSUPPORTED, "more than 2^31 lines along an axis");
   const int N = a.bc == MOLT_BC_PERIODIC ? n : n - 1;  // intervals
   a.mu = std::exp(-nu * double(N));
   a.inv1mmu = 1.0 / (-std::expm1(-nu * double(N)));

@@ -78,6 +78,14 @@ bool plan(const molt_desc& d, int ax, double alpha, int* status, SweepArgs* a, i
   a->q = qt.q;
   a->qE = std::exp(-nu * double(kE));
   a->invq = std::exp(nu);
+  for (int i = 0; i < 6; ++i) a->cf[i] = float(a->c[i]);
+  for (int r = 0; r < 3; ++r) {
+    for (int j = 0; j < 3; ++j) a->subf[r][j] = float(a->sub[r][j]);
+    a->df[r] = float(a->d[r]);
+  }
+  a->qf = float(a->q);
+  a->qEf = float(a->qE);
+  a->alphaf = float(a->alpha);
   a->mu = std::exp(-nu * double(N));
   a->inv1mmu = 1.0 / (-std::expm1(-nu * double(N)));
   a->invdet = 1.0 / (-std::expm1(-2.0 * nu * double(N)));

@@ -81,6 +81,9 @@ struct SweepArgs {
   double mu;          // e^{-alpha(b-a)}
   double invdet;      // 1/(1-mu^2)
   double alpha;
+  // the same coefficients rounded to FP32 on the host (FP32 kernels read
+  // these; converting on the device would use the FP64 pipe)
+  float cf[6], subf[3][3], df[3], qf, qEf, alphaf;
   // epilogue operands
   const void* in;     // sweep input (TIN)
   void* out;          // EPI_STORE destination / HJ: H^_x buffer (state type)
@@ -105,10 +108,17 @@ __device__ __forceinline__ int phys(int e) {
   return ee + (ee >> 4);
 }
 
+// For a lane chunk starting at e0 = kE*t (kE = 16): phys(e0 + j) =
+// 17*t + chunk_off(j), with chunk_off a compile-time constant for unrolled j.
+__host__ __device__ constexpr int chunk_off(int j) { return (j + kG) + ((j + kG) >> 4); }
+static_assert(kE == 16, "chunk_off assumes 16 points per lane");
+
+// Base offset of line l (32-bit division: the host keeps nlines < 2^31; a
+// 64-bit division would run on the FP64 pipe).
 __device__ __forceinline__ long long line_base(const LineGeom& g, long long l) {
-  const long long hi = l / g.nlo;
-  const long long lo = l - hi * g.nlo;
-  return hi * g.s_hi + lo * g.s_lo;
+  const unsigned int lu = unsigned(l), nlo = unsigned(g.nlo);
+  const unsigned int hi = lu / nlo, lo = lu - hi * nlo;
+  return (long long)hi * g.s_hi + (long long)lo * g.s_lo;
 }
 
 // ------------------------------------------------------------ conversions
@@ -139,6 +149,11 @@ __device__ __forceinline__ double f2d(float x) {
   return __hiloint2double(int(hi), int(lo));
 }
 
+template <typename T>
+__device__ __forceinline__ T pick(double d, float f) {
+  if constexpr (sizeof(T) == 4) return f; else return d;
+}
+
 // Non-finite test on the exponent bits (no floating-point instruction).
 __device__ __forceinline__ bool nonfinite(double x) { return (__double2hiint(x) & 0x7FF00000) == 0x7FF00000; }
 __device__ __forceinline__ bool nonfinite(float x) { return (__float_as_uint(x) & 0x7F800000u) == 0x7F800000u; }
@@ -153,11 +168,14 @@ __device__ __forceinline__ TO cvt(FROM x) {
 // ---------------------------------------------------------------- arithmetic
 // y <- a*y + b on y = hi + lo.  FP32: compensated (exact product error by FMA,
 // TwoSum for the addition).  FP64: plain FMA.
+#ifndef MOLT_COMPENSATED
+#define MOLT_COMPENSATED 1
+#endif
 template <typename T>
 struct Acc {
   T hi, lo;
   __device__ __forceinline__ void step(T a, T b) {
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4 && MOLT_COMPENSATED) {
       const T p = a * hi;
       const T pe = fmaf(a, hi, -p);
       const T s = p + b;
@@ -170,7 +188,7 @@ struct Acc {
     }
   }
   __device__ __forceinline__ T value() const {
-    if constexpr (sizeof(T) == 4) return hi + lo; else return hi;
+    if constexpr (sizeof(T) == 4 && MOLT_COMPENSATED) return hi + lo; else return hi;
   }
 };
 
@@ -305,7 +323,130 @@ __device__ __forceinline__ TileSmem carve(unsigned char* smem, const SweepArgs& 
 // step of the header comment) and leaves S_P (or, for MODE_RL, the per-axis
 // Lax-Friedrichs Hamiltonian) in the line buffers.  Returns the thread's
 // largest one-sided derivative magnitude (MODE_RL).  Ends synchronised.
-template <typename T, bool WENO, bool RAGGED>
+// Pairs of compute-type values advanced together: FP32 pairs use the packed
+// FP32x2 instructions of sm_100+ (FFMA2/FADD2/FMUL2), FP64 pairs plain FMAs.
+template <typename T> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+
+template <typename T>
+__device__ __forceinline__ typename Pair<T>::type pair2(T x, T y) {
+  typename Pair<T>::type r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+// a - b exactly as an FMA with -1
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 mul2(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 sub2(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+// Acc on a pair of independent recurrences (y <- a*y + b per component).
+template <typename T>
+struct Acc2 {
+  using V = typename Pair<T>::type;
+  V hi, lo;
+  __device__ __forceinline__ void step(V a, V b) {
+    if constexpr (sizeof(T) == 4 && MOLT_COMPENSATED) {
+      const V p = mul2(a, hi);
+      const V pe = fma2(a, hi, pair2<T>(-p.x, -p.y));
+      const V s = add2(p, b);
+      const V bb = sub2(s, p);
+      const V se = add2(sub2(p, sub2(s, bb)), sub2(b, bb));
+      lo = fma2(a, lo, add2(pe, se));
+      hi = s;
+    } else {
+      hi = fma2(a, hi, b);
+    }
+  }
+  __device__ __forceinline__ V value() const {
+    if constexpr (sizeof(T) == 4 && MOLT_COMPENSATED) return add2(hi, lo); else return hi;
+  }
+};
+
+// Line boundary constants (Sec. 2.3, Sec. 3.3) in FP64 from the line totals
+// I_R(b) = tbR and I_L(a) = tbL, returned as the initial values of the R and
+// L scans: periodic -> the cyclic values I(b)/(1-mu), I(a)/(1-mu);
+// Dirichlet L_0 -> 2A and 2B from the 2x2 system with determinant 1-mu^2;
+// Dirichlet L_R / L_L -> v(a) / v(b).  Exact-fit kernels divide Dirichlet
+// values by q (their end nodes keep the map (q, 0)).
+template <typename T, bool RAGGED>
+__device__ __forceinline__ void boundary_carries(const SweepArgs& a, const T* bw, int n, T tbR, T tbL, double* CR,
+                                                 double* CL) {
+  const double IRb = cvt<double>(tbR);
+  const double ILa = cvt<double>(tbL);
+  if (a.bc == 0) {
+    *CR = IRb * a.inv1mmu;
+    *CL = ILa * a.inv1mmu;
+    return;
+  }
+  const double v0 = cvt<double>(bw[phys(0)]), vN = cvt<double>(bw[phys(n - 1)]);
+  double cr, cl;
+  if (a.mode == MODE_0) {
+    const double r0 = fma(-0.5, ILa, v0), r1 = fma(-0.5, IRb, vN);
+    cr = 2.0 * fma(-a.mu, r1, r0) * a.invdet;
+    cl = 2.0 * fma(-a.mu, r0, r1) * a.invdet;
+  } else {
+    cr = v0;   // L_R^{-1}(a) = v(a)
+    cl = vN;   // L_L^{-1}(b) = v(b)
+  }
+  if (!RAGGED) {
+    cr *= a.invq;
+    cl *= a.invq;
+  }
+  *CR = cr;
+  *CL = cl;
+}
+
+// Compute-type (hi, lo) pair of an FP64 carry.
+template <typename T>
+__device__ __forceinline__ void split_carry(double c, T* hi, T* lo) {
+  const T h = cvt<T>(c);
+  *hi = h;
+  *lo = cvt<T>(c - cvt<double>(h));
+}
+
+// Ghost cells of one line by the lanes of the warp that owns it.
+template <typename T>
+__device__ __forceinline__ void warp_fill_ghosts(const SweepArgs& a, T* b, int lane) {
+  const int n = a.g.n;
+  if (lane < 3) {
+    const int j = lane + 1;  // ghost e = -j
+    T val;
+    if (a.bc == 0) {
+      int s = (-j) % n;
+      if (s < 0) s += n;
+      val = b[phys(s)];
+    } else {
+      const int m = j < n - 1 ? j : n - 1;
+      val = T(2) * b[phys(0)] - b[phys(m)];
+    }
+    b[phys(-j)] = val;
+  } else if (lane < 6) {
+    const int j = lane - 2;  // ghost e = n-1+j
+    T val;
+    if (a.bc == 0) {
+      val = b[phys((n - 1 + j) % n)];
+    } else {
+      const int m = n - 1 - j > 0 ? n - 1 - j : 0;
+      val = T(2) * b[phys(n - 1)] - b[phys(m)];
+    }
+    b[phys(n - 1 + j)] = val;
+  }
+}
+
+// WL (warp-local): every line is owned by a single warp (nwl == 1), so a D
+// application needs no CTA-wide barrier: ghosts, line totals and the FP64
+// boundary solve stay inside the warp (the solve runs on lane 0 and its
+// result is broadcast by shuffles).
+template <typename T, bool WENO, bool RAGGED, bool WL>
 __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSmem& sm, bool line_ok) {
   const int nwl = a.nwl, n = a.g.n;
   double* carries = sm.carries;
@@ -316,23 +457,29 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
   const int tl = part * 32 + lane;
   T* buf = lines + lw * a.LS;
   const int e0 = tl * kE;
+  T* cbase = buf + 17 * tl;   // phys(e0 + j) = 17*tl + chunk_off(j)
 
-  const T q = T(a.q);
-  const T qE = T(a.qE);
+  const T q = pick<T>(a.q, a.qf);
+  const T qE = pick<T>(a.qE, a.qEf);
   T c[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) c[i] = T(a.c[i]);
+  for (int i = 0; i < 6; ++i) c[i] = pick<T>(a.c[i], a.cf[i]);
   T sub[3][3], dw[3];
   if constexpr (WENO) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      dw[r] = T(a.d[r]);
+      dw[r] = pick<T>(a.d[r], a.df[r]);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) sub[r][j] = T(a.sub[r][j]);
+      for (int j = 0; j < 3; ++j) sub[r][j] = pick<T>(a.sub[r][j], a.subf[r][j]);
     }
   }
-  fill_ghosts(a, lines);
-  __syncthreads();
+  if constexpr (WL) {
+    warp_fill_ghosts(a, buf, lane);
+    __syncwarp();
+  } else {
+    fill_ghosts(a, lines);
+    __syncthreads();
+  }
 
   // element maps: (q, J) for points with a local integral, identity for
   // points past the end of the line and for the Dirichlet end nodes where the
@@ -345,7 +492,12 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
   const bool zeroR0 = !RAGGED && a.bc == 1 && e0 == 0;
   const bool zeroLN = !RAGGED && a.bc == 1 && e0 + kE == n;
 
-  T v[kE], S[kE], JR[kE], JL[kE];
+  // J_R(e0+k) and J_L(e0+kE-1-k) share the pair Y[k] so that the R chain
+  // (ascending) and the L chain (descending) of the recurrences advance
+  // together in packed FP32x2 instructions.
+  using T2 = typename Pair<T>::type;
+  T v[kE], S[kE];
+  T2 Y[kE];
 #pragma unroll
   for (int k = 0; k < kE; ++k) S[k] = T(0);
   T rmax = T(0);
@@ -355,7 +507,7 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
     {
       T win[kE + 6];
 #pragma unroll
-      for (int k = 0; k < kE + 6; ++k) win[k] = buf[phys(e0 - 3 + k)];
+      for (int k = 0; k < kE + 6; ++k) win[k] = cbase[chunk_off(k - 3)];
 #pragma unroll
       for (int k = 0; k < kE; ++k) {
         v[k] = win[k + 3];
@@ -366,8 +518,8 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
             wr[j] = win[k + j];        // offsets -3..1
             wl[j] = win[k + 6 - j];    // mirrored: v_{e+3} .. v_{e-1}
           }
-          JR[k] = wenoz_integral<T>(wr, sub, dw);
-          JL[k] = wenoz_integral<T>(wl, sub, dw);
+          Y[k].x = wenoz_integral<T>(wr, sub, dw);
+          Y[kE - 1 - (k)].y = wenoz_integral<T>(wl, sub, dw);
         } else {
           T r = T(0), l = T(0);
 #pragma unroll
@@ -375,26 +527,24 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
             r = fma(c[j], win[k + j], r);       // v_{e + (j-3)}
             l = fma(c[j], win[k + 6 - j], l);   // v_{e - (j-3)}
           }
-          JR[k] = r;
-          JL[k] = l;
+          Y[k].x = r;
+          Y[kE - 1 - (k)].y = l;
         }
       }
     }
-    if (zeroR0) JR[0] = T(0);
-    if (zeroLN) JL[kE - 1] = T(0);
+    if (zeroR0) Y[0].x = T(0);
+    if (zeroLN) Y[kE - 1 - (kE - 1)].y = T(0);
     // ---- 2a. lane folds (R ascending, L descending, interleaved)
     T aR, aL, bR, bL;
     if constexpr (!RAGGED) {
-      T r = T(0), l = T(0);
+      const T2 q2 = pair2<T>(q, q);
+      T2 y = pair2<T>(T(0), T(0));
 #pragma unroll
-      for (int k = 0; k < kE; ++k) {
-        r = fma(q, r, JR[k]);
-        l = fma(q, l, JL[kE - 1 - k]);
-      }
+      for (int k = 0; k < kE; ++k) y = fma2(q2, y, Y[k]);
       aR = qE;
       aL = qE;
-      bR = r;
-      bL = l;
+      bR = y.x;
+      bL = y.y;
     } else {
       T r = T(0), l = T(0);
       aR = T(1);
@@ -402,9 +552,9 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
 #pragma unroll
       for (int k = 0; k < kE; ++k) {
         const int e = e0 + k;
-        if (e >= eR0 && e < n) { r = fma(q, r, JR[k]); aR *= q; }
+        if (e >= eR0 && e < n) { r = fma(q, r, Y[k].x); aR *= q; }
         const int eL = e0 + kE - 1 - k;
-        if (eL <= eL1) { l = fma(q, l, JL[kE - 1 - k]); aL *= q; }
+        if (eL <= eL1) { l = fma(q, l, Y[kE - 1 - (kE - 1 - k)].y); aL *= q; }
       }
       bR = r;
       bL = l;
@@ -422,9 +572,11 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
     if (lane == 0) { exaR = T(1); exbR = T(0); }
     if (lane == 31) { exaL = T(1); exbL = T(0); }
     T* tot = totals + (lw * nwl) * 4;
-    if (lane == 31) { tot[part * 4 + 0] = aR; tot[part * 4 + 1] = bR; }
-    if (lane == 0) { tot[part * 4 + 2] = aL; tot[part * 4 + 3] = bL; }
-    __syncthreads();
+    if constexpr (!WL) {
+      if (lane == 31) { tot[part * 4 + 0] = aR; tot[part * 4 + 1] = bR; }
+      if (lane == 0) { tot[part * 4 + 2] = aL; tot[part * 4 + 3] = bL; }
+      __syncthreads();
+    }
     // ---- 2c. across the warps of the line
     T paR = T(1), pbR = T(0), paL = T(1), pbL = T(0);
     for (int j = 0; j < part; ++j) {
@@ -437,73 +589,67 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
       pbL = fma(A, pbL, B);
       paL *= A;
     }
-    // ---- 3. boundary constants in FP64, vectorised over the CTA's lines:
-    //         lane w of warp 0 solves line w (GB300's FP64 pipe is narrow, so
-    //         one warp instruction for all lines instead of one per line).
-    if (warp == 0 && lane < a.W) {
-      const T* tw = totals + (lane * nwl) * 4;
-      T tbR = T(0), tbL = T(0);
-      for (int j = 0; j < nwl; ++j) tbR = fma(tw[j * 4 + 0], tbR, tw[j * 4 + 1]);
-      for (int j = nwl - 1; j >= 0; --j) tbL = fma(tw[j * 4 + 2], tbL, tw[j * 4 + 3]);
-      const double IRb = cvt<double>(tbR);   // I_R(b): R recurrence total from 0
-      const double ILa = cvt<double>(tbL);   // I_L(a)
-      double CR = 0.0, CL = 0.0;
-      if (a.bc == 0) {
-        // periodic: the cyclic recurrence's value before the first element
-        CR = IRb * a.inv1mmu;
-        CL = ILa * a.inv1mmu;
-      } else {
-        const T* bw = lines + lane * a.LS;
-        const double v0 = cvt<double>(bw[phys(0)]), vN = cvt<double>(bw[phys(n - 1)]);
-        if (a.mode == MODE_0) {
-          const double r0 = fma(-0.5, ILa, v0), r1 = fma(-0.5, IRb, vN);
-          // (A, B) = (1 - mu^2)^{-1} [[1, -mu], [-mu, 1]] (r0, r1); the
-          // carries are 2A and 2B (initial values of the R and L scans)
-          CR = 2.0 * fma(-a.mu, r1, r0) * a.invdet;
-          CL = 2.0 * fma(-a.mu, r0, r1) * a.invdet;
-        } else {
-          CR = v0;   // L_R^{-1}(a) = v(a)
-          CL = vN;   // L_L^{-1}(b) = v(b)
-        }
-        if (!RAGGED) {
-          CR *= a.invq;
-          CL *= a.invq;
-        }
+    // ---- 3. boundary constants in FP64
+    T cRh, cRl, cLh, cLl;
+    if constexpr (WL) {
+      // lane 31 holds the R line total, lane 0 the L line total
+      const T tbR = __shfl_sync(0xffffffffu, bR, 31);
+      const T tbL = __shfl_sync(0xffffffffu, bL, 0);
+      T c4[4] = {T(0), T(0), T(0), T(0)};
+      if (lane == 0) {
+        double CR, CL;
+        boundary_carries<T, RAGGED>(a, buf, n, tbR, tbL, &CR, &CL);
+        split_carry<T>(CR, &c4[0], &c4[1]);
+        split_carry<T>(CL, &c4[2], &c4[3]);
       }
-      // split into compute-type (hi, lo) pairs
-      T* cw = reinterpret_cast<T*>(carries) + lane * 4;
-      const T rh = cvt<T>(CR), lh = cvt<T>(CL);
-      cw[0] = rh;
-      cw[1] = cvt<T>(CR - cvt<double>(rh));
-      cw[2] = lh;
-      cw[3] = cvt<T>(CL - cvt<double>(lh));
+      cRh = __shfl_sync(0xffffffffu, c4[0], 0);
+      cRl = __shfl_sync(0xffffffffu, c4[1], 0);
+      cLh = __shfl_sync(0xffffffffu, c4[2], 0);
+      cLl = __shfl_sync(0xffffffffu, c4[3], 0);
+    } else {
+      // vectorised over the CTA's lines: lane w of warp 0 solves line w
+      // (GB300's FP64 pipe is narrow: one warp instruction for all lines)
+      if (warp == 0 && lane < a.W) {
+        const T* tw = totals + (lane * nwl) * 4;
+        T tbR = T(0), tbL = T(0);
+        for (int j = 0; j < nwl; ++j) tbR = fma(tw[j * 4 + 0], tbR, tw[j * 4 + 1]);
+        for (int j = nwl - 1; j >= 0; --j) tbL = fma(tw[j * 4 + 2], tbL, tw[j * 4 + 3]);
+        double CR, CL;
+        boundary_carries<T, RAGGED>(a, lines + lane * a.LS, n, tbR, tbL, &CR, &CL);
+        T* cw = reinterpret_cast<T*>(carries) + lane * 4;
+        split_carry<T>(CR, &cw[0], &cw[1]);
+        split_carry<T>(CL, &cw[2], &cw[3]);
+      }
+      __syncthreads();
+      const T* cw = reinterpret_cast<const T*>(carries) + lw * 4;
+      cRh = cw[0];
+      cRl = cw[1];
+      cLh = cw[2];
+      cLl = cw[3];
     }
-    __syncthreads();
     // ---- 4. carries into the lane and the fix-up passes
     {
-      const T* cw = reinterpret_cast<const T*>(carries) + lw * 4;
-      const T cRh = cw[0], cRl = cw[1], cLh = cw[2], cLl = cw[3];
       const T laR = exaR * paR, lbR = fma(exaR, pbR, exbR);
       const T laL = exaL * paL, lbL = fma(exaL, pbL, exbL);
-      Acc<T> yR{fma(laR, cRh, lbR), laR * cRl};
-      Acc<T> yL{fma(laL, cLh, lbL), laL * cLl};
       if constexpr (!RAGGED) {
+        const T2 q2 = pair2<T>(q, q);
+        Acc2<T> y{pair2<T>(fma(laR, cRh, lbR), fma(laL, cLh, lbL)), pair2<T>(laR * cRl, laL * cLl)};
 #pragma unroll
         for (int k = 0; k < kE; ++k) {
-          yR.step(q, JR[k]);
-          JR[k] = yR.value();
-          yL.step(q, JL[kE - 1 - k]);
-          JL[kE - 1 - k] = yL.value();
+          y.step(q2, Y[k]);
+          Y[k] = y.value();
         }
       } else {
+        Acc<T> yR{fma(laR, cRh, lbR), laR * cRl};
+        Acc<T> yL{fma(laL, cLh, lbL), laL * cLl};
 #pragma unroll
         for (int k = 0; k < kE; ++k) {
           const int e = e0 + k;
-          if (e >= eR0 && e < n) yR.step(q, JR[k]);
-          JR[k] = yR.value();
+          if (e >= eR0 && e < n) yR.step(q, Y[k].x);
+          Y[k].x = yR.value();
           const int kl = kE - 1 - k;
-          if (e0 + kl <= eL1) yL.step(q, JL[kl]);
-          JL[kl] = yL.value();
+          if (e0 + kl <= eL1) yL.step(q, Y[kE - 1 - (kl)].y);
+          Y[kE - 1 - (kl)].y = yL.value();
         }
       }
     }
@@ -511,11 +657,11 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
     if (a.mode == MODE_RL) {
       // one-sided derivatives v^- = alpha D_R, v^+ = -alpha D_L and the
       // per-axis part of the Lax-Friedrichs Hamiltonian (Sec. 2.5)
-      const T al = T(a.alpha);
+      const T al = pick<T>(a.alpha, a.alphaf);
 #pragma unroll
       for (int k = 0; k < kE; ++k) {
-        const T vm = al * (v[k] - JR[k]);
-        const T vp = -al * (v[k] - JL[k]);
+        const T vm = al * (v[k] - Y[k].x);
+        const T vp = -al * (v[k] - Y[kE - 1 - (k)].y);
         const T r = fmax(fabs(vm), fabs(vp));
         const T mean = T(0.5) * (vm + vp);
         S[k] = T(0.5) * mean * mean + r * T(0.5) * (vm - vp);
@@ -525,107 +671,174 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
 #pragma unroll
       for (int k = 0; k < kE; ++k) {
         T linv;
-        if (a.mode == MODE_0) linv = T(0.5) * (JR[k] + JL[k]);
-        else if (a.mode == MODE_R) linv = JR[k];
-        else linv = JL[k];
+        if (a.mode == MODE_0) linv = T(0.5) * (Y[k].x + Y[kE - 1 - (k)].y);
+        else if (a.mode == MODE_R) linv = Y[k].x;
+        else linv = Y[kE - 1 - (k)].y;
         v[k] = v[k] - linv;
         S[k] += v[k];
       }
     }
     if (p + 1 < a.P) {
-      __syncthreads();
+      if constexpr (WL) {
+        __syncwarp();
 #pragma unroll
-      for (int k = 0; k < kE; ++k)
-        if (e0 + k < n) buf[phys(e0 + k)] = v[k];
-      __syncthreads();
-      fill_ghosts(a, lines);
-      __syncthreads();
+        for (int k = 0; k < kE; ++k)
+          if (RAGGED ? e0 + k < n : true) cbase[chunk_off(k)] = v[k];
+        __syncwarp();
+        warp_fill_ghosts(a, buf, lane);
+        __syncwarp();
+      } else {
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kE; ++k)
+          if (RAGGED ? e0 + k < n : true) cbase[chunk_off(k)] = v[k];
+        __syncthreads();
+        fill_ghosts(a, lines);
+        __syncthreads();
+      }
     }
   }
 
-  __syncthreads();
+  if constexpr (WL) __syncwarp(); else __syncthreads();
 #pragma unroll
   for (int k = 0; k < kE; ++k)
-    if (e0 + k < n) buf[phys(e0 + k)] = S[k];
+    if (RAGGED ? e0 + k < n : true) cbase[chunk_off(k)] = S[k];
   __syncthreads();
   return cvt<double>(rmax);
 }
+
+#ifndef MOLT_WL_MODE
+#define MOLT_WL_MODE 0
+#endif
+template <typename T, bool WENO, bool RAGGED>
+__device__ __forceinline__ double compute_lines_any(const SweepArgs& a, const TileSmem& sm, bool line_ok) {
+#if MOLT_WL_MODE == 0
+  return compute_lines<T, WENO, RAGGED, false>(a, sm, line_ok);
+#elif MOLT_WL_MODE == 2
+  return compute_lines<T, WENO, RAGGED, true>(a, sm, line_ok);
+#else
+  if (a.nwl == 1) return compute_lines<T, WENO, RAGGED, true>(a, sm, line_ok);
+  return compute_lines<T, WENO, RAGGED, false>(a, sm, line_ok);
+#endif
+}
+
+// Epilogue operands of one point, loaded ahead of the stores so that the
+// loads of a batch of points are in flight together (the compiler cannot
+// move a load past a store to a possibly aliasing array).
+template <typename T, typename TST>
+struct EpiOps {
+  T acc;
+  TST x, y;
+};
 
 template <typename T, typename TST, int EPI>
 struct Epilogue {
   const SweepArgs& a;
   double dt;
-  __device__ __forceinline__ void operator()(long long gidx, T s) const {
+
+  __device__ __forceinline__ EpiOps<T, TST> load(long long gidx) const {
+    EpiOps<T, TST> o{T(0), TST(0), TST(0)};
+    if constexpr (EPI == EPI_ACC_ADD) {
+      o.acc = static_cast<const T*>(a.acc)[gidx];
+    } else if constexpr (EPI == EPI_HEAT_FINAL || EPI == EPI_WAVE_FINAL) {
+      if (a.acc) o.acc = static_cast<const T*>(a.acc)[gidx];
+      o.x = static_cast<const TST*>(a.un)[gidx];
+      if (EPI == EPI_HEAT_FINAL || !a.from_rest) o.y = static_cast<const TST*>(a.us)[gidx];
+    } else if constexpr (EPI == EPI_HJ_Y) {
+      o.x = static_cast<const TST*>(a.un)[gidx];
+      if (a.out) o.y = static_cast<const TST*>(a.out)[gidx];
+    }
+    return o;
+  }
+
+  __device__ __forceinline__ void store(long long gidx, T s, const EpiOps<T, TST>& o) const {
     if constexpr (EPI == EPI_STORE) {
       static_cast<TST*>(a.out)[gidx] = cvt<TST>(s);
     } else if constexpr (EPI == EPI_ACC_SET) {
       static_cast<T*>(a.acc)[gidx] = s;
     } else if constexpr (EPI == EPI_ACC_ADD) {
-      static_cast<T*>(a.acc)[gidx] += s;
+      static_cast<T*>(a.acc)[gidx] = o.acc + s;
     } else if constexpr (EPI == EPI_HEAT_FINAL) {
-      const T tot = (a.acc ? static_cast<const T*>(a.acc)[gidx] : T(0)) + s;
-      const TST un = static_cast<const TST*>(a.un)[gidx];
-      const TST us = static_cast<const TST*>(a.us)[gidx];
-      const TST r = fma(TST(a.a0), un, TST(a.a1) * fma(TST(a.coefS), cvt<TST>(tot), us));
+      // u_s = a0 u^n + a1 (u_{s-1} + dt F), dt F = coefS (acc + S)
+      const TST r = fma(TST(a.a0), o.x, TST(a.a1) * fma(TST(a.coefS), cvt<TST>(o.acc + s), o.y));
       static_cast<TST*>(a.dst)[gidx] = r;
       if (a.shadow) a.shadow[gidx] = cvt<float>(r);
       if (nonfinite(r)) atomicOr(a.status, ST_NONFINITE);
     } else if constexpr (EPI == EPI_WAVE_FINAL) {
-      const T tot = (a.acc ? static_cast<const T*>(a.acc)[gidx] : T(0)) + s;
-      const TST u = static_cast<const TST*>(a.un)[gidx];
-      TST r;
-      if (a.from_rest) r = fma(TST(0.5 * a.coefS), cvt<TST>(tot), u);
-      else r = fma(TST(a.coefS), cvt<TST>(tot), fma(TST(2), u, -static_cast<const TST*>(a.us)[gidx]));
-      if (a.dst2) static_cast<TST*>(a.dst2)[gidx] = u;
+      // u^{n+1} = 2u^n - u^{n-1} + coefS (acc + S)   (from rest: u^n + coefS/2 (acc + S))
+      const TST tot = cvt<TST>(o.acc + s);
+      const TST r = a.from_rest ? fma(TST(0.5 * a.coefS), tot, o.x) : fma(TST(a.coefS), tot, fma(TST(2), o.x, -o.y));
+      if (a.dst2) static_cast<TST*>(a.dst2)[gidx] = o.x;
       static_cast<TST*>(a.dst)[gidx] = r;
       if (a.shadow) a.shadow[gidx] = cvt<float>(r);
       if (nonfinite(r)) atomicOr(a.status, ST_NONFINITE);
     } else if constexpr (EPI == EPI_HJ_X) {
       if (a.out) static_cast<TST*>(a.out)[gidx] = TST(s);
     } else if constexpr (EPI == EPI_HJ_Y) {
-      const TST u = static_cast<const TST*>(a.un)[gidx];
-      const TST hx = a.out ? static_cast<const TST*>(a.out)[gidx] : TST(0);
-      const TST r = u - TST(dt) * (hx + TST(s));
+      const TST r = o.x - TST(dt) * (o.y + TST(s));
       static_cast<TST*>(a.dst)[gidx] = r;
       if (nonfinite(r)) atomicOr(a.status, ST_NONFINITE);
     }
   }
-
 };
 
-// Applies the epilogue to the tile's W lines in the coalesced mapping.
+// Applies the epilogue to the tile's W lines in the coalesced mapping, in
+// batches of kEpiBatch points per thread: all operand loads of a batch are
+// issued before its stores.
+constexpr int kEpiBatch = 8;
+
 template <typename T, typename TST, int EPI>
 __device__ __forceinline__ void epilogue_tile(const SweepArgs& a, const T* lines, long long line0, double dt) {
-  const Epilogue<T, TST, EPI> apply{a, dt};
+  const Epilogue<T, TST, EPI> ep{a, dt};
   const int W = a.W, n = a.g.n, nwl = a.nwl;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  long long g0;
+  const T* src0;
+  int p0, pstep, sstep;
+  long long gstep;
   if (a.contiguous) {
     const int lw = warp / nwl, tl = (warp - lw * nwl) * 32 + lane;
-    if (line0 + lw < a.g.nlines) {
-      const long long base = line_base(a.g, line0 + lw);
-      const T* buf = lines + lw * a.LS;
-      const int step = nwl * 32;
-      for (int p = tl; p < n; p += step) apply(base + p, buf[phys(p)]);
-    }
+    if (line0 + lw >= a.g.nlines) return;
+    p0 = tl;
+    pstep = nwl * 32;
+    g0 = line_base(a.g, line0 + lw) + p0;
+    gstep = pstep;
+    src0 = lines + lw * a.LS;
+    sstep = 0;
   } else {
     const int w = tid % W;
-    const int prow = blockDim.x / W;
     const long long gl = line0 + w;
-    if (gl < a.g.nlines) {
-      const long long st = a.g.stride;
-      int p = tid / W;
-      long long g = line_base(a.g, gl) + p * st;
-      const long long gstep = prow * st;
-      const T* src = lines + w * a.LS + phys(p);
-      const int sstep = prow + (prow >> 4);
-#pragma unroll 4
-      for (; p < n; p += prow) {
-        apply(g, *src);
-        g += gstep;
-        src += sstep;
+    if (gl >= a.g.nlines) return;
+    p0 = tid / W;
+    pstep = blockDim.x / W;
+    g0 = line_base(a.g, gl) + p0 * a.g.stride;
+    gstep = pstep * a.g.stride;
+    src0 = lines + w * a.LS;
+    sstep = 1;
+  }
+  // shared index of point p: contiguous lines step p by a multiple of 32,
+  // strided lines by blockDim/W (a multiple of 16), so phys() advances by a
+  // constant in both cases
+  const int pdelta = pstep + (pstep >> 4);
+  const T* sp = src0 + phys(p0);
+  long long g = g0;
+  for (int pb = p0; pb < n; pb += kEpiBatch * pstep) {
+    EpiOps<T, TST> ops[kEpiBatch];
+    T sv[kEpiBatch];
+#pragma unroll
+    for (int k = 0; k < kEpiBatch; ++k) {
+      if (pb + k * pstep < n) {
+        ops[k] = ep.load(g + k * gstep);
+        sv[k] = sp[k * pdelta];
       }
     }
+#pragma unroll
+    for (int k = 0; k < kEpiBatch; ++k)
+      if (pb + k * pstep < n) ep.store(g + k * gstep, sv[k], ops[k]);
+    g += kEpiBatch * gstep;
+    sp += kEpiBatch * pdelta;
   }
+  (void)sstep;
 }
 
 template <int EPI>
@@ -661,7 +874,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) sweep_kernel(const SweepArgs a
   const int tl = (warp - lw * a.nwl) * 32 + (threadIdx.x & 31);
   load_tile<T, TIN>(a, static_cast<const TIN*>(a.in), lines, line0, lw, tl);
   __syncthreads();
-  const double rmax = compute_lines<T, WENO, RAGGED>(a, sm, line0 + lw < a.g.nlines);
+  const double rmax = compute_lines_any<T, WENO, RAGGED>(a, sm, line0 + lw < a.g.nlines);
   publish_speed<EPI>(a, rmax);
   const double dt = hj_dt<EPI>(a);
   if (EPI == EPI_HJ_Y && blockIdx.x == 0 && threadIdx.x == 0 && a.t_dev) *a.t_dev += dt;

@@ -99,7 +99,8 @@ __device__ __forceinline__ void issue_tile(const SweepArgs& a, const TmaGeom& tg
   if (tg.kind == 0) {
     for (int b = 0; b < tg.nbox; ++b) tma_load_2d(stage + b * boxel, map, b * tg.box_p, int(line0), bar);
   } else {
-    const int hi = int(line0 / tg.nx), x0 = int(line0 - (long long)hi * tg.nx);
+    const unsigned int l0 = unsigned(line0), nxu = unsigned(tg.nx);
+    const int hi = int(l0 / nxu), x0 = int(l0 - unsigned(hi) * nxu);
     for (int b = 0; b < tg.nbox; ++b) {
       if (tg.kind == 1) tma_load_3d(stage + b * boxel, map, x0, b * tg.box_p, hi, bar);
       else tma_load_3d(stage + b * boxel, map, x0, hi, b * tg.box_p, bar);
@@ -154,11 +155,17 @@ __device__ __forceinline__ void transpose_tile(const SweepArgs& a, const TmaGeom
     const int tl = (warp - lw * a.nwl) * 32 + (threadIdx.x & 31);
     const int step = a.nwl * 32;
     T* dst = lines + lw * a.LS;
-    const int sh = __ffs(tg.box_p) - 1;
+    // box_p and step are multiples of 16 (or box_p == n < step): phys()
+    // advances by a constant along r
+    for (int b = 0; b < tg.nbox; ++b) {
+      const TIN* src = stage + (b * W + lw) * tg.box_p;
+      T* d = dst + phys(b * tg.box_p + tl);
+      const int dstep = step + (step >> 4);
 #pragma unroll 4
-    for (int p = tl; p < n; p += step) {
-      const int b = p >> sh, r = p & (tg.box_p - 1);
-      dst[phys(p)] = cvt<T>(stage[(b * W + lw) * tg.box_p + r]);
+      for (int r = tl; r < tg.box_p; r += step) {
+        *d = cvt<T>(src[r]);
+        d += dstep;
+      }
     }
   } else {
     // stage: [p][W]
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
       }
       prefetch_operands<T, TST, EPI>(a, next * a.W);
     }
-    rmax = fmax(rmax, compute_lines<T, WENO, false>(a, sm, line0 + lw < a.g.nlines));
+    rmax = fmax(rmax, compute_lines_any<T, WENO, false>(a, sm, line0 + lw < a.g.nlines));
     epilogue_tile<T, TST, EPI>(a, lines, line0, dt);
     __syncthreads();
   }
