@@ -127,7 +127,16 @@ molt_status molt_step(molt_ctx* ctx, void* const* u, void* const* u_prev, int ns
  *   MOLT_OPT_PROFILE  1: record a CUDA event pair around every sweep launch
  *                     (read back with molt_profile_read); 0 (default): off.
  * Returns MOLT_EINVAL for an unknown option or value. */
-typedef enum { MOLT_OPT_TMA = 0, MOLT_OPT_PROFILE = 1 } molt_option;
+typedef enum {
+  MOLT_OPT_TMA = 0,
+  MOLT_OPT_PROFILE = 1,
+  MOLT_OPT_WAIT_LIMIT = 2,        /* cycles a device-side wait may take before the
+                                     kernel records MOLT_ETIMEOUT and returns
+                                     (default 2e9, >= 1000)                      */
+  MOLT_OPT_TEST_SKIP_ARRIVE = 3   /* test hook: 1 makes one CTA of the batched step
+                                     skip its first grid barrier, so the others'
+                                     bounded waits run out (MOLT_ETIMEOUT)       */
+} molt_option;
 molt_status molt_set_option(molt_ctx* ctx, int option, int64_t value);
 
 /* Kinds of sweep launches, by the work their epilogue does. */
@@ -138,7 +147,9 @@ typedef enum {
   MOLT_KERNEL_HEAT_FINAL = 3,  /* last axis + Runge-Kutta stage update        */
   MOLT_KERNEL_WAVE_FINAL = 4,  /* last axis + leapfrog update                 */
   MOLT_KERNEL_HJ_X = 5,        /* Hamilton-Jacobi: first axes                 */
-  MOLT_KERNEL_HJ_Y = 6         /* Hamilton-Jacobi: last axis + update         */
+  MOLT_KERNEL_HJ_Y = 6,        /* Hamilton-Jacobi: last axis + update         */
+  MOLT_KERNEL_UPDATE = 7,      /* FP64 state update of the FP32-sweep forms   */
+  MOLT_KERNEL_BATCH = 8        /* one persistent batched heat step            */
 } molt_kernel_kind;
 
 /* With MOLT_OPT_PROFILE on: synchronises the stream, returns the summed
@@ -173,6 +184,20 @@ molt_status molt_profile_read(molt_ctx* ctx, int kind, double* total_ms, int64_t
  * non-finite value reached u_next).  Allocates nothing, host or device. */
 molt_status molt_wave_step_noalloc(const molt_desc* desc, const double* u, const double* u_prev, double* u_next,
                                    int from_rest, void* cuda_stream);
+
+/* Batched step (count > 1; every problem 2-D heat, MOLT_PREC_F32_F64UPDATE,
+ * linear weights, sides that tile exactly -- multiples of 128 up to 8192 in
+ * power-of-two warps per line): molt_step advances all problems with ONE
+ * persistent cooperative kernel per time step, captured in a CUDA graph when
+ * the stream is not the legacy default stream.  Its phases (x sweeps, y
+ * sweeps, FP64 update; three Runge-Kutta stages) are separated by grid
+ * barriers with bounded waits.  The first molt_step autotunes, per size class
+ * and axis, the line-tile shape (points per lane 16, 8 or 4, hence warps per
+ * line and lines per 512-thread tile) by timing each candidate.  This call
+ * reports the shape chosen for (problem, axis); MOLT_EUNSUPPORTED before the
+ * first batched step or for contexts that do not batch. */
+molt_status molt_batch_tile_shape(molt_ctx* ctx, int problem, int axis, int* points_per_lane, int* warps_per_line,
+                                  int* lines_per_tile);
 
 /* Release everything the context owns.  Synchronises its stream first. */
 molt_status molt_destroy(molt_ctx* ctx);

@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -13,6 +14,7 @@
 #include "coeffs.h"
 #include "molt.h"
 #include "sweep_launch.h"
+#include "batch.cuh"
 
 using namespace molt;
 
@@ -36,8 +38,25 @@ struct Problem {
 
 }  // namespace
 
+struct BatchState {
+  bool checked = false, supported = false, tuned = false;
+  std::vector<int> E[2];                 // tuned points per lane per problem, per axis
+  BatchSweep* d_sweeps = nullptr;
+  BatchUpdate* d_updates = nullptr;
+  unsigned int* d_bar = nullptr;         // [count, generation]
+  BatchParams params{};
+  size_t smem = 0;
+  int grid = 0;
+  std::vector<void*> last_u;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_failed = false;
+};
+
 struct molt_ctx {
   cudaStream_t stream = nullptr;
+  BatchState batch;
+  long long wait_limit = 2000000000LL;   // cycles a device-side wait may take
+  bool test_skip_arrive = false;         // test hook: one CTA skips the first grid barrier
   std::vector<Problem> probs;
   int* status_dev = nullptr;       // device status word
   unsigned long long* speed_dev = nullptr;  // per problem: 2 speed slots (double bits)
@@ -153,7 +172,8 @@ int phys_host(int e) {
 }
 
 // Builds the kernel arguments for sum_{p<=P} D_mode^p along `ax` with alpha.
-molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, double alpha, Plan* out) {
+molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, double alpha, Plan* out,
+                      int E = kE) {
   SweepArgs& a = out->a;
   std::memset(&a, 0, sizeof(a));
   out->ax = ax;
@@ -176,7 +196,7 @@ molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, do
     a.d[r] = qt.d[r];
   }
   a.q = qt.q;
-  a.qE = std::exp(-nu * double(kE));
+  a.qE = std::exp(-nu * double(E));
   a.invq = std::exp(nu);
   for (int i = 0; i < 6; ++i) a.cf[i] = float(a.c[i]);
   for (int r = 0; r < 3; ++r) {
@@ -192,15 +212,15 @@ molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, do
   a.inv1mmu = 1.0 / (-std::expm1(-nu * double(N)));
   a.invdet = 1.0 / (-std::expm1(-2.0 * nu * double(N)));
   // tile shape: nwl warps per line, W lines per CTA, <= kMaxThreads threads
-  const int nwl = (n + 32 * kE - 1) / (32 * kE);
+  const int nwl = (n + 32 * E - 1) / (32 * E);
   if (nwl > kMaxThreads / 32) return fail(c, MOLT_EUNSUPPORTED, "line longer than 8192 points");
   int W = (kMaxThreads / 32) / nwl;
   int Wp = 1;
   while (Wp * 2 <= W) Wp *= 2;
   W = Wp;
   while (W > 1 && (long long)W / 2 >= a.g.nlines) W /= 2;
-  const int cap = nwl * 32 * kE;
-  int LS = phys_host(cap + 3) + 1;
+  const int cap = nwl * 32 * E;
+  int LS = (E == 16 ? phys<16>(cap + 3) : (E == 8 ? phys<8>(cap + 3) : phys<4>(cap + 3))) + 1;
   LS = (LS + 31) / 32 * 32 + (W < 32 ? 32 / W : 1);
   a.W = W;
   a.nwl = nwl;
@@ -403,7 +423,8 @@ molt_status molt_create(const molt_desc* descs, int count, void* cuda_stream, mo
     const size_t cb = compute_bytes(p.d), sb = state_bytes(p.d);
     const size_t tot = size_t(p.total);
     bool ok = true;
-    if (p.d.ndim > 1 && p.d.pde != MOLT_PDE_HJ) ok = ok && cudaMalloc(&p.acc, cb * tot) == cudaSuccess;
+    if ((p.d.ndim > 1 || is_mixed(p.d)) && p.d.pde != MOLT_PDE_HJ)
+      ok = ok && cudaMalloc(&p.acc, cb * tot) == cudaSuccess;
     if (p.d.pde == MOLT_PDE_HEAT) {
       ok = ok && cudaMalloc(&p.stage1, sb * tot) == cudaSuccess;
       ok = ok && cudaMalloc(&p.stage2, sb * tot) == cudaSuccess;
@@ -455,6 +476,70 @@ __global__ void shadow_kernel(const double* __restrict__ in, float* __restrict__
     out[i] = d2f(in[i]);
 }
 
+// FP64 state updates of the FP32-sweep (mixed) forms, as streaming kernels:
+// every warp of the GPU can overlap their loads, stores and FP64 FMAs, which
+// the sweep kernel's epilogue (one CTA per SM, after its scans) cannot.
+//   heat:  u_s = a0 u^n + a1 (u_{s-1} + coefS * acc)       (SSP-RK3 stage)
+//   wave:  u^{n+1} = 2u^n - u^{n-1} + coefS * acc          (leapfrog)
+//          from rest: u^1 = u^0 + coefS/2 * acc            (Taylor start)
+// acc holds sum_d S_{P,d} of the stage input in FP32.  Each also refreshes
+// the FP32 copy the next sweeps read and flags non-finite values.
+__global__ void heat_update_kernel(const float* __restrict__ acc, const double* un, const double* us, double* dst,
+                                   float* __restrict__ shadow, double a0, double a1, double coefS, long long n,
+                                   int* status) {
+  bool bad = false;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double r = fma(a0, un[i], a1 * fma(coefS, f2d(acc[i]), us[i]));
+    dst[i] = r;
+    shadow[i] = d2f(r);
+    bad |= nonfinite(r);
+  }
+  if (bad) atomicOr(status, ST_NONFINITE);
+}
+
+__global__ void wave_update_kernel(const float* __restrict__ acc, const double* un, const double* uprev,
+                                   double* dst, double* dst2, float* __restrict__ shadow, double coefS,
+                                   int from_rest, long long n, int* status) {
+  bool bad = false;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double u = un[i];
+    const double w = f2d(acc[i]);
+    const double r = from_rest ? fma(0.5 * coefS, w, u) : fma(coefS, w, fma(2.0, u, -uprev[i]));
+    if (dst2) dst2[i] = u;
+    dst[i] = r;
+    shadow[i] = d2f(r);
+    bad |= nonfinite(r);
+  }
+  if (bad) atomicOr(status, ST_NONFINITE);
+}
+
+int stream_grid(long long n) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long blocks = (n + 255) / 256;
+  if (blocks > 8LL * sms) blocks = 8LL * sms;
+  return int(blocks < 1 ? 1 : blocks);
+}
+
+molt_status record_begin(molt_ctx* c, molt_ctx::Rec* rec, int kind) {
+  rec->kind = kind;
+  rec->start = rec->stop = nullptr;
+  if (c->profile) {
+    cudaEventCreate(&rec->start);
+    cudaEventCreate(&rec->stop);
+    cudaEventRecord(rec->start, c->stream);
+  }
+  return MOLT_OK;
+}
+
+void record_end(molt_ctx* c, molt_ctx::Rec* rec) {
+  if (c->profile) {
+    cudaEventRecord(rec->stop, c->stream);
+    c->recs.push_back(*rec);
+  }
+}
+
 molt_status refresh_shadow(molt_ctx* c, Problem& p, const void* u) {
   if (!p.shadow) return MOLT_OK;
   int dev = 0, sms = 148;
@@ -485,7 +570,8 @@ molt_status heat_step(molt_ctx* c, Problem& p, void* u) {
       pl.a.in = sweep_input(p, ins[s]);
       pl.a.acc = p.acc;
       int epi;
-      if (ax + 1 < p.d.ndim) {
+      const bool last = ax + 1 == p.d.ndim;
+      if (!last || p.shadow) {
         epi = ax == 0 ? EPI_ACC_SET : EPI_ACC_ADD;
       } else {
         epi = EPI_HEAT_FINAL;
@@ -493,12 +579,21 @@ molt_status heat_step(molt_ctx* c, Problem& p, void* u) {
         pl.a.un = u;
         pl.a.us = ins[s];
         pl.a.dst = dsts[s];
-        pl.a.shadow = p.shadow;
         pl.a.a0 = rk[s][0];
         pl.a.a1 = rk[s][1];
         pl.a.coefS = coefS;
       }
       if ((st = run(c, p, epi, pl)) != MOLT_OK) return st;
+      if (last && p.shadow) {
+        molt_ctx::Rec rec;
+        record_begin(c, &rec, MOLT_KERNEL_UPDATE);
+        heat_update_kernel<<<stream_grid(p.total), 256, 0, c->stream>>>(
+            static_cast<const float*>(p.acc), static_cast<const double*>(u), static_cast<const double*>(ins[s]),
+            static_cast<double*>(dsts[s]), p.shadow, rk[s][0], rk[s][1], coefS, p.total, c->status_dev);
+        record_end(c, &rec);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(c, e, "heat update");
+      }
     }
   }
   return MOLT_OK;
@@ -513,7 +608,8 @@ molt_status wave_step(molt_ctx* c, Problem& p, void* cur, void* prev, bool from_
     pl.a.in = sweep_input(p, cur);
     pl.a.acc = p.acc;
     int epi;
-    if (ax + 1 < p.d.ndim) {
+    const bool last = ax + 1 == p.d.ndim;
+    if (!last || p.shadow) {
       epi = ax == 0 ? EPI_ACC_SET : EPI_ACC_ADD;
     } else {
       epi = EPI_WAVE_FINAL;
@@ -522,7 +618,6 @@ molt_status wave_step(molt_ctx* c, Problem& p, void* cur, void* prev, bool from_
       pl.a.us = prev;
       pl.a.coefS = -p.d.beta * p.d.beta;
       pl.a.from_rest = from_rest ? 1 : 0;
-      pl.a.shadow = p.shadow;
       if (in_place_variant) {
         pl.a.dst = cur;
         pl.a.dst2 = prev;
@@ -531,6 +626,17 @@ molt_status wave_step(molt_ctx* c, Problem& p, void* cur, void* prev, bool from_
       }
     }
     if ((st = run(c, p, epi, pl)) != MOLT_OK) return st;
+    if (last && p.shadow) {
+      molt_ctx::Rec rec;
+      record_begin(c, &rec, MOLT_KERNEL_UPDATE);
+      wave_update_kernel<<<stream_grid(p.total), 256, 0, c->stream>>>(
+          static_cast<const float*>(p.acc), static_cast<const double*>(cur), static_cast<const double*>(prev),
+          static_cast<double*>(in_place_variant ? cur : prev), in_place_variant ? static_cast<double*>(prev) : nullptr,
+          p.shadow, -p.d.beta * p.d.beta, from_rest ? 1 : 0, p.total, c->status_dev);
+      record_end(c, &rec);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(c, e, "wave update");
+    }
   }
   return MOLT_OK;
 }
@@ -583,6 +689,244 @@ molt_status hj_step(molt_ctx* c, Problem& p, int idx, void* u) {
   return MOLT_OK;
 }
 
+// ------------------------------------------------------------------ batch
+// Shapes a batch problem's line tile may take on one axis: points per lane E
+// with n = 32 * nwl * E exactly and nwl | 16 (so 32 * nwl * W = 512).
+bool shape_ok(int64_t n, int E) {
+  if (n % (32 * E) != 0) return false;
+  const int64_t nwl = n / (32 * E);
+  return nwl >= 1 && nwl <= 16 && (16 % nwl) == 0;
+}
+
+bool batch_supported(const molt_ctx* c) {
+  if (c->probs.size() < 2) return false;
+  for (const auto& p : c->probs) {
+    const molt_desc& d = p.d;
+    if (d.pde != MOLT_PDE_HEAT || d.prec != MOLT_PREC_F32_F64UPDATE || d.ndim != 2 || d.weights != MOLT_W_LINEAR)
+      return false;
+    for (int ax = 0; ax < 2; ++ax)
+      if (!shape_ok(p.n[ax], 16) && !shape_ok(p.n[ax], 8) && !shape_ok(p.n[ax], 4)) return false;
+  }
+  return true;
+}
+
+// Fills the device tables for the selected problems and returns the params.
+molt_status batch_build(molt_ctx* c, void* const* u, const std::vector<int>& sel, int phase_mask, int stages,
+                        BatchParams* out, size_t* smem) {
+  BatchState& B = c->batch;
+  std::vector<BatchSweep> hs;
+  std::vector<BatchUpdate> hu;
+  int items[2] = {0, 0};
+  long long chunks = 0;
+  size_t sm = 0;
+  for (int i : sel) {
+    Problem& p = c->probs[i];
+    const double alpha = step_alpha(p);
+    for (int ax = 0; ax < 2; ++ax) {
+      Plan pl;
+      molt_status st = plan_axis(c, p, ax, MODE_0, p.d.P, alpha, &pl, B.E[ax][i]);
+      if (st != MOLT_OK) return st;
+      if (pl.block != 512) return fail(c, MOLT_EUNSUPPORTED, "batch tile does not fill 512 threads");
+      pl.a.in = p.shadow;
+      pl.a.acc = p.acc;
+      pl.a.status = c->status_dev;
+      BatchSweep bs;
+      bs.a = pl.a;
+      bs.E = B.E[ax][i];
+      bs.first_item = items[ax];
+      bs.ntiles = int((pl.a.g.nlines + pl.a.W - 1) / pl.a.W);
+      items[ax] += bs.ntiles;
+      hs.push_back(bs);
+      if (pl.smem > sm) sm = pl.smem;
+    }
+    BatchUpdate bu;
+    bu.acc = static_cast<const float*>(p.acc);
+    bu.u = static_cast<double*>(u ? u[i] : nullptr);
+    bu.st1 = static_cast<double*>(p.stage1);
+    bu.st2 = static_cast<double*>(p.stage2);
+    bu.copy = p.shadow;
+    bu.total = p.total;
+    bu.first_chunk = chunks;
+    chunks += (p.total + kChunk - 1) / kChunk;
+    hu.push_back(bu);
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(B.d_sweeps, hs.data(), hs.size() * sizeof(BatchSweep), cudaMemcpyHostToDevice,
+                           c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(B.d_updates, hu.data(), hu.size() * sizeof(BatchUpdate), cudaMemcpyHostToDevice,
+                           c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "batch tables");
+  BatchParams prm{};
+  prm.nprob = int(sel.size());
+  prm.sweeps = B.d_sweeps;
+  prm.items[0] = items[0];
+  prm.items[1] = items[1];
+  prm.updates = B.d_updates;
+  prm.chunks = chunks;
+  prm.coefS = -c->probs[sel[0]].d.beta * c->probs[sel[0]].d.beta;
+  prm.stages = stages;
+  prm.phase_mask = phase_mask;
+  prm.bar_count = B.d_bar;
+  prm.bar_gen = B.d_bar + 1;
+  prm.status = c->status_dev;
+  prm.wait_limit = c->wait_limit;
+  prm.skip_arrive = c->test_skip_arrive ? 1 : 0;
+  *out = prm;
+  *smem = sm;
+  return MOLT_OK;
+}
+
+// Cooperative launch: every CTA is resident, so the grid barriers complete.
+molt_status batch_launch(molt_ctx* c, const BatchParams& prm, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(batch_heat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch attribute");
+  int per_sm = 0, dev = 0, sms = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_heat_kernel, 512, smem)) != cudaSuccess)
+    return cuda_fail(c, e, "batch occupancy");
+  if (per_sm < 1) return fail(c, MOLT_EUNSUPPORTED, "batch kernel does not fit on an SM");
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if ((e = cudaMemsetAsync(c->batch.d_bar, 0, 2 * sizeof(unsigned int), c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "batch barrier reset");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(sms * per_sm));
+  cfg.blockDim = dim3(512);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  molt_ctx::Rec rec;
+  record_begin(c, &rec, MOLT_KERNEL_BATCH);
+  e = cudaLaunchKernelEx(&cfg, batch_heat_kernel, prm);
+  record_end(c, &rec);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch launch");
+  return MOLT_OK;
+}
+
+// Autotuner: for every size class and axis, time each admissible tile shape
+// (points per lane E in {16, 8, 4}) on that class's sweeps and keep the fastest.
+molt_status batch_tune(molt_ctx* c) {
+  BatchState& B = c->batch;
+  const int np = int(c->probs.size());
+  for (int ax = 0; ax < 2; ++ax) {
+    std::vector<int64_t> sizes;
+    for (int i = 0; i < np; ++i) {
+      const int64_t n = c->probs[i].n[ax];
+      if (std::find(sizes.begin(), sizes.end(), n) == sizes.end()) sizes.push_back(n);
+    }
+    for (int64_t n : sizes) {
+      std::vector<int> sel;
+      for (int i = 0; i < np; ++i)
+        if (c->probs[i].n[ax] == n) sel.push_back(i);
+      std::vector<int> cands;
+      for (int E : {16, 8, 4})
+        if (shape_ok(n, E)) cands.push_back(E);
+      int best = cands[0];
+      if (cands.size() > 1) {
+        float best_ms = 1e30f;
+        cudaEvent_t t0, t1;
+        cudaEventCreate(&t0);
+        cudaEventCreate(&t1);
+        for (int E : cands) {
+          for (int i : sel) B.E[ax][i] = E;
+          BatchParams prm;
+          size_t smem;
+          molt_status st = batch_build(c, nullptr, sel, 1 << ax, 1, &prm, &smem);
+          if (st != MOLT_OK) return st;
+          if ((st = batch_launch(c, prm, smem)) != MOLT_OK) return st;
+          cudaEventRecord(t0, c->stream);
+          for (int r = 0; r < 3; ++r)
+            if ((st = batch_launch(c, prm, smem)) != MOLT_OK) return st;
+          cudaEventRecord(t1, c->stream);
+          cudaEventSynchronize(t1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, t0, t1);
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = E;
+          }
+        }
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+      }
+      for (int i : sel) B.E[ax][i] = best;
+    }
+  }
+  B.tuned = true;
+  return MOLT_OK;
+}
+
+molt_status batch_prepare(molt_ctx* c) {
+  BatchState& B = c->batch;
+  if (B.checked) return MOLT_OK;
+  B.checked = true;
+  B.supported = batch_supported(c);
+  if (!B.supported) return MOLT_OK;
+  const int np = int(c->probs.size());
+  for (int ax = 0; ax < 2; ++ax) {
+    B.E[ax].resize(np);
+    for (int i = 0; i < np; ++i) {
+      const int64_t n = c->probs[i].n[ax];
+      B.E[ax][i] = shape_ok(n, 16) ? 16 : (shape_ok(n, 8) ? 8 : 4);
+    }
+  }
+  if (cudaMalloc(&B.d_sweeps, sizeof(BatchSweep) * 2 * np) != cudaSuccess ||
+      cudaMalloc(&B.d_updates, sizeof(BatchUpdate) * np) != cudaSuccess ||
+      cudaMalloc(&B.d_bar, 2 * sizeof(unsigned int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, MOLT_ENOMEM, "batch tables");
+  }
+  return MOLT_OK;
+}
+
+// One graph-captured persistent launch per time step.
+molt_status batch_steps(molt_ctx* c, void* const* u, int nsteps) {
+  BatchState& B = c->batch;
+  const int np = int(c->probs.size());
+  molt_status st;
+  if (!B.tuned && (st = batch_tune(c)) != MOLT_OK) return st;
+  std::vector<void*> cur(u, u + np);
+  if (cur != B.last_u || (!B.graph && !B.graph_failed)) {
+    if (B.graph) {
+      cudaGraphExecDestroy(B.graph);
+      B.graph = nullptr;
+    }
+    std::vector<int> all(np);
+    for (int i = 0; i < np; ++i) all[i] = i;
+    if ((st = batch_build(c, u, all, 7, 3, &B.params, &B.smem)) != MOLT_OK) return st;
+    B.last_u = cur;
+    B.graph_failed = true;
+    if (c->stream && !c->profile) {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const molt_status lst = batch_launch(c, B.params, B.smem);
+        const cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+        if (lst == MOLT_OK && ce == cudaSuccess && g &&
+            cudaGraphInstantiate(&B.graph, g, 0) == cudaSuccess)
+          B.graph_failed = false;
+        if (g) cudaGraphDestroy(g);
+      }
+      cudaGetLastError();
+    }
+  }
+  for (int k = 0; k < nsteps; ++k) {
+    if (B.graph) {
+      molt_ctx::Rec rec;
+      record_begin(c, &rec, MOLT_KERNEL_BATCH);
+      cudaError_t e = cudaGraphLaunch(B.graph, c->stream);
+      record_end(c, &rec);
+      if (e != cudaSuccess) return cuda_fail(c, e, "batch graph launch");
+    } else if ((st = batch_launch(c, B.params, B.smem)) != MOLT_OK) {
+      return st;
+    }
+  }
+  return MOLT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -608,7 +952,13 @@ molt_status molt_step(molt_ctx* c, void* const* u, void* const* u_prev, int nste
     molt_status st = refresh_shadow(c, c->probs[i], u[i]);
     if (st != MOLT_OK) return st;
   }
-  for (int k = 0; k < nsteps; ++k) {
+  molt_status bst = batch_prepare(c);
+  if (bst != MOLT_OK) return bst;
+  if (c->batch.supported && nsteps > 0) {
+    if ((bst = batch_steps(c, u, nsteps)) != MOLT_OK) return bst;
+    for (int i = 0; i < np; ++i) t_inout[i] += nsteps * c->probs[i].d.dt;
+  }
+  for (int k = 0; k < (c->batch.supported ? 0 : nsteps); ++k) {
     for (int i = 0; i < np; ++i) {
       Problem& p = c->probs[i];
       molt_status st = MOLT_OK;
@@ -652,10 +1002,32 @@ molt_status molt_step(molt_ctx* c, void* const* u, void* const* u_prev, int nste
 
 molt_status molt_set_option(molt_ctx* c, int option, int64_t value) {
   if (!c) return fail(nullptr, MOLT_EINVAL, "null context");
-  if (value != 0 && value != 1) return fail(c, MOLT_EINVAL, "option value must be 0 or 1");
-  if (option == MOLT_OPT_TMA) c->no_tma = value == 0;
-  else if (option == MOLT_OPT_PROFILE) c->profile = value == 1;
-  else return fail(c, MOLT_EINVAL, "unknown option");
+  if (option == MOLT_OPT_WAIT_LIMIT) {
+    if (value < 1000) return fail(c, MOLT_EINVAL, "wait limit below 1000 cycles");
+    c->wait_limit = value;
+  } else {
+    if (value != 0 && value != 1) return fail(c, MOLT_EINVAL, "option value must be 0 or 1");
+    if (option == MOLT_OPT_TMA) c->no_tma = value == 0;
+    else if (option == MOLT_OPT_PROFILE) c->profile = value == 1;
+    else if (option == MOLT_OPT_TEST_SKIP_ARRIVE) c->test_skip_arrive = value == 1;
+    else return fail(c, MOLT_EINVAL, "unknown option");
+  }
+  // baked into the captured batch step: rebuild it on the next step
+  c->batch.last_u.clear();
+  return MOLT_OK;
+}
+
+molt_status molt_batch_tile_shape(molt_ctx* c, int problem, int axis, int* points_per_lane, int* warps_per_line,
+                                  int* lines_per_tile) {
+  if (!c) return fail(nullptr, MOLT_EINVAL, "null context");
+  if (problem < 0 || problem >= int(c->probs.size()) || axis < 0 || axis > 1)
+    return fail(c, MOLT_EINVAL, "problem or axis out of range");
+  if (!c->batch.supported || !c->batch.tuned) return fail(c, MOLT_EUNSUPPORTED, "no tuned batch step yet");
+  const int E = c->batch.E[axis][problem];
+  const int nwl = int(c->probs[problem].n[axis] / (32 * E));
+  if (points_per_lane) *points_per_lane = E;
+  if (warps_per_line) *warps_per_line = nwl;
+  if (lines_per_tile) *lines_per_tile = 16 / nwl;
   return MOLT_OK;
 }
 
@@ -698,6 +1070,10 @@ molt_status molt_destroy(molt_ctx* c) {
     cudaFree(p.hx);
     cudaFree(p.shadow);
   }
+  if (c->batch.graph) cudaGraphExecDestroy(c->batch.graph);
+  cudaFree(c->batch.d_sweeps);
+  cudaFree(c->batch.d_updates);
+  cudaFree(c->batch.d_bar);
   cudaFree(c->status_dev);
   cudaFree(c->speed_dev);
   cudaFree(c->t_dev);

@@ -43,6 +43,10 @@ constexpr int kG = 16;   // ghost slots per side in shared memory (3 used)
 #define MOLT_MAX_THREADS 512
 #endif
 constexpr int kMaxThreads = MOLT_MAX_THREADS;
+#ifndef MOLT_MIN_BLOCKS
+#define MOLT_MIN_BLOCKS 1
+#endif
+constexpr int kMinBlocks = MOLT_MIN_BLOCKS;   // resident CTAs per SM the register budget targets
 
 enum Epi {
   EPI_STORE = 0,       // out = S
@@ -103,15 +107,22 @@ struct SweepArgs {
   int* status;
 };
 
-__device__ __forceinline__ int phys(int e) {
-  const int ee = e + kG;
-  return ee + (ee >> 4);
+// Shared-memory index of point e of a line whose lanes own E points each: one
+// pad word after every E words (kG is a multiple of E), so lane chunks start
+// (E+1) words apart -- an odd stride, hence bank-conflict free.
+template <int E>
+__host__ __device__ constexpr int log2i() { return E == 16 ? 4 : (E == 8 ? 3 : (E == 4 ? 2 : -1)); }
+
+template <int E = kE>
+__host__ __device__ constexpr int phys(int e) {
+  static_assert(log2i<E>() > 0, "points per lane must be 4, 8 or 16");
+  return (e + kG) + ((e + kG) >> log2i<E>());
 }
 
-// For a lane chunk starting at e0 = kE*t (kE = 16): phys(e0 + j) =
-// 17*t + chunk_off(j), with chunk_off a compile-time constant for unrolled j.
-__host__ __device__ constexpr int chunk_off(int j) { return (j + kG) + ((j + kG) >> 4); }
-static_assert(kE == 16, "chunk_off assumes 16 points per lane");
+// For a lane chunk starting at e0 = E*t: phys(e0 + j) = (E+1)*t +
+// chunk_off<E>(j), a compile-time constant for unrolled j.
+template <int E = kE>
+__host__ __device__ constexpr int chunk_off(int j) { return (j + kG) + ((j + kG) >> log2i<E>()); }
 
 // Base offset of line l (32-bit division: the host keeps nlines < 2^31; a
 // 64-bit division would run on the FP64 pipe).
@@ -157,6 +168,13 @@ __device__ __forceinline__ T pick(double d, float f) {
 // Non-finite test on the exponent bits (no floating-point instruction).
 __device__ __forceinline__ bool nonfinite(double x) { return (__double2hiint(x) & 0x7FF00000) == 0x7FF00000; }
 __device__ __forceinline__ bool nonfinite(float x) { return (__float_as_uint(x) & 0x7F800000u) == 0x7F800000u; }
+
+// Global load; CG = true reads through L2 only (data written earlier in the
+// same kernel by other CTAs must not come from a stale L1 line).
+template <bool CG, typename V>
+__device__ __forceinline__ V gload(const V* p) {
+  if constexpr (CG) return __ldcg(p); else return *p;
+}
 
 template <typename TO, typename FROM>
 __device__ __forceinline__ TO cvt(FROM x) {
@@ -233,7 +251,7 @@ __device__ __forceinline__ T wenoz_integral(const T* w, const T (&sub)[3][3], co
 // Contiguous lines: the nwl warps of line lw read it with consecutive lanes.
 // Strided lines: thread (p, w) with w fastest, so a warp reads whole rows of
 // W neighbouring lines.
-template <typename T, typename TIN>
+template <typename T, typename TIN, int E = kE, bool CG = false>
 __device__ __forceinline__ void load_tile(const SweepArgs& a, const TIN* in, T* lines, long long line0,
                                           int lw, int tl) {
   const int W = a.W, n = a.g.n;
@@ -244,9 +262,9 @@ __device__ __forceinline__ void load_tile(const SweepArgs& a, const TIN* in, T* 
     T* dstl = lines + lw * a.LS;
     const int step = a.nwl * 32;
 #pragma unroll 4
-    for (int p = tl; p < n; p += step) dstl[phys(p)] = cvt<T>(src[p]);
+    for (int p = tl; p < n; p += step) dstl[phys<E>(p)] = cvt<T>(gload<CG>(src + p));
   } else {
-    // prow = blockDim/W is a multiple of 16, so phys() advances by a constant
+    // prow = blockDim/W is a multiple of 16, so phys<E>() advances by a constant
     const int w = threadIdx.x % W;
     const int prow = blockDim.x / W;
     const long long gl = line0 + w;
@@ -255,18 +273,18 @@ __device__ __forceinline__ void load_tile(const SweepArgs& a, const TIN* in, T* 
     int p = threadIdx.x / W;
     const TIN* src = in + line_base(a.g, gl) + p * st;
     const long long sstep = prow * st;
-    T* dst = lines + w * a.LS + phys(p);
-    const int dstep = prow + (prow >> 4);
+    T* dst = lines + w * a.LS + phys<E>(p);
+    const int dstep = prow + prow / E;
 #pragma unroll 8
     for (; p < n; p += prow) {
-      *dst = cvt<T>(*src);
+      *dst = cvt<T>(gload<CG>(src));
       src += sstep;
       dst += dstep;
     }
   }
 }
 
-template <typename T>
+template <typename T, int E = kE>
 __device__ __forceinline__ void fill_ghosts(const SweepArgs& a, T* lines) {
   const int n = a.g.n;
   for (int t = threadIdx.x; t < a.W * 6; t += blockDim.x) {
@@ -278,22 +296,22 @@ __device__ __forceinline__ void fill_ghosts(const SweepArgs& a, T* lines) {
       if (a.bc == 0) {
         int s = (-j) % n;
         if (s < 0) s += n;
-        val = b[phys(s)];
+        val = b[phys<E>(s)];
       } else {
         const int m = j < n - 1 ? j : n - 1;
-        val = T(2) * b[phys(0)] - b[phys(m)];
+        val = T(2) * b[phys<E>(0)] - b[phys<E>(m)];
       }
-      b[phys(-j)] = val;
+      b[phys<E>(-j)] = val;
     } else {
       const int j = g - 2;  // ghost e = n-1+j
       T val;
       if (a.bc == 0) {
-        val = b[phys((n - 1 + j) % n)];
+        val = b[phys<E>((n - 1 + j) % n)];
       } else {
         const int m = n - 1 - j > 0 ? n - 1 - j : 0;
-        val = T(2) * b[phys(n - 1)] - b[phys(m)];
+        val = T(2) * b[phys<E>(n - 1)] - b[phys<E>(m)];
       }
-      b[phys(n - 1 + j)] = val;
+      b[phys<E>(n - 1 + j)] = val;
     }
   }
 }
@@ -377,7 +395,7 @@ struct Acc2 {
 // Dirichlet L_0 -> 2A and 2B from the 2x2 system with determinant 1-mu^2;
 // Dirichlet L_R / L_L -> v(a) / v(b).  Exact-fit kernels divide Dirichlet
 // values by q (their end nodes keep the map (q, 0)).
-template <typename T, bool RAGGED>
+template <typename T, bool RAGGED, int E = kE>
 __device__ __forceinline__ void boundary_carries(const SweepArgs& a, const T* bw, int n, T tbR, T tbL, double* CR,
                                                  double* CL) {
   const double IRb = cvt<double>(tbR);
@@ -387,7 +405,7 @@ __device__ __forceinline__ void boundary_carries(const SweepArgs& a, const T* bw
     *CL = ILa * a.inv1mmu;
     return;
   }
-  const double v0 = cvt<double>(bw[phys(0)]), vN = cvt<double>(bw[phys(n - 1)]);
+  const double v0 = cvt<double>(bw[phys<E>(0)]), vN = cvt<double>(bw[phys<E>(n - 1)]);
   double cr, cl;
   if (a.mode == MODE_0) {
     const double r0 = fma(-0.5, ILa, v0), r1 = fma(-0.5, IRb, vN);
@@ -414,7 +432,7 @@ __device__ __forceinline__ void split_carry(double c, T* hi, T* lo) {
 }
 
 // Ghost cells of one line by the lanes of the warp that owns it.
-template <typename T>
+template <typename T, int E = kE>
 __device__ __forceinline__ void warp_fill_ghosts(const SweepArgs& a, T* b, int lane) {
   const int n = a.g.n;
   if (lane < 3) {
@@ -423,22 +441,22 @@ __device__ __forceinline__ void warp_fill_ghosts(const SweepArgs& a, T* b, int l
     if (a.bc == 0) {
       int s = (-j) % n;
       if (s < 0) s += n;
-      val = b[phys(s)];
+      val = b[phys<E>(s)];
     } else {
       const int m = j < n - 1 ? j : n - 1;
-      val = T(2) * b[phys(0)] - b[phys(m)];
+      val = T(2) * b[phys<E>(0)] - b[phys<E>(m)];
     }
-    b[phys(-j)] = val;
+    b[phys<E>(-j)] = val;
   } else if (lane < 6) {
     const int j = lane - 2;  // ghost e = n-1+j
     T val;
     if (a.bc == 0) {
-      val = b[phys((n - 1 + j) % n)];
+      val = b[phys<E>((n - 1 + j) % n)];
     } else {
       const int m = n - 1 - j > 0 ? n - 1 - j : 0;
-      val = T(2) * b[phys(n - 1)] - b[phys(m)];
+      val = T(2) * b[phys<E>(n - 1)] - b[phys<E>(m)];
     }
-    b[phys(n - 1 + j)] = val;
+    b[phys<E>(n - 1 + j)] = val;
   }
 }
 
@@ -446,7 +464,7 @@ __device__ __forceinline__ void warp_fill_ghosts(const SweepArgs& a, T* b, int l
 // application needs no CTA-wide barrier: ghosts, line totals and the FP64
 // boundary solve stay inside the warp (the solve runs on lane 0 and its
 // result is broadcast by shuffles).
-template <typename T, bool WENO, bool RAGGED, bool WL>
+template <typename T, bool WENO, bool RAGGED, bool WL, int E = kE>
 __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSmem& sm, bool line_ok) {
   const int nwl = a.nwl, n = a.g.n;
   double* carries = sm.carries;
@@ -456,8 +474,9 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
   const int lw = warp / nwl, part = warp - lw * nwl;
   const int tl = part * 32 + lane;
   T* buf = lines + lw * a.LS;
-  const int e0 = tl * kE;
-  T* cbase = buf + 17 * tl;   // phys(e0 + j) = 17*tl + chunk_off(j)
+  const int e0 = tl * E;
+  T* cbase = buf + (E + 1) * tl;   // phys<E>(e0 + j) = (E+1)*tl + chunk_off<E>(j)
+  static_assert(phys<E>(E * 3 + 2) == (E + 1) * 3 + chunk_off<E>(2), "lane base / chunk offset mismatch");
 
   const T q = pick<T>(a.q, a.qf);
   const T qE = pick<T>(a.qE, a.qEf);
@@ -474,42 +493,42 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
     }
   }
   if constexpr (WL) {
-    warp_fill_ghosts(a, buf, lane);
+    warp_fill_ghosts<T, E>(a, buf, lane);
     __syncwarp();
   } else {
-    fill_ghosts(a, lines);
+    fill_ghosts<T, E>(a, lines);
     __syncthreads();
   }
 
   // element maps: (q, J) for points with a local integral, identity for
   // points past the end of the line and for the Dirichlet end nodes where the
   // recurrences start (I_R(x_0) = 0, I_L(x_N) = 0).  RAGGED kernels mask per
-  // point.  Exact-fit kernels (n = nwl*32*kE) have no points past the end;
+  // point.  Exact-fit kernels (n = nwl*32*E) have no points past the end;
   // their Dirichlet end nodes keep the map (q, 0) and the line's initial
   // value is divided by q, which yields the same values (x_0: q*(C/q) + 0 = C).
   const int eR0 = (a.bc == 1) ? 1 : 0;          // first R point with a J
   const int eL1 = (a.bc == 1) ? n - 2 : n - 1;  // last L point with a J
   const bool zeroR0 = !RAGGED && a.bc == 1 && e0 == 0;
-  const bool zeroLN = !RAGGED && a.bc == 1 && e0 + kE == n;
+  const bool zeroLN = !RAGGED && a.bc == 1 && e0 + E == n;
 
-  // J_R(e0+k) and J_L(e0+kE-1-k) share the pair Y[k] so that the R chain
+  // J_R(e0+k) and J_L(e0+E-1-k) share the pair Y[k] so that the R chain
   // (ascending) and the L chain (descending) of the recurrences advance
   // together in packed FP32x2 instructions.
   using T2 = typename Pair<T>::type;
-  T v[kE], S[kE];
-  T2 Y[kE];
+  T v[E], S[E];
+  T2 Y[E];
 #pragma unroll
-  for (int k = 0; k < kE; ++k) S[k] = T(0);
+  for (int k = 0; k < E; ++k) S[k] = T(0);
   T rmax = T(0);
 
   for (int p = 0; p < a.P; ++p) {
-    // ---- 1. local integrals from a window of kE + 6 points
+    // ---- 1. local integrals from a window of E + 6 points
     {
-      T win[kE + 6];
+      T win[E + 6];
 #pragma unroll
-      for (int k = 0; k < kE + 6; ++k) win[k] = cbase[chunk_off(k - 3)];
+      for (int k = 0; k < E + 6; ++k) win[k] = cbase[chunk_off<E>(k - 3)];
 #pragma unroll
-      for (int k = 0; k < kE; ++k) {
+      for (int k = 0; k < E; ++k) {
         v[k] = win[k + 3];
         if constexpr (WENO) {
           T wr[5], wl[5];
@@ -519,7 +538,7 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
             wl[j] = win[k + 6 - j];    // mirrored: v_{e+3} .. v_{e-1}
           }
           Y[k].x = wenoz_integral<T>(wr, sub, dw);
-          Y[kE - 1 - (k)].y = wenoz_integral<T>(wl, sub, dw);
+          Y[E - 1 - (k)].y = wenoz_integral<T>(wl, sub, dw);
         } else {
           T r = T(0), l = T(0);
 #pragma unroll
@@ -528,19 +547,19 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
             l = fma(c[j], win[k + 6 - j], l);   // v_{e - (j-3)}
           }
           Y[k].x = r;
-          Y[kE - 1 - (k)].y = l;
+          Y[E - 1 - (k)].y = l;
         }
       }
     }
     if (zeroR0) Y[0].x = T(0);
-    if (zeroLN) Y[kE - 1 - (kE - 1)].y = T(0);
+    if (zeroLN) Y[E - 1 - (E - 1)].y = T(0);
     // ---- 2a. lane folds (R ascending, L descending, interleaved)
     T aR, aL, bR, bL;
     if constexpr (!RAGGED) {
       const T2 q2 = pair2<T>(q, q);
       T2 y = pair2<T>(T(0), T(0));
 #pragma unroll
-      for (int k = 0; k < kE; ++k) y = fma2(q2, y, Y[k]);
+      for (int k = 0; k < E; ++k) y = fma2(q2, y, Y[k]);
       aR = qE;
       aL = qE;
       bR = y.x;
@@ -550,11 +569,11 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
       aR = T(1);
       aL = T(1);
 #pragma unroll
-      for (int k = 0; k < kE; ++k) {
+      for (int k = 0; k < E; ++k) {
         const int e = e0 + k;
         if (e >= eR0 && e < n) { r = fma(q, r, Y[k].x); aR *= q; }
-        const int eL = e0 + kE - 1 - k;
-        if (eL <= eL1) { l = fma(q, l, Y[kE - 1 - (kE - 1 - k)].y); aL *= q; }
+        const int eL = e0 + E - 1 - k;
+        if (eL <= eL1) { l = fma(q, l, Y[E - 1 - (E - 1 - k)].y); aL *= q; }
       }
       bR = r;
       bL = l;
@@ -598,7 +617,7 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
       T c4[4] = {T(0), T(0), T(0), T(0)};
       if (lane == 0) {
         double CR, CL;
-        boundary_carries<T, RAGGED>(a, buf, n, tbR, tbL, &CR, &CL);
+        boundary_carries<T, RAGGED, E>(a, buf, n, tbR, tbL, &CR, &CL);
         split_carry<T>(CR, &c4[0], &c4[1]);
         split_carry<T>(CL, &c4[2], &c4[3]);
       }
@@ -615,7 +634,7 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
         for (int j = 0; j < nwl; ++j) tbR = fma(tw[j * 4 + 0], tbR, tw[j * 4 + 1]);
         for (int j = nwl - 1; j >= 0; --j) tbL = fma(tw[j * 4 + 2], tbL, tw[j * 4 + 3]);
         double CR, CL;
-        boundary_carries<T, RAGGED>(a, lines + lane * a.LS, n, tbR, tbL, &CR, &CL);
+        boundary_carries<T, RAGGED, E>(a, lines + lane * a.LS, n, tbR, tbL, &CR, &CL);
         T* cw = reinterpret_cast<T*>(carries) + lane * 4;
         split_carry<T>(CR, &cw[0], &cw[1]);
         split_carry<T>(CL, &cw[2], &cw[3]);
@@ -635,7 +654,7 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
         const T2 q2 = pair2<T>(q, q);
         Acc2<T> y{pair2<T>(fma(laR, cRh, lbR), fma(laL, cLh, lbL)), pair2<T>(laR * cRl, laL * cLl)};
 #pragma unroll
-        for (int k = 0; k < kE; ++k) {
+        for (int k = 0; k < E; ++k) {
           y.step(q2, Y[k]);
           Y[k] = y.value();
         }
@@ -643,13 +662,13 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
         Acc<T> yR{fma(laR, cRh, lbR), laR * cRl};
         Acc<T> yL{fma(laL, cLh, lbL), laL * cLl};
 #pragma unroll
-        for (int k = 0; k < kE; ++k) {
+        for (int k = 0; k < E; ++k) {
           const int e = e0 + k;
           if (e >= eR0 && e < n) yR.step(q, Y[k].x);
           Y[k].x = yR.value();
-          const int kl = kE - 1 - k;
-          if (e0 + kl <= eL1) yL.step(q, Y[kE - 1 - (kl)].y);
-          Y[kE - 1 - (kl)].y = yL.value();
+          const int kl = E - 1 - k;
+          if (e0 + kl <= eL1) yL.step(q, Y[E - 1 - (kl)].y);
+          Y[E - 1 - (kl)].y = yL.value();
         }
       }
     }
@@ -659,9 +678,9 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
       // per-axis part of the Lax-Friedrichs Hamiltonian (Sec. 2.5)
       const T al = pick<T>(a.alpha, a.alphaf);
 #pragma unroll
-      for (int k = 0; k < kE; ++k) {
+      for (int k = 0; k < E; ++k) {
         const T vm = al * (v[k] - Y[k].x);
-        const T vp = -al * (v[k] - Y[kE - 1 - (k)].y);
+        const T vp = -al * (v[k] - Y[E - 1 - (k)].y);
         const T r = fmax(fabs(vm), fabs(vp));
         const T mean = T(0.5) * (vm + vp);
         S[k] = T(0.5) * mean * mean + r * T(0.5) * (vm - vp);
@@ -669,11 +688,11 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < kE; ++k) {
+      for (int k = 0; k < E; ++k) {
         T linv;
-        if (a.mode == MODE_0) linv = T(0.5) * (Y[k].x + Y[kE - 1 - (k)].y);
+        if (a.mode == MODE_0) linv = T(0.5) * (Y[k].x + Y[E - 1 - (k)].y);
         else if (a.mode == MODE_R) linv = Y[k].x;
-        else linv = Y[kE - 1 - (k)].y;
+        else linv = Y[E - 1 - (k)].y;
         v[k] = v[k] - linv;
         S[k] += v[k];
       }
@@ -682,18 +701,18 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
       if constexpr (WL) {
         __syncwarp();
 #pragma unroll
-        for (int k = 0; k < kE; ++k)
-          if (RAGGED ? e0 + k < n : true) cbase[chunk_off(k)] = v[k];
+        for (int k = 0; k < E; ++k)
+          if (RAGGED ? e0 + k < n : true) cbase[chunk_off<E>(k)] = v[k];
         __syncwarp();
-        warp_fill_ghosts(a, buf, lane);
+        warp_fill_ghosts<T, E>(a, buf, lane);
         __syncwarp();
       } else {
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < kE; ++k)
-          if (RAGGED ? e0 + k < n : true) cbase[chunk_off(k)] = v[k];
+        for (int k = 0; k < E; ++k)
+          if (RAGGED ? e0 + k < n : true) cbase[chunk_off<E>(k)] = v[k];
         __syncthreads();
-        fill_ghosts(a, lines);
+        fill_ghosts<T, E>(a, lines);
         __syncthreads();
       }
     }
@@ -701,8 +720,8 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
 
   if constexpr (WL) __syncwarp(); else __syncthreads();
 #pragma unroll
-  for (int k = 0; k < kE; ++k)
-    if (RAGGED ? e0 + k < n : true) cbase[chunk_off(k)] = S[k];
+  for (int k = 0; k < E; ++k)
+    if (RAGGED ? e0 + k < n : true) cbase[chunk_off<E>(k)] = S[k];
   __syncthreads();
   return cvt<double>(rmax);
 }
@@ -710,15 +729,15 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
 #ifndef MOLT_WL_MODE
 #define MOLT_WL_MODE 0
 #endif
-template <typename T, bool WENO, bool RAGGED>
+template <typename T, bool WENO, bool RAGGED, int E = kE>
 __device__ __forceinline__ double compute_lines_any(const SweepArgs& a, const TileSmem& sm, bool line_ok) {
 #if MOLT_WL_MODE == 0
-  return compute_lines<T, WENO, RAGGED, false>(a, sm, line_ok);
+  return compute_lines<T, WENO, RAGGED, false, E>(a, sm, line_ok);
 #elif MOLT_WL_MODE == 2
-  return compute_lines<T, WENO, RAGGED, true>(a, sm, line_ok);
+  return compute_lines<T, WENO, RAGGED, true, E>(a, sm, line_ok);
 #else
-  if (a.nwl == 1) return compute_lines<T, WENO, RAGGED, true>(a, sm, line_ok);
-  return compute_lines<T, WENO, RAGGED, false>(a, sm, line_ok);
+  if (a.nwl == 1) return compute_lines<T, WENO, RAGGED, true, E>(a, sm, line_ok);
+  return compute_lines<T, WENO, RAGGED, false, E>(a, sm, line_ok);
 #endif
 }
 
@@ -731,7 +750,7 @@ struct EpiOps {
   TST x, y;
 };
 
-template <typename T, typename TST, int EPI>
+template <typename T, typename TST, int EPI, bool CG = false>
 struct Epilogue {
   const SweepArgs& a;
   double dt;
@@ -739,14 +758,14 @@ struct Epilogue {
   __device__ __forceinline__ EpiOps<T, TST> load(long long gidx) const {
     EpiOps<T, TST> o{T(0), TST(0), TST(0)};
     if constexpr (EPI == EPI_ACC_ADD) {
-      o.acc = static_cast<const T*>(a.acc)[gidx];
+      o.acc = gload<CG>(static_cast<const T*>(a.acc) + gidx);
     } else if constexpr (EPI == EPI_HEAT_FINAL || EPI == EPI_WAVE_FINAL) {
-      if (a.acc) o.acc = static_cast<const T*>(a.acc)[gidx];
-      o.x = static_cast<const TST*>(a.un)[gidx];
-      if (EPI == EPI_HEAT_FINAL || !a.from_rest) o.y = static_cast<const TST*>(a.us)[gidx];
+      if (a.acc) o.acc = gload<CG>(static_cast<const T*>(a.acc) + gidx);
+      o.x = gload<CG>(static_cast<const TST*>(a.un) + gidx);
+      if (EPI == EPI_HEAT_FINAL || !a.from_rest) o.y = gload<CG>(static_cast<const TST*>(a.us) + gidx);
     } else if constexpr (EPI == EPI_HJ_Y) {
-      o.x = static_cast<const TST*>(a.un)[gidx];
-      if (a.out) o.y = static_cast<const TST*>(a.out)[gidx];
+      o.x = gload<CG>(static_cast<const TST*>(a.un) + gidx);
+      if (a.out) o.y = gload<CG>(static_cast<const TST*>(a.out) + gidx);
     }
     return o;
   }
@@ -787,9 +806,9 @@ struct Epilogue {
 // issued before its stores.
 constexpr int kEpiBatch = 8;
 
-template <typename T, typename TST, int EPI>
+template <typename T, typename TST, int EPI, int E = kE, bool CG = false>
 __device__ __forceinline__ void epilogue_tile(const SweepArgs& a, const T* lines, long long line0, double dt) {
-  const Epilogue<T, TST, EPI> ep{a, dt};
+  const Epilogue<T, TST, EPI, CG> ep{a, dt};
   const int W = a.W, n = a.g.n, nwl = a.nwl;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   long long g0;
@@ -817,10 +836,10 @@ __device__ __forceinline__ void epilogue_tile(const SweepArgs& a, const T* lines
     sstep = 1;
   }
   // shared index of point p: contiguous lines step p by a multiple of 32,
-  // strided lines by blockDim/W (a multiple of 16), so phys() advances by a
+  // strided lines by blockDim/W (a multiple of 16), so phys<E>() advances by a
   // constant in both cases
-  const int pdelta = pstep + (pstep >> 4);
-  const T* sp = src0 + phys(p0);
+  const int pdelta = pstep + pstep / E;
+  const T* sp = src0 + phys<E>(p0);
   long long g = g0;
   for (int pb = p0; pb < n; pb += kEpiBatch * pstep) {
     EpiOps<T, TST> ops[kEpiBatch];
@@ -864,7 +883,7 @@ __device__ __forceinline__ void publish_speed(const SweepArgs& a, double rmax) {
 
 // One tile per CTA, plain coalesced loads (any size / alignment).
 template <typename T, typename TIN, typename TST, bool WENO, int EPI, bool RAGGED>
-__global__ void __launch_bounds__(kMaxThreads, 1) sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(kMaxThreads, kMinBlocks) sweep_kernel(const SweepArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   size_t used;
   const TileSmem sm = carve<T>(smem_raw, a, &used);

@@ -160,7 +160,7 @@ __device__ __forceinline__ void transpose_tile(const SweepArgs& a, const TmaGeom
     for (int b = 0; b < tg.nbox; ++b) {
       const TIN* src = stage + (b * W + lw) * tg.box_p;
       T* d = dst + phys(b * tg.box_p + tl);
-      const int dstep = step + (step >> 4);
+      const int dstep = step + step / kE;
 #pragma unroll 4
       for (int r = tl; r < tg.box_p; r += step) {
         *d = cvt<T>(src[r]);
@@ -174,7 +174,7 @@ __device__ __forceinline__ void transpose_tile(const SweepArgs& a, const TmaGeom
     int p = threadIdx.x / W;
     const TIN* src = stage + p * W + w;
     T* dst = lines + w * a.LS + phys(p);
-    const int dstep = prow + (prow >> 4);
+    const int dstep = prow + prow / kE;
 #pragma unroll 8
     for (; p < n; p += prow) {
       *dst = cvt<T>(*src);
@@ -185,7 +185,7 @@ __device__ __forceinline__ void transpose_tile(const SweepArgs& a, const TmaGeom
 }
 
 template <typename T, typename TIN, typename TST, bool WENO, int EPI>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+__global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
     sweep_tma_kernel(const SweepArgs a, const TmaGeom tg, const __grid_constant__ CUtensorMap map) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   size_t used;

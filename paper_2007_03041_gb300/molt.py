@@ -19,9 +19,10 @@ PDE_HEAT, PDE_WAVE, PDE_HJ = 0, 1, 2
 W_LINEAR, W_WENOZ, W_LEARNED = 0, 1, 2
 
 EXPORTS = ("molt_create", "molt_apply_D", "molt_step", "molt_set_option", "molt_profile_read", "molt_destroy",
-           "molt_last_error", "molt_wave_step_noalloc")
-OPT_TMA, OPT_PROFILE = 0, 1
-KERNEL_STORE, KERNEL_ACC_SET, KERNEL_ACC_ADD, KERNEL_HEAT_FINAL, KERNEL_WAVE_FINAL, KERNEL_HJ_X, KERNEL_HJ_Y = range(7)
+           "molt_last_error", "molt_wave_step_noalloc", "molt_batch_tile_shape")
+OPT_TMA, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_TEST_SKIP_ARRIVE = 0, 1, 2, 3
+(KERNEL_STORE, KERNEL_ACC_SET, KERNEL_ACC_ADD, KERNEL_HEAT_FINAL, KERNEL_WAVE_FINAL, KERNEL_HJ_X, KERNEL_HJ_Y,
+ KERNEL_UPDATE, KERNEL_BATCH) = range(9)
 
 
 class molt_desc(ctypes.Structure):
@@ -70,6 +71,9 @@ def load_library(path=LIB_PATH):
         lib.molt_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64)]
         lib.molt_destroy.argtypes = [ctypes.c_void_p]
+        lib.molt_batch_tile_shape.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int] + \
+            [ctypes.POINTER(ctypes.c_int)] * 3
+        lib.molt_batch_tile_shape.restype = ctypes.c_int
         lib.molt_wave_step_noalloc.argtypes = [ctypes.POINTER(molt_desc), ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
         lib.molt_wave_step_noalloc.restype = ctypes.c_int
@@ -176,6 +180,15 @@ def molt_wave_step_noalloc(desc, u, u_prev, u_next, from_rest, stream=None):
                                     ctypes.c_void_p(stream.cuda_stream))
     if st != MOLT_OK:
         raise MoltError(st, "molt_wave_step_noalloc")
+
+
+def molt_batch_tile_shape(ctx, problem, axis):
+    """(points per lane, warps per line, lines per tile) the batched step's
+    autotuner chose for (problem, axis)."""
+    lib = load_library()
+    v = [ctypes.c_int() for _ in range(3)]
+    _check(lib, ctx, lib.molt_batch_tile_shape(ctx, problem, axis, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def molt_destroy(ctx):
