@@ -47,9 +47,10 @@ WORKLOAD = {
 # FP32 copy
 BYTES_PER_DOF = {"x": 8, "yz": 12, "update": 32}
 LAUNCHES_PER_STEP = {"x": 1, "yz": 2, "update": 1}
-# DRAM bytes per DOF per launch from an ncu capture of the current kernels
-# (None until captured)
-TRAFFIC_PER_DOF = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per DOF per launch
+# from one ncu capture of these kernels on the 512 x 256 x 512 grid, scaled to
+# a full launch by the points processed (traffic grows with the points)
+TRAFFIC_PER_DOF = {"x": 7.31, "yz": 11.38, "update": 31.37}
 
 
 def dist_env():
