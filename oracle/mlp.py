@@ -16,7 +16,8 @@ Conventions (shared by the CUDA kernels, restated here independently):
   activations to BF16 before each matrix product and accumulate in FP32
   (``emulate_bf16=True`` reproduces those roundings, in FP64 otherwise);
 * loss = mean over stencils of sum_r (p_r - w_r)^2 against WENO-Z targets;
-* fallback: where max_r |p_r - wZ_r| > 1e-2 the WENO-Z weights are used.
+* fallback: where max_r |p_r - wZ_r| > 1e-2 (or is not finite) the WENO-Z
+  weights are used.
 
 Parameter vector (FP32 master order): W1 (32x5), b1 (32), W2 (32x32),
 b2 (32), W3 (3x32), b3 (3).
@@ -137,7 +138,43 @@ def learned_weight_fn(theta, rule, emulate_bf16=True):
         V = Wv.reshape(-1, 5)
         p, _ = forward(theta, normalise(V), emulate_bf16)
         wz = _weno_weights(rule, V)
-        bad = np.abs(p - wz).max(axis=1) > FALLBACK_TOL
+        bad = ~(np.abs(p - wz).max(axis=1) <= FALLBACK_TOL)   # non-finite outputs fall back too
         p[bad] = wz[bad]
         return p.reshape(shp + (3,))
     return fn
+
+
+def adam_step(theta, m, v, grad, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba, 2015, Algorithm 1) in FP64: the first and
+    second moment estimates, their bias corrections by 1 - beta^step, and the
+    step lr * mhat / (sqrt(vhat) + eps).  Returns (theta, m, v)."""
+    g = np.asarray(grad, dtype=np.float64)
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** step)
+    vhat = v / (1.0 - beta2 ** step)
+    return np.asarray(theta, dtype=np.float64) - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def blob_values(theta):
+    """The BF16 network blob as float64 values in its storage order: W1 (32x16,
+    inputs 5.. zero), W2 (32x32), W3 (8x32, rows 3.. zero), b1, b2, b3 (8)."""
+    P = unpack(theta)
+    W1 = np.zeros((32, 16)); W1[:, :5] = P["W1"]
+    W3 = np.zeros((8, 32)); W3[:3] = P["W3"]
+    b3 = np.zeros(8); b3[:3] = P["b3"]
+    flat = np.concatenate([W1.ravel(), P["W2"].ravel(), W3.ravel(), P["b1"], P["b2"], b3])
+    return bf16_round(flat)
+
+
+def stencils(u, pos, axis, side):
+    """5-value stencils of the periodic 2-D array u (ny, nx) at flat indices
+    pos along axis 0 (x) or 1 (y): offsets -3..1 (side 0, J_R orientation) or
+    +3..-1 (side 1, mirrored for J_L)."""
+    u = np.asarray(u)
+    ny, nx = u.shape
+    yi, xi = np.divmod(np.asarray(pos, dtype=np.int64), nx)
+    offs = np.arange(-3, 2) if side == 0 else np.arange(3, -2, -1)
+    if axis == 0:
+        return u[yi[:, None], (xi[:, None] + offs[None, :]) % nx]
+    return u[(yi[:, None] + offs[None, :]) % ny, xi[:, None]]
