@@ -302,6 +302,146 @@ def run_ours(args):
     print(json.dumps(line))
 
 
+# --------------------------------------------------------------- other configs
+# The default line is the 3-D wave workload above.  ``--config`` times the other
+# workloads of the method on the same contract (device-timed DOF/s, step-level
+# algorithmic bytes), and ``--compare`` adds the plain FP64 GPU form of the
+# same problem: its DOF/s, the speedup of the measured form over it, and the
+# relative L2 difference of the two final states.
+CONFIGS = {
+    "heat256": dict(metric="DOF updates/sec (2-D heat, 256^2, P=3, FP64, SSP-RK3) on GB300",
+                    bytes_per_dof=168, bound="latency", dtype="f64"),
+    "batch64": dict(metric="DOF updates/sec (64 batched 2-D heat problems, sides 128..2048, P=3) on GB300",
+                    bytes_per_dof=156, bound="hbm", dtype="f32"),
+    "hj4096": dict(metric="DOF updates/sec (2-D Hamilton-Jacobi, 4096^2, WENO-Z, FP32) on GB300",
+                   bytes_per_dof=20, bound="hbm", dtype="f32"),
+    "hj8192_learned": dict(metric="DOF updates/sec (2-D Hamilton-Jacobi, 8192^2, learned WENO weights, FP32) on GB300",
+                           bytes_per_dof=20, bound="tensor+alu", dtype="f32"),
+}
+
+
+def _problem(config, prec=None):
+    """(descs, initial states as numpy arrays, u_prev needed) of a config."""
+    import math
+    from paper_2007_03041_gb300 import molt as M
+    from paper_2007_03041_gb300 import workloads
+    if config == "heat256":
+        n = 256
+        d = M.make_desc((n, n), P=3, quad_points=3, beta=0.6, pde=M.PDE_HEAT, dt=0.5 / n,
+                        prec=M.PREC_F64 if prec is None else prec)
+        return [d], [workloads.heat_modes(n)]
+    if config == "batch64":
+        sides = workloads.batched_sides()
+        descs = [M.make_desc((n, n), P=3, quad_points=3, beta=0.6, pde=M.PDE_HEAT, dt=0.5 / n,
+                             prec=M.PREC_F32_F64UPDATE if prec is None else prec) for n in sides]
+        return descs, workloads.batched_heat(sides=sides)
+    n = 4096 if config == "hj4096" else 8192
+    weights = M.W_WENOZ if config == "hj4096" else M.W_LEARNED
+    if prec == M.PREC_F64:
+        weights = M.W_WENOZ
+    seed = workloads.SEED_HJ if config == "hj4096" else workloads.SEED_HJ_LARGE
+    d = M.make_desc((n, n), lo=[0, 0], hi=[2 * math.pi] * 2, P=1, quad_points=5, weights=weights, beta=1.0,
+                    pde=M.PDE_HJ, cfl=1.5, dt=0.0, prec=M.PREC_F32 if prec is None else prec)
+    return [d], [workloads.hj_initial(n, seed=seed)]
+
+
+def _timed_steps(config, steps, warmup, prec=None, blob=None, profile_kinds=()):
+    """Runs a config on the device: returns (ms per step, final states (device
+    tensors), per-kind device ms per step, learned-weight stats)."""
+    import torch
+    from paper_2007_03041_gb300 import molt as M
+    descs, u0 = _problem(config, prec)
+    f32 = descs[0].prec == M.PREC_F32
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = M.molt_create(descs, stream)
+        try:
+            if blob is not None and descs[0].weights == M.W_LEARNED:
+                M.molt_set_mlp(ctx, blob)
+            us = [torch.tensor(a, dtype=torch.float32 if f32 else torch.float64, device="cuda") for a in u0]
+            t = M.molt_step(ctx, us, None, nsteps=warmup, t=[0.0] * len(us)) if warmup else [0.0] * len(us)
+            if blob is not None and descs[0].weights == M.W_LEARNED:
+                M.molt_mlp_stats(ctx, reset=True)
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            t = M.molt_step(ctx, us, None, nsteps=steps, t=t)
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            stats = M.molt_mlp_stats(ctx) if (blob is not None and descs[0].weights == M.W_LEARNED) else None
+            # per-kind device times from a separate profiled run of the same
+            # length (event pairs around each launch; no graph replay)
+            kinds = {}
+            for name, kind in profile_kinds:
+                M.molt_set_option(ctx, M.OPT_PROFILE, 1)
+                pu = [x.clone() for x in us]
+                M.molt_step(ctx, pu, None, nsteps=steps, t=list(t))
+                tot, cnt = M.molt_profile_read(ctx, kind)
+                M.molt_set_option(ctx, M.OPT_PROFILE, 0)
+                kinds[name] = tot / steps
+                del pu
+        finally:
+            M.molt_destroy(ctx)
+    return ms, us, kinds, stats
+
+
+def run_config(args):
+    import torch
+    from paper_2007_03041_gb300 import molt as M
+    cfg = CONFIGS[args.config]
+    descs, _ = _problem(args.config)
+    dof = sum(int(d.n[0] * d.n[1] * d.n[2]) for d in descs)
+    extra = {}
+    blob = None
+    if args.config == "hj8192_learned":
+        from paper_2007_03041_gb300 import learned
+        t0 = time.perf_counter()
+        x, y, dlin = learned.harvest(n=4096, steps=500, snapshots=5, count=10_000_000)
+        t1 = time.perf_counter()
+        xe, ye = x[-500_000:], y[-500_000:]
+        _, blob, hist = learned.train(x[:-500_000], y[:-500_000], epochs=3, batch=16384, lr=3e-3, lr_final=3e-4)
+        t2 = time.perf_counter()
+        loss, fb = learned.evaluate(blob, xe, ye, dlin)
+        extra["training"] = {"stencils": int(x.shape[0]), "harvest_s": t1 - t0, "train_s": t2 - t1,
+                             "epochs": 3, "batch": 16384, "heldout_loss": loss, "heldout_fallback": fb,
+                             "source": "4096^2 WENO-Z Hamilton-Jacobi run, 500 steps, 5 snapshots"}
+        del x, y
+    kinds = {"heat256": (("sweep_final", M.KERNEL_HEAT_FINAL), ("sweep_acc", M.KERNEL_ACC_SET)),
+             "batch64": (("batch_step", M.KERNEL_BATCH),),
+             "hj4096": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y)),
+             "hj8192_learned": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y))}[args.config]
+    ms, us, per_kind, stats = _timed_steps(args.config, args.steps, args.warmup, blob=blob, profile_kinds=kinds)
+    value = dof / (ms / 1e3)
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = cfg["bytes_per_dof"] * dof / (ms / 1e3) / 1e9
+    line = {
+        "metric": cfg["metric"], "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": cfg["dtype"], "data": "synthetic",
+        "config": {"workload": args.config, "dof": dof},
+        "roofline": {"bound": cfg["bound"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "scope": "whole step, algorithmic bytes",
+                     "algorithmic_bytes_per_dof_step": cfg["bytes_per_dof"],
+                     "per_kind_ms_per_step": per_kind,
+                     "peak_source": "measured" if peaks else "fallback"},
+    }
+    if stats is not None:
+        extra["learned_stats"] = {"stencils": stats[0], "fallbacks": stats[1],
+                                  "fallback_fraction": stats[1] / max(stats[0], 1)}
+    if args.compare:
+        ms64, us64, _, _ = _timed_steps(args.config, args.steps, args.warmup, prec=M.PREC_F64)
+        num = sum(float(torch.linalg.norm(a.double() - b.double()) ** 2) for a, b in zip(us, us64))
+        den = sum(float(torch.linalg.norm(b.double()) ** 2) for b in us64)
+        extra["vs_plain_fp64_gpu"] = {"fp64_value": dof / (ms64 / 1e3), "fp64_ms_per_step": ms64,
+                                      "speedup": ms64 / ms, "rel_l2_vs_fp64": (num / max(den, 1e-300)) ** 0.5,
+                                      "steps_compared": args.warmup + args.steps}
+    line.update(extra)
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -312,9 +452,15 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--grid", type=lambda t: [int(v) for v in t.split(",")], default=[N, N, N],
                     help="nx,ny,nz (smaller grids are for profiler captures; the metric is quoted at 512^3)")
+    ap.add_argument("--config", default="wave512", choices=["wave512"] + sorted(CONFIGS),
+                    help="workload (default: the 3-D wave step the metric is quoted on)")
+    ap.add_argument("--compare", action="store_true",
+                    help="--config runs: also time the plain FP64 GPU form and report the speedup and difference")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config != "wave512":
+        run_config(args)
     else:
         run_ours(args)
 

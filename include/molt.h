@@ -199,6 +199,90 @@ molt_status molt_wave_step_noalloc(const molt_desc* desc, const double* u, const
 molt_status molt_batch_tile_shape(molt_ctx* ctx, int problem, int axis, int* points_per_lane, int* warps_per_line,
                                   int* lines_per_tile);
 
+/* ---------------------------------------------------------------------------
+ * Learned WENO weights.  The paper has no learned component: its nonlinear
+ * local integrals use WENO-Z weights (Sec. 2.4).  Problems with weights =
+ * MOLT_W_LEARNED (quad_points 5, MOLT_PREC_F32) replace the weight formula by
+ * a small network -- 5 stencil values -> 32 -> 32 -> 3, GELU (tanh form) after
+ * both hidden layers, softmax output -- evaluated on the tensor cores in BF16
+ * with FP32 accumulation inside the sweep.  Network inputs are the stencil
+ * values in J_R orientation (v_{e-3} .. v_{e+1}; J_L uses the mirrored
+ * stencil v_{e+3} .. v_{e-1}) minus the middle value, divided by their
+ * largest magnitude plus 1e-30.  Wherever the network's weights differ from
+ * the WENO-Z weights by more than 1e-2 in any component (or are not finite),
+ * the WENO-Z weights are used (fallback).
+ *
+ * Network blob (MOLT_MLP_BLOB_BYTES bytes, BF16, row-major, zero padded):
+ *   W1[32][16] (inputs 0..4 used), W2[32][32], W3[8][32] (outputs 0..2 used),
+ *   b1[32], b2[32], b3[8] (0..2 used).
+ * FP32 master parameters (MOLT_MLP_PARAMS floats, training entry points):
+ *   W1 (32x5), b1 (32), W2 (32x32), b2 (32), W3 (3x32), b3 (3), row-major.
+ * ------------------------------------------------------------------------- */
+#define MOLT_MLP_PARAMS 1347
+#define MOLT_MLP_BLOB_BYTES 3728
+
+/* Install the network used by the context's learned-weight problems.  blob:
+ * host or device memory (unified addressing), `bytes` must equal
+ * MOLT_MLP_BLOB_BYTES.  Synchronous (the blob may be reused on return).
+ * MOLT_EINVAL if no problem of the context uses learned weights.  Sweeps of
+ * learned-weight problems fail with MOLT_EINVAL until this has been called. */
+molt_status molt_set_mlp(molt_ctx* ctx, const void* blob, size_t bytes);
+
+/* Counters of the context's learned-weight sweeps since creation or the last
+ * reset: stencils evaluated by the network and stencils that fell back to
+ * WENO-Z.  Synchronous; reset != 0 clears both.  Either pointer may be NULL. */
+molt_status molt_mlp_stats(molt_ctx* ctx, int64_t* stencils, int64_t* fallbacks, int reset);
+
+/* The training and evaluation entry points below take no context: every
+ * pointer is a DEVICE pointer (16-byte aligned) unless stated, work is
+ * enqueued on `cuda_stream` (a cudaStream_t, NULL = legacy stream) and the
+ * calls return before it finishes.  n == 0 does nothing; n < 0 or a NULL
+ * required pointer returns MOLT_EINVAL. */
+
+/* WENO linear weights d_0, d_1, d_2 of the 5-point rule at nu = alpha*h
+ * (App. C construction; d_0 from the ratio of first coefficients, d_2 from
+ * the ratio of last ones, d_1 = 1 - d_0 - d_2).  d: host array of 3.
+ * Synchronous, host only. */
+molt_status molt_weno_linear_weights(double nu, double* d);
+
+/* Round FP32 master parameters theta[MOLT_MLP_PARAMS] to the BF16 blob. */
+molt_status molt_mlp_pack(const float* theta, void* blob, void* cuda_stream);
+
+/* Network weights of n stencils.  x: n x 5 raw stencil values (J_R
+ * orientation, not normalised; the call normalises).  w: n x 3 outputs.
+ * d: NULL for the raw network outputs, or the host array of the 3 linear
+ * weights -- then the WENO-Z fallback applies and, if `fallbacks` (device
+ * unsigned 64-bit counter) is not NULL, the number of fallbacks is added. */
+molt_status molt_mlp_forward(const void* blob, const float* x, int64_t n, const double* d, float* w,
+                             unsigned long long* fallbacks, void* cuda_stream);
+
+/* Mean-squared training loss L = (1/n) sum_i sum_r (p_ir - y_ir)^2 of the
+ * network outputs p (as molt_mlp_forward with d = NULL) against targets y
+ * (n x 3), and its gradient with respect to the FP32 master parameters
+ * (through the BF16 forward pass; products of the backward pass in BF16 with
+ * FP32 accumulation).  grad[MOLT_MLP_PARAMS] and *loss are overwritten. */
+molt_status molt_mlp_loss_grad(const void* blob, const float* x, const float* y, int64_t n, float* grad, float* loss,
+                               void* cuda_stream);
+
+/* One Adam step (Kingma & Ba, 2015) on the FP32 master parameters with
+ * moment buffers m, v (MOLT_MLP_PARAMS floats each, zero before step 1):
+ * m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * theta -= lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps); then the
+ * BF16 blob is rewritten from theta.  step >= 1. */
+molt_status molt_mlp_adam(float* theta, float* m, float* v, const float* grad, int64_t step, double lr, double beta1,
+                          double beta2, double eps, void* blob, void* cuda_stream);
+
+/* Training stencils from a periodic 2-D FP32 state u (ny x nx, x fastest):
+ * for each of `count` flat grid indices pos[i] (int64, 0 <= pos < nx*ny),
+ * row i*stride of x (n x 5) receives the 5 values along `axis` (0: x, 1: y)
+ * at offsets -3..1 (side 0, J_R) or +3..-1 (side 1, J_L), periodically
+ * wrapped, and, if y is not NULL, row i*stride of y (n x 3) their WENO-Z
+ * weights with linear weights d (host array of 3).  stride >= 1 interleaves
+ * the stencils of several calls.  An index outside the grid yields a row of
+ * NaNs. */
+molt_status molt_mlp_harvest(const float* u, int64_t nx, int64_t ny, const int64_t* pos, int64_t count, int axis,
+                             int side, const double* d, float* x, float* y, int64_t stride, void* cuda_stream);
+
 /* Release everything the context owns.  Synchronises its stream first. */
 molt_status molt_destroy(molt_ctx* ctx);
 

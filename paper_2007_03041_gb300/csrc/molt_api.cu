@@ -62,6 +62,9 @@ struct molt_ctx {
   unsigned long long* speed_dev = nullptr;  // per problem: 2 speed slots (double bits)
   double* t_dev = nullptr;         // per problem time (HJ)
   bool no_tma = false;             // force the plain kernels (molt_set_option)
+  void* mlp_blob = nullptr;        // learned weights: the BF16 network (MlpBlob)
+  unsigned long long* mlp_stats = nullptr;  // [stencils evaluated, fallbacks]
+  bool mlp_ready = false;          // molt_set_mlp has been called
   bool profile = false;
   struct Rec { int kind; cudaEvent_t start, stop; };
   std::vector<Rec> recs;
@@ -228,6 +231,12 @@ molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, do
   const size_t tb = compute_bytes(p.d);
   size_t off = (size_t(4 * W) * 8 + size_t(W * nwl * 4) * tb + 15) & ~size_t(15);
   out->smem = off + size_t(W) * LS * tb;
+  if (p.d.weights == MOLT_W_LEARNED) {
+    if (!c->mlp_ready) return fail(c, MOLT_EINVAL, "learned weights: call molt_set_mlp first");
+    out->smem += learned_extra_bytes(W, LS);
+    a.mlp = static_cast<const MlpBlob*>(c->mlp_blob);
+    a.mlp_stats = c->mlp_stats;
+  }
   if (out->smem > 200 * 1024) return fail(c, MOLT_EUNSUPPORTED, "tile does not fit in shared memory");
   out->block = 32 * nwl * W;
   out->grid = int((a.g.nlines + W - 1) / W);
@@ -293,48 +302,62 @@ template <typename T, typename TIN, typename TST>
 cudaError_t dispatch_lin(int epi, const Plan& pl, cudaStream_t s) {
   const SweepArgs& a = pl.a;
   switch (epi) {
-    case EPI_STORE: return launch_sweep<T, TIN, TST, false, EPI_STORE>(a, TMA, pl.grid, pl.block, pl.smem, s);
-    case EPI_ACC_SET: return launch_sweep<T, TIN, TST, false, EPI_ACC_SET>(a, TMA, pl.grid, pl.block, pl.smem, s);
-    case EPI_ACC_ADD: return launch_sweep<T, TIN, TST, false, EPI_ACC_ADD>(a, TMA, pl.grid, pl.block, pl.smem, s);
-    case EPI_HEAT_FINAL: return launch_sweep<T, TIN, TST, false, EPI_HEAT_FINAL>(a, TMA, pl.grid, pl.block, pl.smem, s);
-    case EPI_WAVE_FINAL: return launch_sweep<T, TIN, TST, false, EPI_WAVE_FINAL>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    case EPI_STORE: return launch_sweep<T, TIN, TST, JQ_LINEAR, EPI_STORE>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    case EPI_ACC_SET: return launch_sweep<T, TIN, TST, JQ_LINEAR, EPI_ACC_SET>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    case EPI_ACC_ADD: return launch_sweep<T, TIN, TST, JQ_LINEAR, EPI_ACC_ADD>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    case EPI_HEAT_FINAL: return launch_sweep<T, TIN, TST, JQ_LINEAR, EPI_HEAT_FINAL>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    case EPI_WAVE_FINAL: return launch_sweep<T, TIN, TST, JQ_LINEAR, EPI_WAVE_FINAL>(a, TMA, pl.grid, pl.block, pl.smem, s);
     default: return cudaErrorNotSupported;
   }
 }
 
 template <typename T>
-cudaError_t dispatch_same(bool weno, int epi, const Plan& pl, cudaStream_t s) {
+cudaError_t dispatch_same(int jq, int epi, const Plan& pl, cudaStream_t s) {
   const SweepArgs& a = pl.a;
-  if (weno) {
-    if (epi == EPI_STORE) return launch_sweep<T, T, T, true, EPI_STORE>(a, TMA, pl.grid, pl.block, pl.smem, s);
-    if (epi == EPI_HJ_X) return launch_sweep<T, T, T, true, EPI_HJ_X>(a, TMA, pl.grid, pl.block, pl.smem, s);
-    if (epi == EPI_HJ_Y) return launch_sweep<T, T, T, true, EPI_HJ_Y>(a, TMA, pl.grid, pl.block, pl.smem, s);
+  if (jq == JQ_WENOZ) {
+    if (epi == EPI_STORE) return launch_sweep<T, T, T, JQ_WENOZ, EPI_STORE>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    if (epi == EPI_HJ_X) return launch_sweep<T, T, T, JQ_WENOZ, EPI_HJ_X>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    if (epi == EPI_HJ_Y) return launch_sweep<T, T, T, JQ_WENOZ, EPI_HJ_Y>(a, TMA, pl.grid, pl.block, pl.smem, s);
     return cudaErrorNotSupported;
   }
-  if (epi == EPI_HJ_X) return launch_sweep<T, T, T, false, EPI_HJ_X>(a, TMA, pl.grid, pl.block, pl.smem, s);
-  if (epi == EPI_HJ_Y) return launch_sweep<T, T, T, false, EPI_HJ_Y>(a, TMA, pl.grid, pl.block, pl.smem, s);
+  if (jq == JQ_LEARNED) {
+    if constexpr (sizeof(T) == 4) {
+      if (epi == EPI_STORE) return launch_sweep<T, T, T, JQ_LEARNED, EPI_STORE>(a, nullptr, pl.grid, pl.block, pl.smem, s);
+      if (epi == EPI_HJ_X) return launch_sweep<T, T, T, JQ_LEARNED, EPI_HJ_X>(a, nullptr, pl.grid, pl.block, pl.smem, s);
+      if (epi == EPI_HJ_Y) return launch_sweep<T, T, T, JQ_LEARNED, EPI_HJ_Y>(a, nullptr, pl.grid, pl.block, pl.smem, s);
+    }
+    return cudaErrorNotSupported;
+  }
+  if (epi == EPI_HJ_X) return launch_sweep<T, T, T, JQ_LINEAR, EPI_HJ_X>(a, TMA, pl.grid, pl.block, pl.smem, s);
+  if (epi == EPI_HJ_Y) return launch_sweep<T, T, T, JQ_LINEAR, EPI_HJ_Y>(a, TMA, pl.grid, pl.block, pl.smem, s);
   return dispatch_lin<T, T, T>(epi, pl, s);
+}
+
+int jquad(const molt_desc& d) {
+  return d.weights == MOLT_W_WENOZ ? JQ_WENOZ : (d.weights == MOLT_W_LEARNED ? JQ_LEARNED : JQ_LINEAR);
 }
 
 // apply_D in mixed precision reads the FP64 array directly; molt_step's
 // sweeps read the FP32 copy of the state.
 cudaError_t launch(const Problem& p, int epi, const Plan& pl, cudaStream_t s, bool from_state_copy) {
-  const bool weno = p.d.weights == MOLT_W_WENOZ;
-  if (is_f64_sweep(p.d)) return dispatch_same<double>(weno, epi, pl, s);
-  if (is_f32_state(p.d)) return dispatch_same<float>(weno, epi, pl, s);
+  const int jq = jquad(p.d);
+  if (is_f64_sweep(p.d)) return dispatch_same<double>(jq, epi, pl, s);
+  if (is_f32_state(p.d)) return dispatch_same<float>(jq, epi, pl, s);
+  if (jq == JQ_LEARNED) return cudaErrorNotSupported;
   if (!from_state_copy) {
     if (epi != EPI_STORE) return cudaErrorNotSupported;
-    if (weno) return launch_sweep<float, double, double, true, EPI_STORE>(pl.a, TMA, pl.grid, pl.block, pl.smem, s);
-    return launch_sweep<float, double, double, false, EPI_STORE>(pl.a, TMA, pl.grid, pl.block, pl.smem, s);
+    if (jq == JQ_WENOZ)
+      return launch_sweep<float, double, double, JQ_WENOZ, EPI_STORE>(pl.a, TMA, pl.grid, pl.block, pl.smem, s);
+    return launch_sweep<float, double, double, JQ_LINEAR, EPI_STORE>(pl.a, TMA, pl.grid, pl.block, pl.smem, s);
   }
-  if (weno) return cudaErrorNotSupported;
+  if (jq == JQ_WENOZ) return cudaErrorNotSupported;
   return dispatch_lin<float, float, double>(epi, pl, s);
 }
 
 molt_status run(molt_ctx* c, const Problem& p, int epi, Plan& pl, bool from_state_copy = true) {
   // element size of the sweep input: FP64 except FP32 state or the FP32 copy
   const size_t in_bytes = is_f32_state(p.d) || (is_mixed(p.d) && from_state_copy) ? 4 : 8;
-  if (!c->no_tma) plan_tma(p, pl.ax, pl.a.in, in_bytes, &pl);
+  if (!c->no_tma && p.d.weights != MOLT_W_LEARNED) plan_tma(p, pl.ax, pl.a.in, in_bytes, &pl);
   molt_ctx::Rec rec{epi, nullptr, nullptr};
   if (c->profile) {
     cudaEventCreate(&rec.start);
@@ -404,9 +427,9 @@ molt_status molt_create(const molt_desc* descs, int count, void* cuda_stream, mo
         return fail(nullptr, MOLT_EINVAL, "cfl must be positive");
       }
     }
-    if (p.d.weights == MOLT_W_LEARNED) {
+    if (p.d.weights == MOLT_W_LEARNED && p.d.prec != MOLT_PREC_F32) {
       delete c;
-      return fail(nullptr, MOLT_EUNSUPPORTED, "learned weights are not available in this build");
+      return fail(nullptr, MOLT_EUNSUPPORTED, "learned weights run with MOLT_PREC_F32");
     }
     c->probs.push_back(p);
   }
@@ -419,6 +442,16 @@ molt_status molt_create(const molt_desc* descs, int count, void* cuda_stream, mo
   }
   cudaMemset(c->status_dev, 0, sizeof(int));
   cudaMemset(c->speed_dev, 0, sizeof(unsigned long long) * 2 * count);
+  bool learned = false;
+  for (const auto& p : c->probs) learned = learned || p.d.weights == MOLT_W_LEARNED;
+  if (learned) {
+    if ((e = cudaMalloc(&c->mlp_blob, sizeof(MlpBlob))) != cudaSuccess ||
+        (e = cudaMalloc(&c->mlp_stats, 2 * sizeof(unsigned long long))) != cudaSuccess) {
+      molt_destroy(c);
+      return fail(nullptr, MOLT_ENOMEM, std::string("network workspace: ") + cudaGetErrorString(e));
+    }
+    cudaMemset(c->mlp_stats, 0, 2 * sizeof(unsigned long long));
+  }
   for (auto& p : c->probs) {
     const size_t cb = compute_bytes(p.d), sb = state_bytes(p.d);
     const size_t tot = size_t(p.total);
@@ -1077,7 +1110,37 @@ molt_status molt_destroy(molt_ctx* c) {
   cudaFree(c->status_dev);
   cudaFree(c->speed_dev);
   cudaFree(c->t_dev);
+  cudaFree(c->mlp_blob);
+  cudaFree(c->mlp_stats);
   delete c;
+  return MOLT_OK;
+}
+
+molt_status molt_set_mlp(molt_ctx* c, const void* blob, size_t bytes) {
+  if (!c) return fail(nullptr, MOLT_EINVAL, "null context");
+  if (!blob) return fail(c, MOLT_EINVAL, "null network");
+  if (bytes != sizeof(MlpBlob)) return fail(c, MOLT_EINVAL, "network blob must be MOLT_MLP_BLOB_BYTES bytes");
+  if (!c->mlp_blob) return fail(c, MOLT_EINVAL, "no problem of this context uses learned weights");
+  cudaError_t e = cudaMemcpyAsync(c->mlp_blob, blob, bytes, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "molt_set_mlp");
+  c->mlp_ready = true;
+  return MOLT_OK;
+}
+
+molt_status molt_mlp_stats(molt_ctx* c, int64_t* stencils, int64_t* fallbacks, int reset) {
+  if (!c) return fail(nullptr, MOLT_EINVAL, "null context");
+  if (!c->mlp_stats) return fail(c, MOLT_EINVAL, "no problem of this context uses learned weights");
+  unsigned long long h[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(h, c->mlp_stats, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess && reset) {
+    e = cudaMemsetAsync(c->mlp_stats, 0, sizeof(h), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "molt_mlp_stats");
+  if (stencils) *stencils = int64_t(h[0]);
+  if (fallbacks) *fallbacks = int64_t(h[1]);
   return MOLT_OK;
 }
 

@@ -35,6 +35,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "mlp.cuh"
+
 namespace molt {
 
 constexpr int kE = 16;   // points per lane
@@ -105,7 +107,13 @@ struct SweepArgs {
   double cfl_h, dt_max;
   double* t_dev;            // time accumulator (HJ_Y, block 0)
   int* status;
+  // learned weights (JQ_LEARNED kernels)
+  const MlpBlob* mlp;               // BF16 network
+  unsigned long long* mlp_stats;    // [stencils evaluated, WENO-Z fallbacks]
 };
+
+// Local-quadrature kind of a sweep kernel (template parameter JQ).
+enum JQuad { JQ_LINEAR = 0, JQ_WENOZ = 1, JQ_LEARNED = 2 };
 
 // Shared-memory index of point e of a line whose lanes own E points each: one
 // pad word after every E words (kG is a multiple of E), so lane chunks start
@@ -324,9 +332,17 @@ struct TileSmem {
   double* carries;   // [W][4] compute-type (hi, lo) carry pairs (room for FP64)
   void* totals;      // [W][nwl][4] of T
   void* lines;       // [W][LS] of T
+  float* jloc;       // JQ_LEARNED: [W][2][LS] local integrals J_R, J_L
+  MlpNet* net;       // JQ_LEARNED: the network
 };
 
-template <typename T>
+// Shared bytes of a tile beyond the lines for learned weights (the host
+// planner adds the same amount).
+__host__ __device__ constexpr size_t learned_extra_bytes(int W, int LS) {
+  return 16 + size_t(2) * W * LS * sizeof(float) + sizeof(MlpNet);
+}
+
+template <typename T, int JQ = JQ_LINEAR>
 __device__ __forceinline__ TileSmem carve(unsigned char* smem, const SweepArgs& a, size_t* used) {
   TileSmem t;
   t.carries = reinterpret_cast<double*>(smem);
@@ -334,6 +350,15 @@ __device__ __forceinline__ TileSmem carve(unsigned char* smem, const SweepArgs& 
   const size_t off = (size_t(4 * a.W) * sizeof(double) + size_t(a.W * a.nwl * 4) * sizeof(T) + 15) & ~size_t(15);
   t.lines = smem + off;
   *used = off + size_t(a.W) * a.LS * sizeof(T);
+  t.jloc = nullptr;
+  t.net = nullptr;
+  if constexpr (JQ == JQ_LEARNED) {
+    const size_t j0 = (*used + 15) & ~size_t(15);
+    t.jloc = reinterpret_cast<float*>(smem + j0);
+    const size_t n0 = j0 + size_t(2) * a.W * a.LS * sizeof(float);
+    t.net = reinterpret_cast<MlpNet*>(smem + n0);
+    *used = n0 + sizeof(MlpNet);
+  }
   return t;
 }
 
@@ -460,12 +485,81 @@ __device__ __forceinline__ void warp_fill_ghosts(const SweepArgs& a, T* b, int l
   }
 }
 
+// Learned local integrals of the points a warp owns (32*E consecutive points
+// of its line from `first`): for 16 points at a time and each side, the lanes
+// gather the 5-value stencils (J_R: v_{e-3..e+1}; J_L mirrored: v_{e+3..e-1})
+// from the staged line, the warp evaluates the network on the tensor cores,
+// and lanes t = 0, 1 of each row group finish rows g, g+8: WENO-Z fallback
+// check, then J = sum_r w_r J^{(r)} into jr / jl (shared, line layout).
+template <int E>
+__device__ __forceinline__ void learned_local_integrals(const SweepArgs& a, const MlpNet& net, const float* buf,
+                                                        float* jr, float* jl, int first, int n, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  MlpRegs R;
+  mlp_load_regs(net, lane, R);
+  float sub[3][3], d[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    d[r] = a.df[r];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) sub[r][j] = a.subf[r][j];
+  }
+  unsigned evaluated = 0, fallbacks = 0;
+  for (int b = 0; b < 32 * E; b += 16) {
+    if (first + b >= n) break;   // warp-uniform
+    const int e0 = first + b + g, e1 = e0 + 8;
+    const int c0 = e0 < n ? e0 : n - 1, c1 = e1 < n ? e1 : n - 1;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      float v0[5], v1[5];
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        const int o = side == 0 ? j - 3 : 3 - j;
+        v0[j] = buf[phys<E>(c0 + o)];
+        v1[j] = buf[phys<E>(c1 + o)];
+      }
+      float x0[5], x1[5];
+      mlp_normalise(v0, x0);
+      mlp_normalise(v1, x1);
+      uint32_t xa[4];
+      mlp_input_frag(x0, x1, t, xa);
+      MlpCache f;
+      float p0[3], p1[3];
+      mlp_forward16(R, xa, f, p0, p1);
+      const int e = t == 0 ? e0 : e1;
+      if (t < 2 && e < n) {
+        float v[5], p[3], w[3];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) v[j] = t == 0 ? v0[j] : v1[j];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) p[r] = t == 0 ? p0[r] : p1[r];
+        fallbacks += mlp_final_weights(v, p, d, w) ? 1u : 0u;
+        ++evaluated;
+        float J = 0.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) J = fmaf(w[r], fmaf(sub[r][0], v[r], fmaf(sub[r][1], v[r + 1], sub[r][2] * v[r + 2])), J);
+        (side == 0 ? jr : jl)[phys<E>(e)] = J;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    evaluated += __shfl_xor_sync(0xffffffffu, evaluated, o);
+    fallbacks += __shfl_xor_sync(0xffffffffu, fallbacks, o);
+  }
+  if (lane == 0 && a.mlp_stats) {
+    atomicAdd(a.mlp_stats, (unsigned long long)evaluated);
+    if (fallbacks) atomicAdd(a.mlp_stats + 1, (unsigned long long)fallbacks);
+  }
+}
+
 // WL (warp-local): every line is owned by a single warp (nwl == 1), so a D
 // application needs no CTA-wide barrier: ghosts, line totals and the FP64
 // boundary solve stay inside the warp (the solve runs on lane 0 and its
 // result is broadcast by shuffles).
-template <typename T, bool WENO, bool RAGGED, bool WL, int E = kE>
+template <typename T, int JQ, bool RAGGED, bool WL, int E = kE>
 __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSmem& sm, bool line_ok) {
+  static_assert(JQ != JQ_LEARNED || sizeof(T) == 4, "learned weights run in FP32");
   const int nwl = a.nwl, n = a.g.n;
   double* carries = sm.carries;
   T* totals = static_cast<T*>(sm.totals);
@@ -484,7 +578,7 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
 #pragma unroll
   for (int i = 0; i < 6; ++i) c[i] = pick<T>(a.c[i], a.cf[i]);
   T sub[3][3], dw[3];
-  if constexpr (WENO) {
+  if constexpr (JQ == JQ_WENOZ) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       dw[r] = pick<T>(a.d[r], a.df[r]);
@@ -523,6 +617,12 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
 
   for (int p = 0; p < a.P; ++p) {
     // ---- 1. local integrals from a window of E + 6 points
+    float* jrl = nullptr;
+    if constexpr (JQ == JQ_LEARNED) {
+      jrl = sm.jloc + lw * 2 * a.LS;
+      if (line_ok) learned_local_integrals<E>(a, *sm.net, buf, jrl, jrl + a.LS, part * 32 * E, n, lane);
+      __syncwarp();
+    }
     {
       T win[E + 6];
 #pragma unroll
@@ -530,7 +630,10 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
 #pragma unroll
       for (int k = 0; k < E; ++k) {
         v[k] = win[k + 3];
-        if constexpr (WENO) {
+        if constexpr (JQ == JQ_LEARNED) {
+          Y[k].x = jrl[(E + 1) * tl + chunk_off<E>(k)];
+          Y[E - 1 - (k)].y = jrl[a.LS + (E + 1) * tl + chunk_off<E>(k)];
+        } else if constexpr (JQ == JQ_WENOZ) {
           T wr[5], wl[5];
 #pragma unroll
           for (int j = 0; j < 5; ++j) {
@@ -729,15 +832,15 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
 #ifndef MOLT_WL_MODE
 #define MOLT_WL_MODE 0
 #endif
-template <typename T, bool WENO, bool RAGGED, int E = kE>
+template <typename T, int JQ, bool RAGGED, int E = kE>
 __device__ __forceinline__ double compute_lines_any(const SweepArgs& a, const TileSmem& sm, bool line_ok) {
 #if MOLT_WL_MODE == 0
-  return compute_lines<T, WENO, RAGGED, false, E>(a, sm, line_ok);
+  return compute_lines<T, JQ, RAGGED, false, E>(a, sm, line_ok);
 #elif MOLT_WL_MODE == 2
-  return compute_lines<T, WENO, RAGGED, true, E>(a, sm, line_ok);
+  return compute_lines<T, JQ, RAGGED, true, E>(a, sm, line_ok);
 #else
-  if (a.nwl == 1) return compute_lines<T, WENO, RAGGED, true, E>(a, sm, line_ok);
-  return compute_lines<T, WENO, RAGGED, false, E>(a, sm, line_ok);
+  if (a.nwl == 1) return compute_lines<T, JQ, RAGGED, true, E>(a, sm, line_ok);
+  return compute_lines<T, JQ, RAGGED, false, E>(a, sm, line_ok);
 #endif
 }
 
@@ -882,18 +985,19 @@ __device__ __forceinline__ void publish_speed(const SweepArgs& a, double rmax) {
 }
 
 // One tile per CTA, plain coalesced loads (any size / alignment).
-template <typename T, typename TIN, typename TST, bool WENO, int EPI, bool RAGGED>
+template <typename T, typename TIN, typename TST, int JQ, int EPI, bool RAGGED>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) sweep_kernel(const SweepArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   size_t used;
-  const TileSmem sm = carve<T>(smem_raw, a, &used);
+  const TileSmem sm = carve<T, JQ>(smem_raw, a, &used);
+  if constexpr (JQ == JQ_LEARNED) mlp_load_net(*sm.net, a.mlp);
   T* lines = static_cast<T*>(sm.lines);
   const long long line0 = (long long)blockIdx.x * a.W;
   const int warp = threadIdx.x >> 5, lw = warp / a.nwl;
   const int tl = (warp - lw * a.nwl) * 32 + (threadIdx.x & 31);
   load_tile<T, TIN>(a, static_cast<const TIN*>(a.in), lines, line0, lw, tl);
   __syncthreads();
-  const double rmax = compute_lines_any<T, WENO, RAGGED>(a, sm, line0 + lw < a.g.nlines);
+  const double rmax = compute_lines_any<T, JQ, RAGGED>(a, sm, line0 + lw < a.g.nlines);
   publish_speed<EPI>(a, rmax);
   const double dt = hj_dt<EPI>(a);
   if (EPI == EPI_HJ_Y && blockIdx.x == 0 && threadIdx.x == 0 && a.t_dev) *a.t_dev += dt;

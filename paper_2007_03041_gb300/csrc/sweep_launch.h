@@ -19,7 +19,7 @@ struct TmaPlan {
 
 // tma == nullptr: one tile per CTA with plain loads (grid/block/smem given);
 // otherwise the persistent TMA kernel on at most `grid` CTAs.
-template <typename T, typename TIN, typename TST, bool WENO, int EPI>
+template <typename T, typename TIN, typename TST, int JQ, int EPI>
 cudaError_t launch_sweep(const SweepArgs& a, const TmaPlan* tma, int grid, int block, size_t smem,
                          cudaStream_t s);
 
@@ -27,11 +27,13 @@ cudaError_t launch_sweep(const SweepArgs& a, const TmaPlan* tma, int grid, int b
 inline bool exact_fit(const SweepArgs& a) { return a.g.n == a.nwl * 32 * kE; }
 
 #define MOLT_DEFINE_LAUNCH                                                                       \
-  template <typename T, typename TIN, typename TST, bool WENO, int EPI>                          \
+  template <typename T, typename TIN, typename TST, int JQ, int EPI>                             \
   cudaError_t launch_sweep(const SweepArgs& a, const TmaPlan* tma, int grid, int block,          \
                            size_t smem, cudaStream_t s) {                                        \
-    if (tma) {                                                                                   \
-      auto k = &sweep_tma_kernel<T, TIN, TST, WENO, EPI>;                                        \
+    if constexpr (JQ == JQ_LEARNED) {                                                            \
+      if (tma) return cudaErrorNotSupported;                                                     \
+    } else if (tma) {                                                                            \
+      auto k = &sweep_tma_kernel<T, TIN, TST, JQ, EPI>;                                          \
       static bool configured = false;                                                            \
       if (!configured) {                                                                         \
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
@@ -51,8 +53,8 @@ inline bool exact_fit(const SweepArgs& a) { return a.g.n == a.nwl * 32 * kE; }
       return cudaGetLastError();                                                                 \
     }                                                                                            \
     const bool fit = exact_fit(a);                                                               \
-    auto k = fit ? &sweep_kernel<T, TIN, TST, WENO, EPI, false>                                  \
-                 : &sweep_kernel<T, TIN, TST, WENO, EPI, true>;                                  \
+    auto k = fit ? &sweep_kernel<T, TIN, TST, JQ, EPI, false>                                    \
+                 : &sweep_kernel<T, TIN, TST, JQ, EPI, true>;                                    \
     static bool configured[2] = {false, false};                                                  \
     if (!configured[fit]) {                                                                      \
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
@@ -64,8 +66,8 @@ inline bool exact_fit(const SweepArgs& a) { return a.g.n == a.nwl * 32 * kE; }
     return cudaGetLastError();                                                                   \
   }
 
-#define MOLT_INST(T, TIN, TST, WENO, EPI)                                                        \
-  template cudaError_t launch_sweep<T, TIN, TST, WENO, EPI>(const SweepArgs&, const TmaPlan*, int, \
+#define MOLT_INST(T, TIN, TST, JQ, EPI)                                                          \
+  template cudaError_t launch_sweep<T, TIN, TST, JQ, EPI>(const SweepArgs&, const TmaPlan*, int,   \
                                                             int, size_t, cudaStream_t);
 
 }  // namespace molt

@@ -4,11 +4,11 @@
 
 namespace molt {
 MOLT_DEFINE_LAUNCH
-MOLT_INST(float, float, double, false, EPI_STORE)
-MOLT_INST(float, float, double, false, EPI_ACC_SET)
-MOLT_INST(float, float, double, false, EPI_ACC_ADD)
-MOLT_INST(float, float, double, false, EPI_HEAT_FINAL)
-MOLT_INST(float, float, double, false, EPI_WAVE_FINAL)
-MOLT_INST(float, double, double, false, EPI_STORE)
-MOLT_INST(float, double, double, true, EPI_STORE)
+MOLT_INST(float, float, double, JQ_LINEAR, EPI_STORE)
+MOLT_INST(float, float, double, JQ_LINEAR, EPI_ACC_SET)
+MOLT_INST(float, float, double, JQ_LINEAR, EPI_ACC_ADD)
+MOLT_INST(float, float, double, JQ_LINEAR, EPI_HEAT_FINAL)
+MOLT_INST(float, float, double, JQ_LINEAR, EPI_WAVE_FINAL)
+MOLT_INST(float, double, double, JQ_LINEAR, EPI_STORE)
+MOLT_INST(float, double, double, JQ_WENOZ, EPI_STORE)
 }  // namespace molt

@@ -184,7 +184,7 @@ __device__ __forceinline__ void transpose_tile(const SweepArgs& a, const TmaGeom
   }
 }
 
-template <typename T, typename TIN, typename TST, bool WENO, int EPI>
+template <typename T, typename TIN, typename TST, int JQ, int EPI>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
     sweep_tma_kernel(const SweepArgs a, const TmaGeom tg, const __grid_constant__ CUtensorMap map) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
       }
       prefetch_operands<T, TST, EPI>(a, next * a.W);
     }
-    rmax = fmax(rmax, compute_lines_any<T, WENO, false>(a, sm, line0 + lw < a.g.nlines));
+    rmax = fmax(rmax, compute_lines_any<T, JQ, false>(a, sm, line0 + lw < a.g.nlines));
     epilogue_tile<T, TST, EPI>(a, lines, line0, dt);
     __syncthreads();
   }

@@ -19,7 +19,11 @@ PDE_HEAT, PDE_WAVE, PDE_HJ = 0, 1, 2
 W_LINEAR, W_WENOZ, W_LEARNED = 0, 1, 2
 
 EXPORTS = ("molt_create", "molt_apply_D", "molt_step", "molt_set_option", "molt_profile_read", "molt_destroy",
-           "molt_last_error", "molt_wave_step_noalloc", "molt_batch_tile_shape")
+           "molt_last_error", "molt_wave_step_noalloc", "molt_batch_tile_shape", "molt_set_mlp", "molt_mlp_stats",
+           "molt_weno_linear_weights", "molt_mlp_pack", "molt_mlp_forward", "molt_mlp_loss_grad", "molt_mlp_adam",
+           "molt_mlp_harvest")
+MLP_PARAMS = 1347
+MLP_BLOB_BYTES = 3728
 OPT_TMA, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_TEST_SKIP_ARRIVE = 0, 1, 2, 3
 (KERNEL_STORE, KERNEL_ACC_SET, KERNEL_ACC_ADD, KERNEL_HEAT_FINAL, KERNEL_WAVE_FINAL, KERNEL_HJ_X, KERNEL_HJ_Y,
  KERNEL_UPDATE, KERNEL_BATCH) = range(9)
@@ -77,6 +81,19 @@ def load_library(path=LIB_PATH):
         lib.molt_wave_step_noalloc.argtypes = [ctypes.POINTER(molt_desc), ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
         lib.molt_wave_step_noalloc.restype = ctypes.c_int
+        vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+        lib.molt_set_mlp.argtypes = [vp, vp, ctypes.c_size_t]
+        lib.molt_mlp_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.c_int]
+        lib.molt_weno_linear_weights.argtypes = [dbl, ctypes.POINTER(dbl)]
+        lib.molt_mlp_pack.argtypes = [vp, vp, vp]
+        lib.molt_mlp_forward.argtypes = [vp, vp, i64, ctypes.POINTER(dbl), vp, vp, vp]
+        lib.molt_mlp_loss_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+        lib.molt_mlp_adam.argtypes = [vp, vp, vp, vp, i64, dbl, dbl, dbl, dbl, vp, vp]
+        lib.molt_mlp_harvest.argtypes = [vp, i64, i64, vp, i64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl), vp,
+                                         vp, i64, vp]
+        for f in ("molt_set_mlp", "molt_mlp_stats", "molt_weno_linear_weights", "molt_mlp_pack", "molt_mlp_forward",
+                  "molt_mlp_loss_grad", "molt_mlp_adam", "molt_mlp_harvest"):
+            getattr(lib, f).restype = ctypes.c_int
         lib.molt_last_error.argtypes = [ctypes.c_void_p]
         lib.molt_last_error.restype = ctypes.c_char_p
         for f in ("molt_create", "molt_apply_D", "molt_step", "molt_set_option", "molt_profile_read", "molt_destroy"):
@@ -194,3 +211,85 @@ def molt_batch_tile_shape(ctx, problem, axis):
 def molt_destroy(ctx):
     lib = load_library()
     _check(lib, ctx, lib.molt_destroy(ctx))
+
+
+# ------------------------------------------------------------ learned weights
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _status(st, what):
+    if st != MOLT_OK:
+        raise MoltError(st, what)
+
+
+def _dvec3(d):
+    return None if d is None else (ctypes.c_double * 3)(*[float(v) for v in d])
+
+
+def molt_set_mlp(ctx, blob):
+    """Install the BF16 network (a CUDA or CPU uint8 tensor of MLP_BLOB_BYTES)."""
+    lib = load_library()
+    if not blob.is_contiguous():
+        raise ValueError("network blob must be contiguous")
+    _check(lib, ctx, lib.molt_set_mlp(ctx, ctypes.c_void_p(blob.data_ptr()), blob.numel() * blob.element_size()))
+
+
+def molt_mlp_stats(ctx, reset=False):
+    """(stencils evaluated, WENO-Z fallbacks) of the context's learned sweeps."""
+    lib = load_library()
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib, ctx, lib.molt_mlp_stats(ctx, ctypes.byref(a), ctypes.byref(b), 1 if reset else 0))
+    return a.value, b.value
+
+
+def molt_weno_linear_weights(nu):
+    """Linear weights (d_0, d_1, d_2) of the 5-point rule at nu = alpha*h."""
+    lib = load_library()
+    d = (ctypes.c_double * 3)()
+    _status(lib.molt_weno_linear_weights(float(nu), d), "molt_weno_linear_weights")
+    return tuple(d)
+
+
+def molt_mlp_pack(theta, blob, stream=None):
+    lib = load_library()
+    _status(lib.molt_mlp_pack(_ptr(theta), _ptr(blob), _stream_ptr(stream)), "molt_mlp_pack")
+
+
+def molt_mlp_forward(blob, x, w, d=None, fallbacks=None, stream=None):
+    """Network weights w (n x 3) of raw stencils x (n x 5); with linear
+    weights ``d`` the WENO-Z fallback applies (count added to ``fallbacks``,
+    a CUDA int64 tensor of one element)."""
+    lib = load_library()
+    fb = _ptr(fallbacks) if fallbacks is not None else None
+    _status(lib.molt_mlp_forward(_ptr(blob), _ptr(x), int(x.shape[0]), _dvec3(d), _ptr(w), fb, _stream_ptr(stream)),
+            "molt_mlp_forward")
+
+
+def molt_mlp_loss_grad(blob, x, y, grad, loss, stream=None):
+    lib = load_library()
+    _status(lib.molt_mlp_loss_grad(_ptr(blob), _ptr(x), _ptr(y), int(x.shape[0]), _ptr(grad), _ptr(loss),
+                                   _stream_ptr(stream)), "molt_mlp_loss_grad")
+
+
+def molt_mlp_adam(theta, m, v, grad, step, lr, blob, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    lib = load_library()
+    _status(lib.molt_mlp_adam(_ptr(theta), _ptr(m), _ptr(v), _ptr(grad), int(step), float(lr), float(beta1),
+                              float(beta2), float(eps), _ptr(blob), _stream_ptr(stream)), "molt_mlp_adam")
+
+
+def molt_mlp_harvest(u, pos, axis, side, x, y=None, d=None, stride=1, stream=None):
+    """Stencils at flat indices ``pos`` (int64) of the periodic 2-D FP32 state
+    u (ny x nx) along ``axis`` (0: x, 1: y), side 0 (J_R) or 1 (J_L), into
+    rows 0, stride, 2 stride, ... of x (n x 5); WENO-Z targets into the same
+    rows of y (n x 3) with linear weights d.  x and y may be views that start
+    at a row offset."""
+    lib = load_library()
+    ny, nx = u.shape
+    _status(lib.molt_mlp_harvest(_ptr(u), int(nx), int(ny), _ptr(pos), int(pos.shape[0]), int(axis), int(side),
+                                 _dvec3(d), ctypes.c_void_p(x.data_ptr()),
+                                 ctypes.c_void_p(y.data_ptr()) if y is not None else None, int(stride),
+                                 _stream_ptr(stream)), "molt_mlp_harvest")

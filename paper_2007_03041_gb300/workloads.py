@@ -18,6 +18,11 @@ boundary nodes, h = (hi-lo)/(n-1)):
                       {128, 256, 512, 1024, 2048}.
 * ``hj_initial``   -- 2-D periodic [0,2pi]^2, u0 = -cos x - cos y plus iid
                       1e-3 N(0,1) noise per node.
+* ``mlp_stencils`` -- raw 5-value stencils of the kinds the learned weight
+                      path meets: smooth data sampled at h = 2 pi / 4096 on an
+                      O(1) level, the same with 1e-3 noise, kinks and jumps.
+* ``mlp_initial_params`` -- seeded He-style initial network parameters.
+* ``mlp_positions`` -- seeded flat grid indices for harvesting stencils.
 """
 import numpy as np
 
@@ -26,6 +31,7 @@ SEED_WAVE = 2
 SEED_BATCH = 3
 SEED_HJ = 4
 SEED_HJ_LARGE = 5
+SEED_MLP = 50
 
 
 def rng(seed):
@@ -94,3 +100,43 @@ def hj_initial(n, seed=SEED_HJ, noise=1e-3):
 def random_lines(shape, seed=0):
     """Generic seeded test field, N(0,1) iid."""
     return rng(seed).standard_normal(shape)
+
+
+def mlp_stencils(n, seed=SEED_MLP, h=2 * np.pi / 4096):
+    """(n, 5) float32 raw stencils: a quarter each of smooth samples
+    a sin(k x + phi) + c, the same plus 1e-3 N(0,1) noise, kinks
+    a |x - x0| + c and jumps a [x > x0] + c, x on five nodes spaced h (smooth)
+    or 1 (kinks, jumps)."""
+    g = rng(seed)
+    q = n // 4
+    kinds = np.repeat(np.arange(4), [q, q, q, n - 3 * q])
+    g.shuffle(kinds)
+    j = np.arange(-2, 3, dtype=np.float64)
+    a = g.uniform(0.5, 2.0, size=(n, 1)) * g.choice([-1.0, 1.0], size=(n, 1))
+    c = g.uniform(-2.0, 2.0, size=(n, 1))
+    k = g.uniform(0.5, 4.0, size=(n, 1))
+    phi = g.uniform(0.0, 2 * np.pi, size=(n, 1))
+    x0 = g.uniform(-2.0, 2.0, size=(n, 1))
+    noise = 1e-3 * g.standard_normal((n, 5))
+    smooth = a * np.sin(k * h * j[None, :] + phi) + c
+    out = np.where((kinds == 0)[:, None], smooth, 0.0)
+    out = np.where((kinds == 1)[:, None], smooth + noise, out)
+    out = np.where((kinds == 2)[:, None], a * np.abs(j[None, :] - x0) + c, out)
+    out = np.where((kinds == 3)[:, None], a * (j[None, :] > x0) + c, out)
+    return out.astype(np.float32)
+
+
+def mlp_initial_params(seed=SEED_MLP):
+    """1347 FP32 network parameters (order W1 32x5, b1, W2 32x32, b2, W3 3x32,
+    b3): weights N(0, 2/fan_in) (last layer N(0, 1/fan_in)), biases zero."""
+    g = rng(seed)
+    w1 = g.standard_normal((32, 5)) * np.sqrt(2.0 / 5)
+    w2 = g.standard_normal((32, 32)) * np.sqrt(2.0 / 32)
+    w3 = g.standard_normal((3, 32)) * np.sqrt(1.0 / 32)
+    return np.concatenate([w1.ravel(), np.zeros(32), w2.ravel(), np.zeros(32), w3.ravel(),
+                           np.zeros(3)]).astype(np.float32)
+
+
+def mlp_positions(count, nx, ny, seed=SEED_MLP):
+    """`count` flat indices drawn uniformly from an ny x nx grid (int64)."""
+    return rng(seed).integers(0, nx * ny, size=count, dtype=np.int64)
