@@ -175,14 +175,39 @@ int phys_host(int e) {
 }
 
 // Builds the kernel arguments for sum_{p<=P} D_mode^p along `ax` with alpha.
+int device_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
+  }
+  return sms;
+}
+
+// Points per lane for a line of n points: the largest of 16, 8, 4 whose
+// tile fits the line exactly (n = 32 * E * nwl, nwl <= 16 warps), else 16
+// with masked (ragged) tiles.
+int choose_E(int n) {
+  for (int E : {16, 8, 4})
+    if (n % (32 * E) == 0 && n / (32 * E) <= kMaxThreads / 32) return E;
+  return kE;
+}
+
+// E = 0: the planner chooses E and, for grids with few lines, fewer lines per
+// CTA so that at least two CTAs per SM are launched.  E != 0: that E and the
+// full-CTA tile shape (the batched kernel's tiles).
 molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, double alpha, Plan* out,
-                      int E = kE) {
+                      int E = 0) {
   SweepArgs& a = out->a;
   std::memset(&a, 0, sizeof(a));
   out->ax = ax;
   out->use_tma = false;
   a.g = geom(p, ax);
   const int n = a.g.n;
+  const bool auto_shape = E == 0;
+  if (auto_shape) E = choose_E(n);
+  a.E = E;
   a.bc = p.d.bc[ax];
   a.mode = mode;
   a.P = P;
@@ -222,6 +247,8 @@ molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, do
   while (Wp * 2 <= W) Wp *= 2;
   W = Wp;
   while (W > 1 && (long long)W / 2 >= a.g.nlines) W /= 2;
+  if (auto_shape)
+    while (W > 1 && (a.g.nlines + W - 1) / W < 2LL * device_sms()) W /= 2;
   const int cap = nwl * 32 * E;
   int LS = (E == 16 ? phys<16>(cap + 3) : (E == 8 ? phys<8>(cap + 3) : phys<4>(cap + 3))) + 1;
   LS = (LS + 31) / 32 * 32 + (W < 32 ? 32 / W : 1);
@@ -252,6 +279,7 @@ void plan_tma(const Problem& p, int ax, const void* in, size_t in_bytes, Plan* p
   pl->use_tma = false;
   SweepArgs& a = pl->a;
   if (!exact_fit(a)) return;
+  if (plan_E(a) != kE) return;   // the TMA kernel runs 16 points per lane
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return;
   if (reinterpret_cast<uintptr_t>(in) & 15) return;

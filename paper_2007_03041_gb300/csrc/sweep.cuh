@@ -73,6 +73,7 @@ struct LineGeom {
 struct SweepArgs {
   LineGeom g;
   int W, nwl, LS;     // lines per CTA, warps per line, shared line stride (elements)
+  int E;              // points per lane of the plain kernel (16, 8 or 4; others mean 16)
   int bc;             // 0 periodic, 1 Dirichlet
   int mode;           // Mode
   int P;
@@ -81,7 +82,7 @@ struct SweepArgs {
   double sub[3][4];   // WENO substencil weights (5-point rule)
   double d[3];        // linear weights
   double q;           // e^{-nu}
-  double qE;          // e^{-nu kE}
+  double qE;          // e^{-nu E}
   double invq;        // e^{+nu}
   double inv1mmu;     // 1/(1-mu)
   double mu;          // e^{-alpha(b-a)}
@@ -586,7 +587,11 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
       for (int j = 0; j < 3; ++j) sub[r][j] = pick<T>(a.sub[r][j], a.subf[r][j]);
     }
   }
-  if constexpr (WL) {
+  // lines owned by one warp (nwl == 1) need CTA barriers only around the
+  // vectorised boundary solve: ghosts, write-backs and the final store of a
+  // line are warp-local
+  const bool own = nwl == 1;
+  if (WL || own) {
     warp_fill_ghosts<T, E>(a, buf, lane);
     __syncwarp();
   } else {
@@ -801,7 +806,7 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
       }
     }
     if (p + 1 < a.P) {
-      if constexpr (WL) {
+      if (WL || own) {
         __syncwarp();
 #pragma unroll
         for (int k = 0; k < E; ++k)
@@ -821,7 +826,7 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
     }
   }
 
-  if constexpr (WL) __syncwarp(); else __syncthreads();
+  if (WL || own) __syncwarp(); else __syncthreads();
 #pragma unroll
   for (int k = 0; k < E; ++k)
     if (RAGGED ? e0 + k < n : true) cbase[chunk_off<E>(k)] = S[k];
@@ -985,7 +990,7 @@ __device__ __forceinline__ void publish_speed(const SweepArgs& a, double rmax) {
 }
 
 // One tile per CTA, plain coalesced loads (any size / alignment).
-template <typename T, typename TIN, typename TST, int JQ, int EPI, bool RAGGED>
+template <typename T, typename TIN, typename TST, int JQ, int EPI, bool RAGGED, int E = kE>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) sweep_kernel(const SweepArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   size_t used;
@@ -995,13 +1000,13 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) sweep_kernel(const Sw
   const long long line0 = (long long)blockIdx.x * a.W;
   const int warp = threadIdx.x >> 5, lw = warp / a.nwl;
   const int tl = (warp - lw * a.nwl) * 32 + (threadIdx.x & 31);
-  load_tile<T, TIN>(a, static_cast<const TIN*>(a.in), lines, line0, lw, tl);
+  load_tile<T, TIN, E>(a, static_cast<const TIN*>(a.in), lines, line0, lw, tl);
   __syncthreads();
-  const double rmax = compute_lines_any<T, JQ, RAGGED>(a, sm, line0 + lw < a.g.nlines);
+  const double rmax = compute_lines_any<T, JQ, RAGGED, E>(a, sm, line0 + lw < a.g.nlines);
   publish_speed<EPI>(a, rmax);
   const double dt = hj_dt<EPI>(a);
   if (EPI == EPI_HJ_Y && blockIdx.x == 0 && threadIdx.x == 0 && a.t_dev) *a.t_dev += dt;
-  epilogue_tile<T, TST, EPI>(a, lines, line0, dt);
+  epilogue_tile<T, TST, EPI, E>(a, lines, line0, dt);
 }
 
 }  // namespace molt

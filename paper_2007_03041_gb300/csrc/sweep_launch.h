@@ -23,8 +23,11 @@ template <typename T, typename TIN, typename TST, int JQ, int EPI>
 cudaError_t launch_sweep(const SweepArgs& a, const TmaPlan* tma, int grid, int block, size_t smem,
                          cudaStream_t s);
 
-// Exact-fit lines (n a multiple of 32*kE*nwl) run the unmasked kernels.
-inline bool exact_fit(const SweepArgs& a) { return a.g.n == a.nwl * 32 * kE; }
+// Points per lane of a plan (16 unless the planner chose 8 or 4).
+inline int plan_E(const SweepArgs& a) { return a.E == 8 || a.E == 4 ? a.E : kE; }
+
+// Exact-fit lines (n = 32*E*nwl) run the unmasked kernels.
+inline bool exact_fit(const SweepArgs& a) { return a.g.n == a.nwl * 32 * plan_E(a); }
 
 #define MOLT_DEFINE_LAUNCH                                                                       \
   template <typename T, typename TIN, typename TST, int JQ, int EPI>                             \
@@ -53,14 +56,19 @@ inline bool exact_fit(const SweepArgs& a) { return a.g.n == a.nwl * 32 * kE; }
       return cudaGetLastError();                                                                 \
     }                                                                                            \
     const bool fit = exact_fit(a);                                                               \
-    auto k = fit ? &sweep_kernel<T, TIN, TST, JQ, EPI, false>                                    \
-                 : &sweep_kernel<T, TIN, TST, JQ, EPI, true>;                                    \
-    static bool configured[2] = {false, false};                                                  \
-    if (!configured[fit]) {                                                                      \
+    const int ei = plan_E(a) == 16 ? 0 : (plan_E(a) == 8 ? 1 : 2);                               \
+    using KFn = void (*)(SweepArgs);                                                             \
+    static const KFn kfn[3][2] = {                                                               \
+        {&sweep_kernel<T, TIN, TST, JQ, EPI, true, 16>, &sweep_kernel<T, TIN, TST, JQ, EPI, false, 16>}, \
+        {&sweep_kernel<T, TIN, TST, JQ, EPI, true, 8>, &sweep_kernel<T, TIN, TST, JQ, EPI, false, 8>},   \
+        {&sweep_kernel<T, TIN, TST, JQ, EPI, true, 4>, &sweep_kernel<T, TIN, TST, JQ, EPI, false, 4>}};  \
+    const KFn k = kfn[ei][fit ? 1 : 0];                                                          \
+    static bool configured[3][2] = {};                                                           \
+    if (!configured[ei][fit]) {                                                                  \
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
                                            200 * 1024);                                          \
       if (e != cudaSuccess) return e;                                                            \
-      configured[fit] = true;                                                                    \
+      configured[ei][fit] = true;                                                                \
     }                                                                                            \
     k<<<grid, block, smem, s>>>(a);                                                              \
     return cudaGetLastError();                                                                   \
