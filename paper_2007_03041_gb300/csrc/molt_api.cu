@@ -188,8 +188,11 @@ int device_sms() {
 // Points per lane for a line of n points: the largest of 16, 8, 4 whose
 // tile fits the line exactly (n = 32 * E * nwl, nwl <= 16 warps), else 16
 // with masked (ragged) tiles.
+#ifndef MOLT_PREFER_E
+#define MOLT_PREFER_E 16
+#endif
 int choose_E(int n) {
-  for (int E : {16, 8, 4})
+  for (int E : {MOLT_PREFER_E, 16, 8, 4})
     if (n % (32 * E) == 0 && n / (32 * E) <= kMaxThreads / 32) return E;
   return kE;
 }
@@ -660,6 +663,12 @@ molt_status heat_step(molt_ctx* c, Problem& p, void* u) {
   return MOLT_OK;
 }
 
+// Mixed precision: the FP64 leapfrog update runs as its own streaming kernel
+// after the last axis (default), or, with MOLT_WAVE_FUSED_UPDATE=1, in the
+// last sweep's epilogue.
+#ifndef MOLT_WAVE_FUSED_UPDATE
+#define MOLT_WAVE_FUSED_UPDATE 0
+#endif
 molt_status wave_step(molt_ctx* c, Problem& p, void* cur, void* prev, bool from_rest, bool in_place_variant) {
   const double alpha = step_alpha(p);
   for (int ax = 0; ax < p.d.ndim; ++ax) {
@@ -670,11 +679,13 @@ molt_status wave_step(molt_ctx* c, Problem& p, void* cur, void* prev, bool from_
     pl.a.acc = p.acc;
     int epi;
     const bool last = ax + 1 == p.d.ndim;
-    if (!last || p.shadow) {
+    const bool split_update = p.shadow && !MOLT_WAVE_FUSED_UPDATE;
+    if (!last || split_update) {
       epi = ax == 0 ? EPI_ACC_SET : EPI_ACC_ADD;
     } else {
       epi = EPI_WAVE_FINAL;
       if (p.d.ndim == 1) pl.a.acc = nullptr;
+      pl.a.shadow = p.shadow;
       pl.a.un = cur;
       pl.a.us = prev;
       pl.a.coefS = -p.d.beta * p.d.beta;
@@ -687,7 +698,7 @@ molt_status wave_step(molt_ctx* c, Problem& p, void* cur, void* prev, bool from_
       }
     }
     if ((st = run(c, p, epi, pl)) != MOLT_OK) return st;
-    if (last && p.shadow) {
+    if (last && split_update) {
       molt_ctx::Rec rec;
       record_begin(c, &rec, MOLT_KERNEL_UPDATE);
       wave_update_kernel<<<stream_grid(p.total), 256, 0, c->stream>>>(

@@ -38,10 +38,16 @@ def rng(seed):
     return np.random.Generator(np.random.PCG64(seed))
 
 
-def heat_modes(n, seed=SEED_HEAT, nmodes=8, kmax=8):
+def heat_mode_params(seed=SEED_HEAT, nmodes=8, kmax=8):
+    """Wavenumbers (nmodes x 2: kx, ky) and amplitudes of ``heat_modes``."""
     g = rng(seed)
     k = g.integers(1, kmax + 1, size=(nmodes, 2))
     a = g.standard_normal(nmodes)
+    return k, a
+
+
+def heat_modes(n, seed=SEED_HEAT, nmodes=8, kmax=8):
+    k, a = heat_mode_params(seed, nmodes, kmax)
     x = np.arange(n) / n
     u = np.zeros((n, n))          # [y][x]
     for m in range(nmodes):
