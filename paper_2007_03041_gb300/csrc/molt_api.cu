@@ -307,16 +307,26 @@ void plan_tma(const Problem& p, int ax, const void* in, size_t in_bytes, Plan* p
     r = enc(&map, dt, 2, const_cast<void*>(in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   } else {
-    if ((W * in_bytes) % 16 != 0 || nx % W != 0) return;
+    // boxes of bw >= W columns starting on a 16-byte boundary (tiles of
+    // fewer than 16 bytes of lines load a wider box and use part of it)
+    tg.xalign = int(16 / in_bytes);
+    if (nx % W != 0) return;
+    if (W < tg.xalign) {
+      if (nx % tg.xalign != 0) return;
+      tg.bw = tg.xalign;
+    } else {
+      if (W % tg.xalign != 0) return;
+      tg.bw = W;
+    }
     tg.kind = ax == 1 ? 1 : 2;
     cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(ny), cuuint64_t(nz)};
     cuuint64_t strides[2] = {cuuint64_t(nx * in_bytes), cuuint64_t(nx * ny * in_bytes)};
-    cuuint32_t box[3] = {cuuint32_t(W), ax == 1 ? cuuint32_t(tg.box_p) : 1u, ax == 2 ? cuuint32_t(tg.box_p) : 1u};
+    cuuint32_t box[3] = {cuuint32_t(tg.bw), ax == 1 ? cuuint32_t(tg.box_p) : 1u, ax == 2 ? cuuint32_t(tg.box_p) : 1u};
     r = enc(&map, dt, 3, const_cast<void*>(in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   }
   if (r != CUDA_SUCCESS) return;
-  tg.tx_bytes = unsigned(size_t(tg.nbox) * tg.box_p * W * in_bytes);
+  tg.tx_bytes = unsigned(size_t(tg.nbox) * tg.box_p * (tg.kind == 0 ? W : tg.bw) * in_bytes);
   const size_t bar_off = (pl->smem + 15) & ~size_t(15);
   const size_t stage_off = (bar_off + 16 + 127) & ~size_t(127);
   const size_t total = stage_off + size_t(tg.tx_bytes);

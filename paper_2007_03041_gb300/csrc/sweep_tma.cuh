@@ -26,8 +26,22 @@ struct TmaGeom {
   int kind;       // 0: contiguous rows (2-D map {n, rows}); 1: y lines (3-D);
                   // 2: z lines (3-D)
   int nx;         // x extent (strided kinds)
+  int bw;         // strided kinds: box columns (>= W, a 16-byte multiple)
+  int xalign;     // strided kinds: elements per 16 bytes (box x start alignment)
   unsigned int tx_bytes;   // bytes per tile
 };
+
+// Strided kinds: the tile's first line sits at column x0 of its row; the box
+// starts at x0 rounded down to a 16-byte boundary (a TMA requirement on the
+// innermost coordinate), so the tile's lines are columns off..off+W-1 of the
+// box.
+__device__ __forceinline__ void strided_origin(const TmaGeom& tg, long long line0, int* hi, int* xbox, int* off) {
+  const unsigned int l0 = unsigned(line0), nxu = unsigned(tg.nx);
+  *hi = int(l0 / nxu);
+  const int x0 = int(l0 - unsigned(*hi) * nxu);
+  *xbox = x0 & ~(tg.xalign - 1);
+  *off = x0 - *xbox;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -95,15 +109,16 @@ template <typename TIN>
 __device__ __forceinline__ void issue_tile(const SweepArgs& a, const TmaGeom& tg, const CUtensorMap* map, TIN* stage,
                                            long long line0, uint64_t* bar) {
   mbar_expect_tx(bar, tg.tx_bytes);
-  const int boxel = tg.box_p * a.W;
   if (tg.kind == 0) {
+    const int boxel = tg.box_p * a.W;
     for (int b = 0; b < tg.nbox; ++b) tma_load_2d(stage + b * boxel, map, b * tg.box_p, int(line0), bar);
   } else {
-    const unsigned int l0 = unsigned(line0), nxu = unsigned(tg.nx);
-    const int hi = int(l0 / nxu), x0 = int(l0 - unsigned(hi) * nxu);
+    const int boxel = tg.box_p * tg.bw;
+    int hi, xbox, off;
+    strided_origin(tg, line0, &hi, &xbox, &off);
     for (int b = 0; b < tg.nbox; ++b) {
-      if (tg.kind == 1) tma_load_3d(stage + b * boxel, map, x0, b * tg.box_p, hi, bar);
-      else tma_load_3d(stage + b * boxel, map, x0, hi, b * tg.box_p, bar);
+      if (tg.kind == 1) tma_load_3d(stage + b * boxel, map, xbox, b * tg.box_p, hi, bar);
+      else tma_load_3d(stage + b * boxel, map, xbox, hi, b * tg.box_p, bar);
     }
   }
 }
@@ -168,17 +183,19 @@ __device__ __forceinline__ void transpose_tile(const SweepArgs& a, const TmaGeom
       }
     }
   } else {
-    // stage: [p][W]
+    // stage: [p][bw], the tile's lines in columns off..off+W-1
+    int hi, xbox, off;
+    strided_origin(tg, line0, &hi, &xbox, &off);
     const int w = threadIdx.x % W;
     const int prow = blockDim.x / W;
     int p = threadIdx.x / W;
-    const TIN* src = stage + p * W + w;
+    const TIN* src = stage + p * tg.bw + off + w;
     T* dst = lines + w * a.LS + phys(p);
     const int dstep = prow + prow / kE;
 #pragma unroll 8
     for (; p < n; p += prow) {
       *dst = cvt<T>(*src);
-      src += prow * W;
+      src += prow * tg.bw;
       dst += dstep;
     }
   }

@@ -58,6 +58,21 @@ def test_tma_sweep_matches_oracle_and_plain(prec, bc):
         assert rel_l2(tma, plain) < 1e-13 * (1 if prec == M.PREC_F64 else 1e6), (shape, axis)
 
 
+# Long strided lines whose tiles hold fewer than 16 bytes of lines (one or two
+# FP32 lines, one FP64 line): the TMA box is widened to a 16-byte-aligned
+# column group and the tile's lines are picked out of it.
+LONG = [((4096, 1280), 1, M.PREC_F32), ((8192, 40), 1, M.PREC_F32), ((4096, 2, 640), 2, M.PREC_F32),
+        ((8192, 10), 1, M.PREC_F64)]
+
+
+@pytest.mark.parametrize("shape,axis,prec", LONG)
+def test_tma_long_strided_lines_with_narrow_tiles(shape, axis, prec):
+    tma, plain, want = apply_both(shape, axis, M.OP_0, 1, 0.5, M.BC_PERIODIC, 6, prec)
+    assert rel_l2(tma, want) < tol_for(prec)
+    assert rel_l2(plain, want) < tol_for(prec)
+    assert rel_l2(tma, plain) < 1e-13 * (1 if prec == M.PREC_F64 else 1e6)
+
+
 @pytest.mark.parametrize("op", [M.OP_L, M.OP_R])
 def test_tma_wenoz_one_sided(op):
     tma, plain, want = apply_both((64, 512), 0, op, 1, 2.0 / 3.0, M.BC_PERIODIC, 5, M.PREC_F32, M.W_WENOZ)
