@@ -13,6 +13,7 @@
 #pragma once
 
 #include "sweep.cuh"
+#include "sweep_tma.cuh"
 
 namespace molt {
 
@@ -102,6 +103,30 @@ __device__ __forceinline__ void batch_tile(const SweepArgs& a, const TileSmem& s
   __syncthreads();
 }
 
+// L2 prefetch of a tile's sweep input (and, for the y phase, of the
+// accumulator its epilogue reads): issued for the CTA's next work item
+// before the current one is computed, so that the plain loads of the next
+// tile hit L2.  One request per 128-byte segment (contiguous lines) or per
+// row of the tile (strided lines).
+__device__ __forceinline__ void prefetch_tile(const SweepArgs& a, long long line0, int ax) {
+  const LineGeom& g = a.g;
+  const int n = g.n, W = a.W;
+  const char* ops[2] = {static_cast<const char*>(a.in), ax == 1 ? static_cast<const char*>(a.acc) : nullptr};
+  for (int o = 0; o < 2; ++o) {
+    if (!ops[o]) continue;
+    if (a.contiguous) {
+      const int nseg = (n + 31) / 32;
+      for (int t = threadIdx.x; t < W * nseg; t += blockDim.x) {
+        const int w = t / nseg, sg = t - w * nseg;
+        if (line0 + w < g.nlines) prefetch_l2(ops[o] + (line_base(g, line0 + w) + 32LL * sg) * 4);
+      }
+    } else if (line0 < g.nlines) {
+      const long long b0 = line_base(g, line0);
+      for (int q = threadIdx.x; q < n; q += blockDim.x) prefetch_l2(ops[o] + (b0 + q * g.stride) * 4);
+    }
+  }
+}
+
 __device__ __forceinline__ int find_problem(const BatchParams& p, long long item, int ax) {
   int lo = 0, hi = p.nprob - 1;
   while (lo < hi) {
@@ -123,7 +148,7 @@ __device__ __forceinline__ int find_update(const BatchParams& p, long long chunk
 __global__ void __launch_bounds__(512, 1) batch_heat_kernel(const BatchParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SweepArgs sa;
-  __shared__ int s_prob, s_tile;
+  __shared__ int s_prob, s_tile, s_nprob, s_ntile;
   static const double rk[3][2] = {{0.0, 1.0}, {0.75, 0.25}, {1.0 / 3.0, 2.0 / 3.0}};
   bool first = true;
   for (int s = 0; s < p.stages; ++s) {
@@ -133,8 +158,15 @@ __global__ void __launch_bounds__(512, 1) batch_heat_kernel(const BatchParams p)
           if (threadIdx.x == 0) {
             s_prob = find_problem(p, item, ax);
             s_tile = int(item - p.sweeps[s_prob * 2 + ax].first_item);
+            const long long nx = item + gridDim.x;
+            s_nprob = nx < p.items[ax] ? find_problem(p, nx, ax) : -1;
+            if (s_nprob >= 0) s_ntile = int(nx - p.sweeps[s_nprob * 2 + ax].first_item);
           }
           __syncthreads();
+          if (s_nprob >= 0) {
+            const SweepArgs& na = p.sweeps[s_nprob * 2 + ax].a;
+            prefetch_tile(na, (long long)s_ntile * na.W, ax);
+          }
           const BatchSweep* bs = p.sweeps + s_prob * 2 + ax;
           const int* src = reinterpret_cast<const int*>(&bs->a);
           int* dst = reinterpret_cast<int*>(&sa);
