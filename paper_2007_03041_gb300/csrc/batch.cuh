@@ -48,7 +48,66 @@ struct BatchParams {
   int* status;
   long long wait_limit;       // cycles
   int skip_arrive;            // test hook: CTA 0 never arrives at the first barrier
+  unsigned int stage_off;     // shared-memory offset of the tile staging buffer
 };
+
+// Staging buffer of one tile's raw input (W lines x n points, FP32): the
+// asynchronous copy of a CTA's next tile lands here while the current tile
+// is computed.
+constexpr int kStageFloats = 512 * 16;   // W * n = 512 * E <= 8192
+
+// 16-byte asynchronous copy through L2 only (.cg): the sweep inputs were
+// written earlier in the same launch by other CTAs, so no L1 line may serve
+// them.
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  const unsigned int d = static_cast<unsigned int>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Issues the copy of the tile starting at line0 into the staging buffer:
+// contiguous lines as [w][n], strided lines as [p][W].  Batch tiles are exact
+// fits (n a multiple of 128, the line count a multiple of W), so contiguous
+// rows and strided rows of W >= 4 floats move as asynchronous 16-byte
+// pieces; rows of one or two floats are loaded synchronously (through L2).
+__device__ __forceinline__ void stage_tile(const SweepArgs& a, float* stage, long long line0) {
+  const float* in = static_cast<const float*>(a.in);
+  const int n = a.g.n, W = a.W;
+  if (a.contiguous) {
+    const int chunks = n >> 2;
+    for (int t = threadIdx.x; t < W * chunks; t += blockDim.x) {
+      const int w = t / chunks, c = t - w * chunks;
+      if (line0 + w < a.g.nlines) cp_async16(stage + w * n + 4 * c, in + line_base(a.g, line0 + w) + 4 * c);
+    }
+  } else if (line0 < a.g.nlines) {
+    const long long b0 = line_base(a.g, line0);
+    if (W >= 4) {
+      const int per = W >> 2;
+      for (int t = threadIdx.x; t < n * per; t += blockDim.x) {
+        const int q = t / per, c = t - q * per;
+        cp_async16(stage + q * W + 4 * c, in + b0 + q * a.g.stride + 4 * c);
+      }
+    } else {
+      for (int t = threadIdx.x; t < n * W; t += blockDim.x) {
+        const int q = t / W, w = t - q * W;
+        stage[t] = __ldcg(in + b0 + q * a.g.stride + w);
+      }
+    }
+  }
+  cp_async_commit();
+}
+
+// Staging layout -> padded per-line layout of the compute core.
+template <int E>
+__device__ __forceinline__ void unstage_tile(const SweepArgs& a, const float* stage, float* lines) {
+  const int n = a.g.n, W = a.W;
+  for (int t = threadIdx.x; t < W * n; t += blockDim.x) {
+    int w, q;
+    if (a.contiguous) { w = t / n; q = t - w * n; } else { q = t / W; w = t - q * W; }
+    lines[w * a.LS + phys<E>(q)] = a.contiguous ? stage[w * n + q] : stage[q * W + w];
+  }
+}
 
 constexpr int kChunk = 4096;  // points per update work item
 
@@ -90,40 +149,38 @@ __device__ __forceinline__ bool grid_sync(const BatchParams& p, bool skip) {
 
 // One (problem, line tile) work item: the tile shape fills the CTA exactly
 // (32 * nwl * W == blockDim.x) and the lines are an exact fit (n = 32*nwl*E).
+// The tile's input is in the staging buffer (copy complete and visible); the
+// copy of the next tile (if any) is issued once the buffer has been read.
 template <int E>
-__device__ __forceinline__ void batch_tile(const SweepArgs& a, const TileSmem& sm, long long line0, int ax) {
+__device__ __forceinline__ void batch_tile(const SweepArgs& a, const TileSmem& sm, long long line0, int ax,
+                                           float* stage, const SweepArgs* next, long long next_line0) {
   float* lines = static_cast<float*>(sm.lines);
   const int warp = threadIdx.x >> 5, lw = warp / a.nwl;
-  const int tl = (warp - lw * a.nwl) * 32 + (threadIdx.x & 31);
-  load_tile<float, float, E, true>(a, static_cast<const float*>(a.in), lines, line0, lw, tl);
+  unstage_tile<E>(a, stage, lines);
   __syncthreads();
+  if (next) stage_tile(*next, stage, next_line0);
   compute_lines_any<float, false, false, E>(a, sm, line0 + lw < a.g.nlines);
   if (ax == 0) epilogue_tile<float, double, EPI_ACC_SET, E, true>(a, lines, line0, 0.0);
   else epilogue_tile<float, double, EPI_ACC_ADD, E, true>(a, lines, line0, 0.0);
   __syncthreads();
 }
 
-// L2 prefetch of a tile's sweep input (and, for the y phase, of the
-// accumulator its epilogue reads): issued for the CTA's next work item
-// before the current one is computed, so that the plain loads of the next
-// tile hit L2.  One request per 128-byte segment (contiguous lines) or per
-// row of the tile (strided lines).
-__device__ __forceinline__ void prefetch_tile(const SweepArgs& a, long long line0, int ax) {
+// L2 prefetch of the accumulator a y-phase tile's epilogue reads, issued for
+// the CTA's next work item before the current one is computed.  One request
+// per 128-byte segment (contiguous lines) or per row (strided lines).
+__device__ __forceinline__ void prefetch_acc(const SweepArgs& a, long long line0) {
   const LineGeom& g = a.g;
   const int n = g.n, W = a.W;
-  const char* ops[2] = {static_cast<const char*>(a.in), ax == 1 ? static_cast<const char*>(a.acc) : nullptr};
-  for (int o = 0; o < 2; ++o) {
-    if (!ops[o]) continue;
-    if (a.contiguous) {
-      const int nseg = (n + 31) / 32;
-      for (int t = threadIdx.x; t < W * nseg; t += blockDim.x) {
-        const int w = t / nseg, sg = t - w * nseg;
-        if (line0 + w < g.nlines) prefetch_l2(ops[o] + (line_base(g, line0 + w) + 32LL * sg) * 4);
-      }
-    } else if (line0 < g.nlines) {
-      const long long b0 = line_base(g, line0);
-      for (int q = threadIdx.x; q < n; q += blockDim.x) prefetch_l2(ops[o] + (b0 + q * g.stride) * 4);
+  const char* acc = static_cast<const char*>(a.acc);
+  if (a.contiguous) {
+    const int nseg = (n + 31) / 32;
+    for (int t = threadIdx.x; t < W * nseg; t += blockDim.x) {
+      const int w = t / nseg, sg = t - w * nseg;
+      if (line0 + w < g.nlines) prefetch_l2(acc + (line_base(g, line0 + w) + 32LL * sg) * 4);
     }
+  } else if (line0 < g.nlines) {
+    const long long b0 = line_base(g, line0);
+    for (int q = threadIdx.x; q < n; q += blockDim.x) prefetch_l2(acc + (b0 + q * g.stride) * 4);
   }
 }
 
@@ -154,6 +211,12 @@ __global__ void __launch_bounds__(512, 1) batch_heat_kernel(const BatchParams p)
   for (int s = 0; s < p.stages; ++s) {
     for (int ax = 0; ax < 2; ++ax) {
       if (p.phase_mask & (1 << ax)) {
+        float* stage = reinterpret_cast<float*>(smem_raw + p.stage_off);
+        if (blockIdx.x < p.items[ax]) {
+          const int p0 = find_problem(p, blockIdx.x, ax);
+          const SweepArgs& a0 = p.sweeps[p0 * 2 + ax].a;
+          stage_tile(a0, stage, (long long)(blockIdx.x - p.sweeps[p0 * 2 + ax].first_item) * a0.W);
+        }
         for (long long item = blockIdx.x; item < p.items[ax]; item += gridDim.x) {
           if (threadIdx.x == 0) {
             s_prob = find_problem(p, item, ax);
@@ -162,11 +225,11 @@ __global__ void __launch_bounds__(512, 1) batch_heat_kernel(const BatchParams p)
             s_nprob = nx < p.items[ax] ? find_problem(p, nx, ax) : -1;
             if (s_nprob >= 0) s_ntile = int(nx - p.sweeps[s_nprob * 2 + ax].first_item);
           }
+          cp_async_wait_all();
           __syncthreads();
-          if (s_nprob >= 0) {
-            const SweepArgs& na = p.sweeps[s_nprob * 2 + ax].a;
-            prefetch_tile(na, (long long)s_ntile * na.W, ax);
-          }
+          const SweepArgs* na = s_nprob >= 0 ? &p.sweeps[s_nprob * 2 + ax].a : nullptr;
+          const long long nline0 = na ? (long long)s_ntile * na->W : 0;
+          if (na && ax == 1) prefetch_acc(*na, nline0);
           const BatchSweep* bs = p.sweeps + s_prob * 2 + ax;
           const int* src = reinterpret_cast<const int*>(&bs->a);
           int* dst = reinterpret_cast<int*>(&sa);
@@ -176,9 +239,9 @@ __global__ void __launch_bounds__(512, 1) batch_heat_kernel(const BatchParams p)
           size_t used;
           const TileSmem sm = carve<float>(smem_raw, sa, &used);
           const long long line0 = (long long)s_tile * sa.W;
-          if (E == 16) batch_tile<16>(sa, sm, line0, ax);
-          else if (E == 8) batch_tile<8>(sa, sm, line0, ax);
-          else batch_tile<4>(sa, sm, line0, ax);
+          if (E == 16) batch_tile<16>(sa, sm, line0, ax, stage, na, nline0);
+          else if (E == 8) batch_tile<8>(sa, sm, line0, ax, stage, na, nline0);
+          else batch_tile<4>(sa, sm, line0, ax, stage, na, nline0);
         }
       }
       const bool skip = first && p.skip_arrive && blockIdx.x == 0;
@@ -194,11 +257,29 @@ __global__ void __launch_bounds__(512, 1) batch_heat_kernel(const BatchParams p)
         const long long i1 = i0 + kChunk < U.total ? i0 + kChunk : U.total;
         const double* us = s == 0 ? U.u : (s == 1 ? U.st1 : U.st2);
         double* dstp = s == 0 ? U.st1 : (s == 1 ? U.st2 : U.u);
-        for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-          const double r = fma(a0, __ldcg(U.u + i), a1 * fma(p.coefS, f2d(__ldcg(U.acc + i)), __ldcg(us + i)));
-          dstp[i] = r;
-          U.copy[i] = d2f(r);
-          bad |= nonfinite(r);
+        // all loads of a thread's points are issued before its stores (the
+        // CTA is the SM's only one, so memory parallelism comes from here)
+        constexpr int kPer = kChunk / 512;
+        double uu[kPer], ss[kPer];
+        float aa[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+          const long long i = i0 + threadIdx.x + (long long)k * blockDim.x;
+          if (i < i1) {
+            uu[k] = __ldcg(U.u + i);
+            ss[k] = __ldcg(us + i);
+            aa[k] = __ldcg(U.acc + i);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+          const long long i = i0 + threadIdx.x + (long long)k * blockDim.x;
+          if (i < i1) {
+            const double r = fma(a0, uu[k], a1 * fma(p.coefS, f2d(aa[k]), ss[k]));
+            dstp[i] = r;
+            U.copy[i] = d2f(r);
+            bad |= nonfinite(r);
+          }
         }
       }
       if (bad) atomicOr(p.status, ST_NONFINITE);

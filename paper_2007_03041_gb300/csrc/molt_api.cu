@@ -854,8 +854,9 @@ molt_status batch_build(molt_ctx* c, void* const* u, const std::vector<int>& sel
   prm.status = c->status_dev;
   prm.wait_limit = c->wait_limit;
   prm.skip_arrive = c->test_skip_arrive ? 1 : 0;
+  prm.stage_off = unsigned((sm + 127) & ~size_t(127));
   *out = prm;
-  *smem = sm;
+  *smem = prm.stage_off + size_t(kStageFloats) * sizeof(float);
   return MOLT_OK;
 }
 
