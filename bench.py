@@ -111,37 +111,6 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def bind_to_gpu_numa_node(device_index):
-    """Restricts this process to the CPUs of the GPU's NUMA node (best
-    effort, before the pinned host buffers are allocated, so that their
-    pages are local to the GPU).  Returns the node or None."""
-    try:
-        import torch
-        bus = torch.cuda.get_device_properties(device_index).pci_bus_id
-    except Exception:
-        return None
-    for cand in (bus, bus.lower(), "0000" + bus[4:] if len(bus) > 4 else bus):
-        path = "/sys/bus/pci/devices/%s/numa_node" % cand.lower()
-        if os.path.exists(path):
-            try:
-                node = int(open(path).read().strip())
-                if node < 0:
-                    return None
-                cpus = set()
-                for part in open("/sys/devices/system/node/node%d/cpulist" % node).read().strip().split(","):
-                    if "-" in part:
-                        lo, hi = part.split("-")
-                        cpus.update(range(int(lo), int(hi) + 1))
-                    elif part:
-                        cpus.add(int(part))
-                if cpus:
-                    os.sched_setaffinity(0, cpus)
-                return node
-            except (OSError, ValueError):
-                return None
-    return None
-
-
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -279,7 +248,6 @@ def run_ours(args):
     # of step k's result run on their own streams, overlapping step k's (or
     # k+1's) sweeps; each step is an independent problem read from the host.
     e2e_steps = 0 if args.no_e2e else max(4, min(args.steps, 8))
-    numa = bind_to_gpu_numa_node(local) if e2e_steps else None
     hu = torch.empty_like(u, device="cpu").pin_memory()
     hup = torch.empty_like(u, device="cpu").pin_memory()
     hout = [torch.empty_like(u, device="cpu").pin_memory() for _ in range(2)]
@@ -331,8 +299,7 @@ def run_ours(args):
     e2e = None if args.no_e2e else {"value": ws * dof * e2e_steps / e2e_s, "unit": UNIT,
                                     "h2d_bytes_per_step": 2 * 8 * dof, "d2h_bytes_per_step": 8 * dof,
                                     "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps,
-                                    "pipelining": "double-buffered H2D/D2H on copy streams",
-                                    "host_numa_node": numa}
+                                    "pipelining": "double-buffered H2D/D2H on copy streams"}
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     # dominant kernel: the largest share of the step's device time
