@@ -149,7 +149,9 @@ typedef enum {
   MOLT_KERNEL_HJ_X = 5,        /* Hamilton-Jacobi: first axes                 */
   MOLT_KERNEL_HJ_Y = 6,        /* Hamilton-Jacobi: last axis + update         */
   MOLT_KERNEL_UPDATE = 7,      /* FP64 state update of the FP32-sweep forms   */
-  MOLT_KERNEL_BATCH = 8        /* one persistent batched heat step            */
+  MOLT_KERNEL_BATCH = 8,       /* one persistent batched heat step            */
+  MOLT_KERNEL_TRANSPOSE = 9    /* state transposes of the 2-D Hamilton-Jacobi
+                                  y pass on long lines                        */
 } molt_kernel_kind;
 
 /* With MOLT_OPT_PROFILE on: synchronises the stream, returns the summed

@@ -31,6 +31,8 @@ struct Problem {
   void* stage1 = nullptr;   // heat RK stages (state type)
   void* stage2 = nullptr;
   void* hx = nullptr;       // HJ H^_x (state type)
+  void* tu = nullptr;       // HJ, transposed y pass: u^T and (H^_x)^T / u^{n+1}^T
+  void* thx = nullptr;
   float* shadow = nullptr;  // FP32 copy of the state the sweeps read (mixed precision)
   int64_t hj_steps = 0;     // HJ steps taken (rotates the speed slots)
   bool hj_lag_ready = false;
@@ -425,6 +427,8 @@ double step_alpha(const Problem& p) {
   return d.beta / (d.cfl * hmin);
 }
 
+bool hj_transposed_y(molt_ctx* c, const Problem& p);
+
 }  // namespace
 
 extern "C" {
@@ -504,6 +508,9 @@ molt_status molt_create(const molt_desc* descs, int count, void* cuda_stream, mo
       ok = ok && cudaMalloc(&p.stage2, sb * tot) == cudaSuccess;
     }
     if (p.d.pde == MOLT_PDE_HJ && p.d.ndim > 1) ok = ok && cudaMalloc(&p.hx, sb * tot) == cudaSuccess;
+    if (ok && hj_transposed_y(c, p)) {
+      ok = cudaMalloc(&p.tu, sb * tot) == cudaSuccess && cudaMalloc(&p.thx, sb * tot) == cudaSuccess;
+    }
     if (is_mixed(p.d) && p.d.pde != MOLT_PDE_HJ) ok = ok && cudaMalloc(&p.shadow, 4 * tot) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
@@ -723,8 +730,68 @@ molt_status wave_step(molt_ctx* c, Problem& p, void* cur, void* prev, bool from_
   return MOLT_OK;
 }
 
+// out[x][y] = in[y][x] for an ny x nx array, through 32 x 32 shared tiles.
+template <typename T>
+__global__ void transpose_kernel(const T* __restrict__ in, T* __restrict__ out, long long ny, long long nx) {
+  __shared__ T tile[32][33];
+  const long long x0 = (long long)blockIdx.x * 32, y0 = (long long)blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const long long y = y0 + j, x = x0 + threadIdx.x;
+    if (y < ny && x < nx) tile[j][threadIdx.x] = in[y * nx + x];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const long long x = x0 + j, y = y0 + threadIdx.x;
+    if (x < nx && y < ny) out[x * ny + y] = tile[threadIdx.x][j];
+  }
+}
+
+molt_status transpose(molt_ctx* c, const Problem& p, const void* in, void* out, long long ny, long long nx) {
+  molt_ctx::Rec rec;
+  record_begin(c, &rec, MOLT_KERNEL_TRANSPOSE);
+  const dim3 grid(unsigned((nx + 31) / 32), unsigned((ny + 31) / 32)), block(32, 8);
+  if (state_bytes(p.d) == 4)
+    transpose_kernel<float><<<grid, block, 0, c->stream>>>(static_cast<const float*>(in), static_cast<float*>(out),
+                                                           ny, nx);
+  else
+    transpose_kernel<double><<<grid, block, 0, c->stream>>>(static_cast<const double*>(in),
+                                                            static_cast<double*>(out), ny, nx);
+  record_end(c, &rec);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MOLT_OK : cuda_fail(c, e, "transpose");
+}
+
+// 2-D Hamilton-Jacobi: y lines long enough that a tile holds less than 32
+// bytes of them (four FP32 lines of 2048 points, two of 4096, one of 8192)
+// make the y pass a strided gather and scatter of a few bytes per row.  Such
+// problems run the y pass on the transposed state instead, where the lines
+// are rows.
+bool hj_transposed_y(molt_ctx* c, const Problem& p) {
+  if (p.d.pde != MOLT_PDE_HJ || p.d.ndim != 2) return false;
+  Problem q = p;                     // the tile shape does not depend on the weights
+  q.d.weights = MOLT_W_WENOZ;
+  Plan pl;
+  if (plan_axis(c, q, 1, MODE_RL, 1, step_alpha(q), &pl) != MOLT_OK) {
+    c->err.clear();
+    return false;
+  }
+  return size_t(pl.a.W) * state_bytes(p.d) < 32;
+}
+
+// The problem with x and y exchanged (the transposed state's geometry).
+Problem transposed(const Problem& p) {
+  Problem t = p;
+  std::swap(t.n[0], t.n[1]);
+  std::swap(t.h[0], t.h[1]);
+  std::swap(t.d.n[0], t.d.n[1]);
+  std::swap(t.d.lo[0], t.d.lo[1]);
+  std::swap(t.d.hi[0], t.d.hi[1]);
+  std::swap(t.d.bc[0], t.d.bc[1]);
+  return t;
+}
+
 molt_status hj_pass(molt_ctx* c, Problem& p, int idx, void* u, int ax, int epi, unsigned long long* speed,
-                    const unsigned long long* lag, void* hx) {
+                    const unsigned long long* lag, void* hx, void* dst = nullptr) {
   Plan pl;
   molt_status st = plan_axis(c, p, ax, MODE_RL, 1, step_alpha(p), &pl);
   if (st != MOLT_OK) return st;
@@ -733,7 +800,7 @@ molt_status hj_pass(molt_ctx* c, Problem& p, int idx, void* u, int ax, int epi, 
   pl.a.in = u;
   pl.a.un = u;
   pl.a.out = hx;
-  pl.a.dst = u;
+  pl.a.dst = dst ? dst : u;
   pl.a.speed = speed;
   pl.a.lag = lag;
   pl.a.cfl_h = p.d.cfl * hmin;
@@ -745,12 +812,22 @@ molt_status hj_pass(molt_ctx* c, Problem& p, int idx, void* u, int ax, int epi, 
 molt_status hj_step(molt_ctx* c, Problem& p, int idx, void* u) {
   unsigned long long* slots = c->speed_dev + 2 * idx;
   cudaError_t e;
+  const bool ty = p.tu && p.thx && hj_transposed_y(c, p);
+  Problem pt;
+  if (ty) pt = transposed(p);
+  const long long ny = p.n[1], nx = p.n[0];
   if (!p.hj_lag_ready) {
     // speeds of u^0 serve as the lagged speeds of the first step (Algorithm 1)
     if ((e = cudaMemsetAsync(slots + 1, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "memset");
     for (int ax = 0; ax < p.d.ndim; ++ax) {
-      molt_status st = hj_pass(c, p, idx, u, ax, EPI_HJ_X, slots + 1, nullptr, nullptr);
+      molt_status st;
+      if (ty && ax == 1) {
+        if ((st = transpose(c, p, u, p.tu, ny, nx)) != MOLT_OK) return st;
+        st = hj_pass(c, pt, idx, p.tu, 0, EPI_HJ_X, slots + 1, nullptr, nullptr);
+      } else {
+        st = hj_pass(c, p, idx, u, ax, EPI_HJ_X, slots + 1, nullptr, nullptr);
+      }
       if (st != MOLT_OK) return st;
     }
     p.hj_lag_ready = true;
@@ -764,7 +841,17 @@ molt_status hj_step(molt_ctx* c, Problem& p, int idx, void* u) {
   for (int ax = 0; ax < p.d.ndim; ++ax) {
     const bool last = ax + 1 == p.d.ndim;
     const int epi = last ? EPI_HJ_Y : EPI_HJ_X;
-    molt_status st = hj_pass(c, p, idx, u, ax, epi, slot, lag, p.d.ndim > 1 ? p.hx : nullptr);
+    molt_status st;
+    if (ty && ax == 1) {
+      // y pass on the transposed state: rows of u^T; H^_x^T is read and
+      // u^{n+1 T} written in its place, then transposed back into u
+      if ((st = transpose(c, p, u, p.tu, ny, nx)) != MOLT_OK) return st;
+      if ((st = transpose(c, p, p.hx, p.thx, ny, nx)) != MOLT_OK) return st;
+      if ((st = hj_pass(c, pt, idx, p.tu, 0, epi, slot, lag, p.thx, p.thx)) != MOLT_OK) return st;
+      st = transpose(c, p, p.thx, u, nx, ny);
+    } else {
+      st = hj_pass(c, p, idx, u, ax, epi, slot, lag, p.d.ndim > 1 ? p.hx : nullptr);
+    }
     if (st != MOLT_OK) return st;
   }
   p.hj_steps++;
@@ -1151,6 +1238,8 @@ molt_status molt_destroy(molt_ctx* c) {
     cudaFree(p.stage1);
     cudaFree(p.stage2);
     cudaFree(p.hx);
+    cudaFree(p.tu);
+    cudaFree(p.thx);
     cudaFree(p.shadow);
   }
   if (c->batch.graph) cudaGraphExecDestroy(c->batch.graph);

@@ -26,7 +26,7 @@ MLP_PARAMS = 1347
 MLP_BLOB_BYTES = 3728
 OPT_TMA, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_TEST_SKIP_ARRIVE = 0, 1, 2, 3
 (KERNEL_STORE, KERNEL_ACC_SET, KERNEL_ACC_ADD, KERNEL_HEAT_FINAL, KERNEL_WAVE_FINAL, KERNEL_HJ_X, KERNEL_HJ_Y,
- KERNEL_UPDATE, KERNEL_BATCH) = range(9)
+ KERNEL_UPDATE, KERNEL_BATCH, KERNEL_TRANSPOSE) = range(10)
 
 
 class molt_desc(ctypes.Structure):

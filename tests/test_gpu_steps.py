@@ -134,3 +134,42 @@ def test_nonfinite_state_is_reported():
         assert ei.value.status == M.MOLT_ENONFINITE
     finally:
         M.molt_destroy(ctx)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("nx,ny,prec,transposed", [(256, 4096, M.PREC_F32, True), (4096, 256, M.PREC_F32, False),
+                                                    (64, 4096, M.PREC_F64, True)])
+def test_hj_anisotropic_long_lines(nx, ny, prec, transposed):
+    """Long y lines run the y pass on the transposed state (their tiles would
+    hold fewer than 32 bytes of lines); long x lines do not.  FP64 dt: the
+    speeds are one-sided derivatives alpha*D[u], whose FP64 rounding is
+    amplified by the cancellation in D = u - L^{-1}u, so dt agrees to 1e-10
+    relative."""
+    need_gpu()
+    import torch
+    hx_, hy_ = 2 * np.pi / nx, 2 * np.pi / ny
+    g = workloads.rng(9)
+    x = 2 * np.pi * np.arange(nx) / nx
+    y = 2 * np.pi * np.arange(ny) / ny
+    u0 = -np.cos(x)[None, :] - np.cos(2 * y)[:, None] + 1e-3 * g.standard_normal((ny, nx))
+    d = M.make_desc((nx, ny), lo=[0, 0], hi=[2 * np.pi] * 2, P=1, quad_points=5, weights=M.W_WENOZ, beta=1.0,
+                    pde=M.PDE_HJ, cfl=1.5, dt=0.0, prec=prec)
+    ctx = M.molt_create(d)
+    try:
+        u = to_dev(u0, state_dtype(prec))
+        M.molt_set_option(ctx, M.OPT_PROFILE, 1)
+        t = M.molt_step(ctx, u, None, nsteps=2, t=[0.0])
+        _, ntr = M.molt_profile_read(ctx, M.KERNEL_TRANSPOSE)
+        got = u.double().cpu().numpy()
+    finally:
+        M.molt_destroy(ctx)
+    assert (ntr > 0) == transposed
+    uu = u0.astype(np.float32).astype(np.float64) if prec == M.PREC_F32 else u0
+    dxs = [hy_, hx_]            # numpy axis order: y, x
+    speeds = schemes.hj_initial_speeds(uu, dxs, 1.5, 1.0, 5, "wenoz")
+    tt = 0.0
+    for _ in range(2):
+        uu, dt, speeds = schemes.hj_step(uu, dxs, speeds, 1.5, 1.0, 5, "wenoz")
+        tt += dt
+    assert rel_l2(got, uu) < tol_for(prec)
+    assert abs(t[0] - tt) < (1e-10 if prec == M.PREC_F64 else 1e-4) * tt
