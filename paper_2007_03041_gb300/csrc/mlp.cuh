@@ -166,13 +166,27 @@ struct MlpCache {
   uint32_t a1[2][4], a2[2][4];  // BF16 activations, A layout per k-tile
 };
 
+// GELU of a pair of pre-activations in packed FP32x2 arithmetic (the same
+// formula as gelu(), with 0.5z(1+t) taken as the FMA 0.5z + 0.5z*t), packed
+// as BF16x2.
+__device__ __forceinline__ uint32_t gelu2_pack(float z0, float z1) {
+  const float2 z = make_float2(z0, z1);
+  const float2 zz = __fmul2_rn(z, z);
+  const float2 az = __fmul2_rn(make_float2(kGeluA, kGeluA), z);
+  const float2 v = __fmul2_rn(make_float2(kGeluC, kGeluC), __ffma2_rn(az, zz, z));
+  const float2 t = make_float2(tanh_approx(v.x), tanh_approx(v.y));
+  const float2 hz = __fmul2_rn(make_float2(0.5f, 0.5f), z);
+  const float2 g = __ffma2_rn(hz, t, hz);
+  return pack_bf16(g.x, g.y);
+}
+
 __device__ __forceinline__ void gelu_pack(const float (&z)[4][4], uint32_t (&a)[2][4]) {
 #pragma unroll
   for (int kk = 0; kk < 2; ++kk) {
-    a[kk][0] = pack_bf16(gelu(z[2 * kk][0]), gelu(z[2 * kk][1]));
-    a[kk][1] = pack_bf16(gelu(z[2 * kk][2]), gelu(z[2 * kk][3]));
-    a[kk][2] = pack_bf16(gelu(z[2 * kk + 1][0]), gelu(z[2 * kk + 1][1]));
-    a[kk][3] = pack_bf16(gelu(z[2 * kk + 1][2]), gelu(z[2 * kk + 1][3]));
+    a[kk][0] = gelu2_pack(z[2 * kk][0], z[2 * kk][1]);
+    a[kk][1] = gelu2_pack(z[2 * kk][2], z[2 * kk][3]);
+    a[kk][2] = gelu2_pack(z[2 * kk + 1][0], z[2 * kk + 1][1]);
+    a[kk][3] = gelu2_pack(z[2 * kk + 1][2], z[2 * kk + 1][3]);
   }
 }
 
