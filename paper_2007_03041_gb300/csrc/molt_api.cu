@@ -565,15 +565,35 @@ __global__ void shadow_kernel(const double* __restrict__ in, float* __restrict__
 //          from rest: u^1 = u^0 + coefS/2 * acc            (Taylor start)
 // acc holds sum_d S_{P,d} of the stage input in FP32.  Each also refreshes
 // the FP32 copy the next sweeps read and flags non-finite values.
+constexpr int kUpdPer = 4;   // points per thread and iteration; their loads are issued first
+
 __global__ void heat_update_kernel(const float* __restrict__ acc, const double* un, const double* us, double* dst,
                                    float* __restrict__ shadow, double a0, double a1, double coefS, long long n,
                                    int* status) {
   bool bad = false;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double r = fma(a0, un[i], a1 * fma(coefS, f2d(acc[i]), us[i]));
-    dst[i] = r;
-    shadow[i] = d2f(r);
-    bad |= nonfinite(r);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kUpdPer) {
+    double x[kUpdPer], y[kUpdPer];
+    float w[kUpdPer];
+#pragma unroll
+    for (int k = 0; k < kUpdPer; ++k) {
+      const long long i = i0 + k * stride;
+      if (i < n) {
+        x[k] = un[i];
+        y[k] = us[i];
+        w[k] = acc[i];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kUpdPer; ++k) {
+      const long long i = i0 + k * stride;
+      if (i < n) {
+        const double r = fma(a0, x[k], a1 * fma(coefS, f2d(w[k]), y[k]));
+        dst[i] = r;
+        shadow[i] = d2f(r);
+        bad |= nonfinite(r);
+      }
+    }
   }
   if (bad) atomicOr(status, ST_NONFINITE);
 }
@@ -582,14 +602,32 @@ __global__ void wave_update_kernel(const float* __restrict__ acc, const double* 
                                    double* dst, double* dst2, float* __restrict__ shadow, double coefS,
                                    int from_rest, long long n, int* status) {
   bool bad = false;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double u = un[i];
-    const double w = f2d(acc[i]);
-    const double r = from_rest ? fma(0.5 * coefS, w, u) : fma(coefS, w, fma(2.0, u, -uprev[i]));
-    if (dst2) dst2[i] = u;
-    dst[i] = r;
-    shadow[i] = d2f(r);
-    bad |= nonfinite(r);
+  const double half = 0.5 * coefS;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kUpdPer) {
+    double x[kUpdPer], y[kUpdPer];
+    float w[kUpdPer];
+#pragma unroll
+    for (int k = 0; k < kUpdPer; ++k) {
+      const long long i = i0 + k * stride;
+      if (i < n) {
+        x[k] = un[i];
+        y[k] = from_rest ? 0.0 : uprev[i];
+        w[k] = acc[i];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kUpdPer; ++k) {
+      const long long i = i0 + k * stride;
+      if (i < n) {
+        const double wd = f2d(w[k]);
+        const double r = from_rest ? fma(half, wd, x[k]) : fma(coefS, wd, fma(2.0, x[k], -y[k]));
+        if (dst2) dst2[i] = x[k];
+        dst[i] = r;
+        shadow[i] = d2f(r);
+        bad |= nonfinite(r);
+      }
+    }
   }
   if (bad) atomicOr(status, ST_NONFINITE);
 }
