@@ -925,7 +925,10 @@ struct Epilogue {
 // Applies the epilogue to the tile's W lines in the coalesced mapping, in
 // batches of kEpiBatch points per thread: all operand loads of a batch are
 // issued before its stores.
-constexpr int kEpiBatch = 8;
+#ifndef MOLT_EPI_BATCH
+#define MOLT_EPI_BATCH 8
+#endif
+constexpr int kEpiBatch = MOLT_EPI_BATCH;
 
 template <typename T, typename TST, int EPI, int E = kE, bool CG = false>
 __device__ __forceinline__ void epilogue_tile(const SweepArgs& a, const T* lines, long long line0, double dt) {
