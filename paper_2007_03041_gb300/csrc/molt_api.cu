@@ -551,10 +551,19 @@ molt_status molt_apply_D(molt_ctx* c, int problem, int axis, int op, int P, doub
 
 namespace {
 
-// FP32 copy of an FP64 state (integer-pattern conversion, grid-stride).
+// FP32 copy of an FP64 state (integer-pattern conversion, grid-stride, four
+// points per thread with their loads issued first).
 __global__ void shadow_kernel(const double* __restrict__ in, float* __restrict__ out, long long n) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = d2f(in[i]);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+    double v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (i0 + k * stride < n) v[k] = in[i0 + k * stride];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (i0 + k * stride < n) out[i0 + k * stride] = d2f(v[k]);
+  }
 }
 
 // FP64 state updates of the FP32-sweep (mixed) forms, as streaming kernels:
