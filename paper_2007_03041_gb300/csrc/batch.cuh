@@ -71,26 +71,30 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // fits (n a multiple of 128, the line count a multiple of W), so contiguous
 // rows and strided rows of W >= 4 floats move as asynchronous 16-byte
 // pieces; rows of one or two floats are loaded synchronously (through L2).
+// log2 of a power of two
+__device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
+
 __device__ __forceinline__ void stage_tile(const SweepArgs& a, float* stage, long long line0) {
   const float* in = static_cast<const float*>(a.in);
-  const int n = a.g.n, W = a.W;
+  const int n = a.g.n, W = a.W;          // powers of two in batch tiles
+  const int ln = ilog2(n), lW = ilog2(W);
   if (a.contiguous) {
-    const int chunks = n >> 2;
-    for (int t = threadIdx.x; t < W * chunks; t += blockDim.x) {
-      const int w = t / chunks, c = t - w * chunks;
-      if (line0 + w < a.g.nlines) cp_async16(stage + w * n + 4 * c, in + line_base(a.g, line0 + w) + 4 * c);
+    const int lc = ln - 2;               // 16-byte chunks per line
+    for (int t = threadIdx.x; t < W << lc; t += blockDim.x) {
+      const int w = t >> lc, c = t & ((1 << lc) - 1);
+      if (line0 + w < a.g.nlines) cp_async16(stage + (w << ln) + 4 * c, in + line_base(a.g, line0 + w) + 4 * c);
     }
   } else if (line0 < a.g.nlines) {
     const long long b0 = line_base(a.g, line0);
     if (W >= 4) {
-      const int per = W >> 2;
-      for (int t = threadIdx.x; t < n * per; t += blockDim.x) {
-        const int q = t / per, c = t - q * per;
-        cp_async16(stage + q * W + 4 * c, in + b0 + q * a.g.stride + 4 * c);
+      const int lp = lW - 2;             // 16-byte pieces per row
+      for (int t = threadIdx.x; t < n << lp; t += blockDim.x) {
+        const int q = t >> lp, c = t & ((1 << lp) - 1);
+        cp_async16(stage + (q << lW) + 4 * c, in + b0 + q * a.g.stride + 4 * c);
       }
     } else {
-      for (int t = threadIdx.x; t < n * W; t += blockDim.x) {
-        const int q = t / W, w = t - q * W;
+      for (int t = threadIdx.x; t < n << lW; t += blockDim.x) {
+        const int q = t >> lW, w = t & (W - 1);
         stage[t] = __ldcg(in + b0 + q * a.g.stride + w);
       }
     }
@@ -102,10 +106,17 @@ __device__ __forceinline__ void stage_tile(const SweepArgs& a, float* stage, lon
 template <int E>
 __device__ __forceinline__ void unstage_tile(const SweepArgs& a, const float* stage, float* lines) {
   const int n = a.g.n, W = a.W;
-  for (int t = threadIdx.x; t < W * n; t += blockDim.x) {
-    int w, q;
-    if (a.contiguous) { w = t / n; q = t - w * n; } else { q = t / W; w = t - q * W; }
-    lines[w * a.LS + phys<E>(q)] = a.contiguous ? stage[w * n + q] : stage[q * W + w];
+  const int ln = ilog2(n), lW = ilog2(W);
+  if (a.contiguous) {
+    for (int t = threadIdx.x; t < W << ln; t += blockDim.x) {
+      const int w = t >> ln, q = t & (n - 1);
+      lines[w * a.LS + phys<E>(q)] = stage[t];
+    }
+  } else {
+    for (int t = threadIdx.x; t < n << lW; t += blockDim.x) {
+      const int q = t >> lW, w = t & (W - 1);
+      lines[w * a.LS + phys<E>(q)] = stage[t];
+    }
   }
 }
 
