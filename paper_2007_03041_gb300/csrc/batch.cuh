@@ -120,7 +120,10 @@ __device__ __forceinline__ void unstage_tile(const SweepArgs& a, const float* st
   }
 }
 
-constexpr int kChunk = 4096;  // points per update work item
+#ifndef MOLT_BATCH_CHUNK
+#define MOLT_BATCH_CHUNK 4096
+#endif
+constexpr int kChunk = MOLT_BATCH_CHUNK;  // points per update work item
 
 // Grid barrier with a bounded wait (cooperative launch: all CTAs resident).
 __device__ __forceinline__ bool grid_sync(const BatchParams& p, bool skip) {
