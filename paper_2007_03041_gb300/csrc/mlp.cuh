@@ -252,10 +252,13 @@ __device__ __forceinline__ void wenoz_omega(const float (&w)[5], const float (&d
   float sum = 0.f;
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    om[r] = d[r] * (1.f + tau / (1e-6f + beta[r]));
+    float rc;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rc) : "f"(1e-6f + beta[r]));
+    om[r] = fmaf(d[r] * tau, rc, d[r]);      // d_r (1 + tau/(eps+beta_r))
     sum += om[r];
   }
-  const float inv = 1.f / sum;
+  float inv;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(sum));
 #pragma unroll
   for (int r = 0; r < 3; ++r) om[r] *= inv;
 }

@@ -232,6 +232,16 @@ __device__ __forceinline__ T shfl_down(T v, int d) { return __shfl_down_sync(0xf
 //   beta_0 = s1^2 + 3 s1 s2 + 10/3 s2^2,  beta_1 = s1^2 + s1 s2 + 4/3 s2^2,
 //   beta_2 = s1^2 - s1 s2 + 4/3 s2^2.
 // WENO-Z (Sec. 2.4): w~_r = d_r (1 + tau/(eps+beta_r)), tau = |beta_0-beta_2|.
+// Reciprocal for the nonlinear weights: FP32 takes the hardware
+// approximation (at most 1 ulp; the arguments eps + beta_r and sum_r w~_r are
+// at least 1e-6 and about 1), FP64 the division.
+__device__ __forceinline__ float weight_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double weight_rcp(double x) { return 1.0 / x; }
+
 template <typename T>
 __device__ __forceinline__ T wenoz_integral(const T* w, const T (&sub)[3][3], const T (&d)[3]) {
   T J[3], beta[3];
@@ -250,10 +260,10 @@ __device__ __forceinline__ T wenoz_integral(const T* w, const T (&sub)[3][3], co
   T wt[3], sum = T(0);
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    wt[r] = d[r] * (T(1) + tau / (eps + beta[r]));
+    wt[r] = fma(d[r] * tau, weight_rcp(eps + beta[r]), d[r]);   // d_r (1 + tau/(eps+beta_r))
     sum += wt[r];
   }
-  return (wt[0] * J[0] + wt[1] * J[1] + wt[2] * J[2]) / sum;
+  return (wt[0] * J[0] + wt[1] * J[1] + wt[2] * J[2]) * weight_rcp(sum);
 }
 
 // -------------------------------------------------------------- tile staging
