@@ -777,26 +777,34 @@ molt_status wave_step(molt_ctx* c, Problem& p, void* cur, void* prev, bool from_
   return MOLT_OK;
 }
 
-// out[x][y] = in[y][x] for an ny x nx array, through 32 x 32 shared tiles.
+// out[x][y] = in[y][x] for an ny x nx array, through 64 x 64 shared tiles;
+// each of the 32 x 8 threads moves 16 elements, all loads issued first.
 template <typename T>
 __global__ void transpose_kernel(const T* __restrict__ in, T* __restrict__ out, long long ny, long long nx) {
-  __shared__ T tile[32][33];
-  const long long x0 = (long long)blockIdx.x * 32, y0 = (long long)blockIdx.y * 32;
-  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-    const long long y = y0 + j, x = x0 + threadIdx.x;
-    if (y < ny && x < nx) tile[j][threadIdx.x] = in[y * nx + x];
+  __shared__ T tile[64][65];
+  const long long x0 = (long long)blockIdx.x * 64, y0 = (long long)blockIdx.y * 64;
+  T v[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int j = threadIdx.y + 8 * (k >> 1), cx = threadIdx.x + 32 * (k & 1);
+    const long long y = y0 + j, x = x0 + cx;
+    v[k] = (y < ny && x < nx) ? in[y * nx + x] : T(0);
   }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) tile[threadIdx.y + 8 * (k >> 1)][threadIdx.x + 32 * (k & 1)] = v[k];
   __syncthreads();
-  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-    const long long x = x0 + j, y = y0 + threadIdx.x;
-    if (x < nx && y < ny) out[x * ny + y] = tile[threadIdx.x][j];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int j = threadIdx.y + 8 * (k >> 1), cy = threadIdx.x + 32 * (k & 1);
+    const long long x = x0 + j, y = y0 + cy;
+    if (x < nx && y < ny) out[x * ny + y] = tile[cy][j];
   }
 }
 
 molt_status transpose(molt_ctx* c, const Problem& p, const void* in, void* out, long long ny, long long nx) {
   molt_ctx::Rec rec;
   record_begin(c, &rec, MOLT_KERNEL_TRANSPOSE);
-  const dim3 grid(unsigned((nx + 31) / 32), unsigned((ny + 31) / 32)), block(32, 8);
+  const dim3 grid(unsigned((nx + 63) / 64), unsigned((ny + 63) / 64)), block(32, 8);
   if (state_bytes(p.d) == 4)
     transpose_kernel<float><<<grid, block, 0, c->stream>>>(static_cast<const float*>(in), static_cast<float*>(out),
                                                            ny, nx);
