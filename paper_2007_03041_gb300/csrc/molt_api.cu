@@ -171,11 +171,6 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-int phys_host(int e) {
-  const int ee = e + kG;
-  return ee + (ee >> 4);
-}
-
 // Builds the kernel arguments for sum_{p<=P} D_mode^p along `ax` with alpha.
 int device_sms() {
   static int sms = 0;
