@@ -247,6 +247,16 @@ molt_status molt_mlp_stats(molt_ctx* ctx, int64_t* stencils, int64_t* fallbacks,
  * Synchronous, host only. */
 molt_status molt_weno_linear_weights(double nu, double* d);
 
+/* The quadrature weights the sweeps use (App. C construction, from
+ * exponential moments: a power series for nu <= 1, the integration-by-parts
+ * recurrence above), host only and synchronous.  quad_points 3, 5 or 6;
+ * nu = alpha*h > 0.  c[6]: weights of J_R(x_i) = sum_l c_l v_{i+l} on the
+ * offsets l = -3..2 (zero where the rule has no node).  sub[12] (may be NULL):
+ * substencil weights [r][j] for r = 0..2, node j of substencil r (5-point
+ * rule: offsets -3+r..-1+r, j = 3 zero; 6-point: -3+r..r); d[3] (may be
+ * NULL): the linear weights.  Both zero for the 3-point rule. */
+molt_status molt_quadrature_weights(int quad_points, double nu, double* c, double* sub, double* d);
+
 /* Round FP32 master parameters theta[MOLT_MLP_PARAMS] to the BF16 blob. */
 molt_status molt_mlp_pack(const float* theta, void* blob, void* cuda_stream);
 

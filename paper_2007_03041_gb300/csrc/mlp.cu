@@ -448,6 +448,19 @@ molt_status molt_weno_linear_weights(double nu, double* d) {
   return MOLT_OK;
 }
 
+molt_status molt_quadrature_weights(int quad_points, double nu, double* c, double* sub, double* d) {
+  if (!c || !(nu > 0) || !std::isfinite(nu)) return MOLT_EINVAL;
+  QuadTable qt;
+  if (!build_quadrature(quad_points, nu, &qt)) return MOLT_EINVAL;
+  for (int i = 0; i < 6; ++i) c[i] = qt.c[i];
+  for (int r = 0; r < 3; ++r) {
+    for (int j = 0; j < 4; ++j)
+      if (sub) sub[4 * r + j] = quad_points == 3 ? 0.0 : qt.sub[r][j];
+    if (d) d[r] = quad_points == 3 ? 0.0 : qt.d[r];
+  }
+  return MOLT_OK;
+}
+
 molt_status molt_mlp_pack(const float* theta, void* blob, void* cuda_stream) {
   if (!theta || !blob || !aligned16(theta) || !aligned16(blob)) return MOLT_EINVAL;
   mlp_pack_kernel<<<1, 512, 0, static_cast<cudaStream_t>(cuda_stream)>>>(theta, static_cast<MlpBlob*>(blob));

@@ -21,7 +21,7 @@ W_LINEAR, W_WENOZ, W_LEARNED = 0, 1, 2
 EXPORTS = ("molt_create", "molt_apply_D", "molt_step", "molt_set_option", "molt_profile_read", "molt_destroy",
            "molt_last_error", "molt_wave_step_noalloc", "molt_batch_tile_shape", "molt_set_mlp", "molt_mlp_stats",
            "molt_weno_linear_weights", "molt_mlp_pack", "molt_mlp_forward", "molt_mlp_loss_grad", "molt_mlp_adam",
-           "molt_mlp_harvest")
+           "molt_mlp_harvest", "molt_quadrature_weights")
 MLP_PARAMS = 1347
 MLP_BLOB_BYTES = 3728
 OPT_TMA, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_TEST_SKIP_ARRIVE = 0, 1, 2, 3
@@ -85,13 +85,16 @@ def load_library(path=LIB_PATH):
         lib.molt_set_mlp.argtypes = [vp, vp, ctypes.c_size_t]
         lib.molt_mlp_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.c_int]
         lib.molt_weno_linear_weights.argtypes = [dbl, ctypes.POINTER(dbl)]
+        lib.molt_quadrature_weights.argtypes = [ctypes.c_int, dbl, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                                ctypes.POINTER(dbl)]
         lib.molt_mlp_pack.argtypes = [vp, vp, vp]
         lib.molt_mlp_forward.argtypes = [vp, vp, i64, ctypes.POINTER(dbl), vp, vp, vp]
         lib.molt_mlp_loss_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp]
         lib.molt_mlp_adam.argtypes = [vp, vp, vp, vp, i64, dbl, dbl, dbl, dbl, vp, vp]
         lib.molt_mlp_harvest.argtypes = [vp, i64, i64, vp, i64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl), vp,
                                          vp, i64, vp]
-        for f in ("molt_set_mlp", "molt_mlp_stats", "molt_weno_linear_weights", "molt_mlp_pack", "molt_mlp_forward",
+        for f in ("molt_set_mlp", "molt_mlp_stats", "molt_weno_linear_weights", "molt_quadrature_weights",
+                  "molt_mlp_pack", "molt_mlp_forward",
                   "molt_mlp_loss_grad", "molt_mlp_adam", "molt_mlp_harvest"):
             getattr(lib, f).restype = ctypes.c_int
         lib.molt_last_error.argtypes = [ctypes.c_void_p]
@@ -293,3 +296,13 @@ def molt_mlp_harvest(u, pos, axis, side, x, y=None, d=None, stride=1, stream=Non
                                  _dvec3(d), ctypes.c_void_p(x.data_ptr()),
                                  ctypes.c_void_p(y.data_ptr()) if y is not None else None, int(stride),
                                  _stream_ptr(stream)), "molt_mlp_harvest")
+
+
+def molt_quadrature_weights(quad_points, nu):
+    """(c[6] on offsets -3..2, sub[3][4], d[3]) of the rule the sweeps use."""
+    lib = load_library()
+    c = (ctypes.c_double * 6)()
+    sub = (ctypes.c_double * 12)()
+    d = (ctypes.c_double * 3)()
+    _status(lib.molt_quadrature_weights(int(quad_points), float(nu), c, sub, d), "molt_quadrature_weights")
+    return list(c), [list(sub[4 * r:4 * r + 4]) for r in range(3)], list(d)
