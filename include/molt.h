@@ -112,7 +112,7 @@ molt_status molt_apply_D(molt_ctx* ctx, int problem, int axis, int op, int P, do
  *              second-order Taylor step and ignores u_prev[i] on entry.
  * Heat: 3-stage SSP Runge-Kutta on dt*F = -beta^2 sum_d S_{P,d}, alpha =
  * beta/sqrt(kappa dt).  Wave: u^{n+1} = 2u^n - u^{n-1} - beta^2 sum_d S_{P,d},
- * alpha = beta/(c dt).  Hamilton-Jacobi (H = |grad u|^2/2, periodic):
+ * alpha = beta/(c dt).  Hamilton-Jacobi (H = |grad u|^2/2, periodic, 1-D or 2-D):
  * forward Euler with the local Lax-Friedrichs numerical Hamiltonian, one-
  * sided derivatives alpha D_R, -alpha D_L, alpha = beta/(cfl h), dt from the
  * wave speeds of the previous step (Algorithm 1; the speeds of u^0 on the

@@ -458,6 +458,10 @@ molt_status molt_create(const molt_desc* descs, int count, void* cuda_stream, mo
           delete c;
           return fail(nullptr, MOLT_EUNSUPPORTED, "Hamilton-Jacobi needs periodic axes");
         }
+      if (p.d.ndim > 2) {
+        delete c;
+        return fail(nullptr, MOLT_EUNSUPPORTED, "Hamilton-Jacobi runs in 1-D and 2-D");
+      }
       if (p.d.prec == MOLT_PREC_F32_F64UPDATE) {
         delete c;
         return fail(nullptr, MOLT_EUNSUPPORTED, "Hamilton-Jacobi runs in MOLT_PREC_F32 or MOLT_PREC_F64");

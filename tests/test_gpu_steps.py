@@ -173,3 +173,86 @@ def test_hj_anisotropic_long_lines(nx, ny, prec, transposed):
         tt += dt
     assert rel_l2(got, uu) < tol_for(prec)
     assert abs(t[0] - tt) < (1e-10 if prec == M.PREC_F64 else 1e-4) * tt
+
+
+@pytest.mark.parametrize("case", ["heat1d", "heat3d", "wave1d", "wave2d_periodic", "hj1d"])
+def test_other_dimensions(case):
+    """Every PDE in the other dimensions the descriptor allows, against the
+    oracle's schemes (FP64 and mixed precision)."""
+    need_gpu()
+    import torch
+    g = workloads.rng(12)
+    if case.startswith("heat"):
+        shape = (48,) if case == "heat1d" else (20, 24, 28)           # numpy order
+        shape_xyz = tuple(reversed(shape))
+        hs = [1.0 / s for s in shape]
+        dt = min(hs) / 2
+        u0 = g.standard_normal(shape)
+        for prec in (M.PREC_F64, M.PREC_F32_F64UPDATE):
+            d = M.make_desc(shape_xyz, P=3, quad_points=3, beta=0.6, pde=M.PDE_HEAT, dt=dt, prec=prec)
+            ctx = M.molt_create(d)
+            try:
+                u = to_dev(u0, torch.float64)
+                M.molt_step(ctx, u, None, nsteps=2, t=[0.0])
+                got = u.cpu().numpy()
+            finally:
+                M.molt_destroy(ctx)
+            want = u0
+            for _ in range(2):
+                want = schemes.heat_step(want, hs, dt, 1.0, 0.6, None, 3, 3)
+            assert rel_l2(got, want) < tol_for(prec), prec
+    elif case.startswith("wave"):
+        shape = (64,) if case == "wave1d" else (40, 56)
+        shape_xyz = tuple(reversed(shape))
+        per = case == "wave2d_periodic"
+        bc = M.BC_PERIODIC if per else M.BC_DIRICHLET
+        hs = [1.0 / (s if per else s - 1) for s in shape]
+        dt = 2 * min(hs)
+        u0 = g.standard_normal(shape)
+        if not per:
+            workloads.zero_boundary(u0)
+        for prec in (M.PREC_F64, M.PREC_F32_F64UPDATE):
+            d = M.make_desc(shape_xyz, bc=[bc] * len(shape), P=2, quad_points=6, beta=0.8, pde=M.PDE_WAVE, c=1.0,
+                            dt=dt, prec=prec)
+            ctx = M.molt_create(d)
+            try:
+                u = to_dev(u0, torch.float64)
+                up = torch.empty_like(u)
+                M.molt_step(ctx, u, up, nsteps=3, t=[0.0])
+                got = u.cpu().numpy()
+            finally:
+                M.molt_destroy(ctx)
+            bcs = ["periodic" if per else "dirichlet"] * len(shape)
+            prev, cur = None, u0
+            for k in range(3):
+                nxt = schemes.wave_step(cur, prev, hs, dt, 1.0, 0.8, bcs, 6, 2, from_rest=(k == 0))
+                prev, cur = cur, nxt
+            assert rel_l2(got, cur) < tol_for(prec), prec
+    else:
+        n = 256
+        h = 2 * np.pi / n
+        x = np.arange(n) * h
+        u0 = -np.cos(x) + 1e-3 * g.standard_normal(n)
+        for prec in (M.PREC_F64, M.PREC_F32):
+            d = M.make_desc((n,), lo=[0.0], hi=[2 * np.pi], P=1, quad_points=5, weights=M.W_WENOZ, beta=1.0,
+                            pde=M.PDE_HJ, cfl=1.5, dt=0.0, prec=prec)
+            ctx = M.molt_create(d)
+            try:
+                u = to_dev(u0, state_dtype(prec))
+                t = M.molt_step(ctx, u, None, nsteps=3, t=[0.0])
+                got = u.double().cpu().numpy()
+            finally:
+                M.molt_destroy(ctx)
+            uu = u0.astype(np.float32).astype(np.float64) if prec == M.PREC_F32 else u0
+            speeds = schemes.hj_initial_speeds(uu, [h], 1.5, 1.0, 5, "wenoz")
+            for _ in range(3):
+                uu, _, speeds = schemes.hj_step(uu, [h], speeds, 1.5, 1.0, 5, "wenoz")
+            assert rel_l2(got, uu) < tol_for(prec), prec
+
+
+def test_hj_3d_is_rejected():
+    need_gpu()
+    d = M.make_desc((16, 16, 16), P=1, quad_points=5, weights=M.W_WENOZ, pde=M.PDE_HJ, cfl=1.5, prec=M.PREC_F32)
+    with pytest.raises(M.MoltError) as e:
+        M.molt_create(d)
+    assert e.value.status == M.MOLT_EUNSUPPORTED
