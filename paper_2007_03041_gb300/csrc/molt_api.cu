@@ -239,6 +239,8 @@ molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, do
   a.mu = std::exp(-nu * double(N));
   a.inv1mmu = 1.0 / (-std::expm1(-nu * double(N)));
   a.invdet = 1.0 / (-std::expm1(-2.0 * nu * double(N)));
+  a.k2det = 2.0 * a.invdet;
+  a.k2detq = a.k2det * a.invq;
   // tile shape: nwl warps per line, W lines per CTA, <= kMaxThreads threads
   const int nwl = (n + 32 * E - 1) / (32 * E);
   if (nwl > kMaxThreads / 32) return fail(c, MOLT_EUNSUPPORTED, "line longer than 8192 points");

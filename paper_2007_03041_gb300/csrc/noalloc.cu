@@ -89,6 +89,8 @@ bool plan(const molt_desc& d, int ax, double alpha, int* status, SweepArgs* a, i
   a->mu = std::exp(-nu * double(N));
   a->inv1mmu = 1.0 / (-std::expm1(-nu * double(N)));
   a->invdet = 1.0 / (-std::expm1(-2.0 * nu * double(N)));
+  a->k2det = 2.0 * a->invdet;
+  a->k2detq = a->k2det * a->invq;
   const int nwl = (n + 32 * kE - 1) / (32 * kE);
   if (nwl > kMaxThreads / 32) return false;
   int W = 1;

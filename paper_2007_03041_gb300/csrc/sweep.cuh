@@ -87,6 +87,7 @@ struct SweepArgs {
   double inv1mmu;     // 1/(1-mu)
   double mu;          // e^{-alpha(b-a)}
   double invdet;      // 1/(1-mu^2)
+  double k2det, k2detq;  // 2/(1-mu^2) and 2 e^{nu}/(1-mu^2) (Dirichlet L_0 carries)
   double alpha;
   // the same coefficients rounded to FP32 on the host (FP32 kernels read
   // these; converting on the device would use the FP64 pipe)
@@ -444,16 +445,18 @@ __device__ __forceinline__ void boundary_carries(const SweepArgs& a, const T* bw
   const double v0 = cvt<double>(bw[phys<E>(0)]), vN = cvt<double>(bw[phys<E>(n - 1)]);
   double cr, cl;
   if (a.mode == MODE_0) {
+    // 2A, 2B (the 1/q of exact-fit kernels folded into the constant)
     const double r0 = fma(-0.5, ILa, v0), r1 = fma(-0.5, IRb, vN);
-    cr = 2.0 * fma(-a.mu, r1, r0) * a.invdet;
-    cl = 2.0 * fma(-a.mu, r0, r1) * a.invdet;
+    const double k = RAGGED ? a.k2det : a.k2detq;
+    cr = fma(-a.mu, r1, r0) * k;
+    cl = fma(-a.mu, r0, r1) * k;
   } else {
     cr = v0;   // L_R^{-1}(a) = v(a)
     cl = vN;   // L_L^{-1}(b) = v(b)
-  }
-  if (!RAGGED) {
-    cr *= a.invq;
-    cl *= a.invq;
+    if (!RAGGED) {
+      cr *= a.invq;
+      cl *= a.invq;
+    }
   }
   *CR = cr;
   *CL = cl;
