@@ -271,6 +271,25 @@ __global__ void __launch_bounds__(512, 1) batch_heat_kernel(const BatchParams p)
         const long long i1 = i0 + kChunk < U.total ? i0 + kChunk : U.total;
         const double* us = s == 0 ? U.u : (s == 1 ? U.st1 : U.st2);
         double* dstp = s == 0 ? U.st1 : (s == 1 ? U.st2 : U.u);
+        // L2 prefetch of the CTA's next chunk (u, the stage input, acc)
+        {
+          const long long cn = c + gridDim.x;
+          if (cn < p.chunks) {
+            const BatchUpdate& V = p.updates[find_update(p, cn)];
+            const long long j0 = (cn - V.first_chunk) * kChunk;
+            const long long j1 = j0 + kChunk < V.total ? j0 + kChunk : V.total;
+            const double* vs = s == 0 ? V.u : (s == 1 ? V.st1 : V.st2);
+            for (long long j = j0 + 16LL * threadIdx.x; j < j1; j += 16LL * blockDim.x) {
+              prefetch_l2(V.u + j);
+              prefetch_l2(j + 8 < j1 ? V.u + j + 8 : V.u + j);
+              if (vs != V.u) {
+                prefetch_l2(vs + j);
+                prefetch_l2(j + 8 < j1 ? vs + j + 8 : vs + j);
+              }
+              prefetch_l2(V.acc + j);
+            }
+          }
+        }
         // all loads of a thread's points are issued before its stores (the
         // CTA is the SM's only one, so memory parallelism comes from here)
         constexpr int kPer = kChunk / 512;
