@@ -24,7 +24,19 @@ TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__``.
   alpha = beta/(CFL dx) (= beta/(c_max dt) whenever the CFL rule sets dt, so
   nu = beta/CFL stays fixed); dt is capped at 10 dx when c -> 0; at the first
   step the speeds of u^0 serve as the lagged speeds.
+* The test problems of Sec. 5.1 (first order in time, P = 1): forward Euler
+  for the heat equation (Example 2), u^{n+1} = u^n - beta^2 sum_d S_{1,d}[u^n];
+  the Hamilton-Jacobi step with other Hamiltonians, H = u_x + u_y (Example 1,
+  linear advection) and H = (1 + u_x + u_y)^2/2 (Example 3), and a source
+  F(x, t) on the right-hand side (Example 3's manufactured solution):
+  u^{n+1} = u^n - dt^n (H^ - F(., t_n)).  The local Lax-Friedrichs r_d is the
+  largest |dH/dp_d| over the box of one-sided derivatives prod_d
+  [min(v_d^-, v_d^+), max(v_d^-, v_d^+)]; for these Hamiltonians |dH/dp_d| is
+  the absolute value of an affine function, so the largest value sits at a
+  corner of the box, and the oracle evaluates every corner.
 """
+import itertools
+
 import numpy as np
 
 from .sweep import partial_sum, BC_PERIODIC
@@ -75,17 +87,60 @@ def hj_derivatives(u, alpha, dxs, npts=5, weights="wenoz", weight_fn=None):
     return out
 
 
-def hj_hamiltonian(ders):
-    """Local Lax-Friedrichs numerical Hamiltonian for H(p) = |p|^2/2 and the
-    per-axis wave speeds c_d = max_grid r_d (Sec. 2.5, Sec. 4.4)."""
-    Hh = 0.0
+H_HALF_SQ, H_LINEAR, H_AFFINE_SQ = "half_sq", "linear", "affine_sq"
+
+
+def hamiltonian(kind, p, a=None, h0=0.0):
+    """H(p) for the gradient components p[d]: |p|^2/2, a.p, or (h0 + a.p)^2/2
+    (d and a[d] follow the array axes, as everywhere in the oracle)."""
+    if kind == H_HALF_SQ:
+        return 0.5 * sum(pd * pd for pd in p)
+    s = sum(a[d] * pd for d, pd in enumerate(p))
+    if kind == H_LINEAR:
+        return s
+    return 0.5 * (h0 + s) ** 2
+
+
+def hamiltonian_grad(kind, p, a=None, h0=0.0):
+    """[dH/dp_d] for the same Hamiltonians."""
+    if kind == H_HALF_SQ:
+        return list(p)
+    if kind == H_LINEAR:
+        return [a[d] + 0.0 * p[d] for d in range(len(p))]
+    s = h0 + sum(a[d] * pd for d, pd in enumerate(p))
+    return [a[d] * s for d in range(len(p))]
+
+
+def llf_r(ders, kind=H_HALF_SQ, a=None, h0=0.0):
+    """r_d = max over the corners of the box prod_d I(v_d^-, v_d^+) of |dH/dp_d|."""
+    nd = len(ders)
+    r = [np.zeros_like(np.asarray(ders[0][0], dtype=np.float64)) for _ in range(nd)]
+    for corner in itertools.product((0, 1), repeat=nd):
+        p = [ders[d][corner[d]] for d in range(nd)]
+        g = hamiltonian_grad(kind, p, a, h0)
+        for d in range(nd):
+            r[d] = np.maximum(r[d], np.abs(g[d]))
+    return r
+
+
+def hj_hamiltonian(ders, kind=H_HALF_SQ, a=None, h0=0.0):
+    """Local Lax-Friedrichs numerical Hamiltonian (Sec. 2.5)
+        H^ = H(means) - sum_d r_d (v_d^+ - v_d^-)/2,
+    r_d from ``llf_r``, and the per-axis wave speeds c_d = max_grid r_d
+    (Sec. 4.4)."""
+    means = [0.5 * (dm + dp) for dm, dp in ders]
+    Hh = hamiltonian(kind, means, a, h0)
+    r = llf_r(ders, kind, a, h0)
     speeds = []
-    for dm, dp in ders:
-        r = np.maximum(np.abs(dm), np.abs(dp))
-        mean = 0.5 * (dm + dp)
-        Hh = Hh + 0.5 * mean * mean + r * 0.5 * (dm - dp)
-        speeds.append(float(r.max()))
+    for d, (dm, dp) in enumerate(ders):
+        Hh = Hh - r[d] * 0.5 * (dp - dm)
+        speeds.append(float(r[d].max()))
     return Hh, speeds
+
+
+def source_at(coefs, t):
+    """F(x, t) = sum_k t^k F_k(x)."""
+    return sum((t ** k) * F for k, F in enumerate(coefs))
 
 
 def hj_dt(speeds, dxs, cfl):
@@ -95,17 +150,28 @@ def hj_dt(speeds, dxs, cfl):
     return min(cands + [cap])
 
 
-def hj_initial_speeds(u, dxs, cfl=1.5, beta=1.0, npts=5, weights="wenoz", weight_fn=None):
+def hj_initial_speeds(u, dxs, cfl=1.5, beta=1.0, npts=5, weights="wenoz", weight_fn=None,
+                      hamiltonian=H_HALF_SQ, a=None, h0=0.0):
     alpha = beta / (cfl * min(dxs))
-    _, speeds = hj_hamiltonian(hj_derivatives(u, alpha, dxs, npts, weights, weight_fn))
+    _, speeds = hj_hamiltonian(hj_derivatives(u, alpha, dxs, npts, weights, weight_fn), hamiltonian, a, h0)
     return speeds
 
 
-def hj_step(u, dxs, lagged_speeds, cfl=1.5, beta=1.0, npts=5, weights="wenoz", weight_fn=None):
-    """One forward-Euler step u^{n+1} = u^n - dt^n H^; returns
+def hj_step(u, dxs, lagged_speeds, cfl=1.5, beta=1.0, npts=5, weights="wenoz", weight_fn=None,
+            hamiltonian=H_HALF_SQ, a=None, h0=0.0, source=None, t=0.0):
+    """One forward-Euler step u^{n+1} = u^n - dt^n (H^ - F(., t)); returns
     (u^{n+1}, dt^n, speeds of u^n) -- the speeds become the lagged speeds of
-    the next step (Algorithm 1)."""
+    the next step (Algorithm 1).  source: the coefficients F_k of F."""
     alpha = beta / (cfl * min(dxs))
     dt = hj_dt(lagged_speeds, dxs, cfl)
-    Hh, speeds = hj_hamiltonian(hj_derivatives(u, alpha, dxs, npts, weights, weight_fn))
+    Hh, speeds = hj_hamiltonian(hj_derivatives(u, alpha, dxs, npts, weights, weight_fn), hamiltonian, a, h0)
+    if source is not None:
+        Hh = Hh - source_at(source, t)
     return u - dt * Hh, dt, speeds
+
+
+def heat_euler_step(u, dxs, dt, kappa=1.0, beta=1.0, bc=None, npts=6, P=1):
+    """One forward-Euler step of the heat equation (Sec. 5.1, Example 2)."""
+    bc = bc or [BC_PERIODIC] * u.ndim
+    un = np.asarray(u, dtype=np.float64)
+    return un + heat_rhs_dt(un, dxs, dt, kappa, beta, bc, npts, P)

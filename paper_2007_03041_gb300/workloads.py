@@ -23,6 +23,13 @@ boundary nodes, h = (hi-lo)/(n-1)):
                       O(1) level, the same with 1e-3 noise, kinks and jumps.
 * ``mlp_initial_params`` -- seeded He-style initial network parameters.
 * ``mlp_positions`` -- seeded flat grid indices for harvesting stencils.
+* the test problems of Sec. 5.1 on [0,2pi]^2, periodic (analytic, no seed):
+  ``advection_initial`` (Example 1) u0 = (1 - cos x)(1 - cos y)/4;
+  ``diffusion_initial`` (Example 2) u0 = sin x + sin y;
+  ``manufactured_hj_solution`` / ``manufactured_hj_source`` (Example 3)
+  u = t (sin x + sin y) for u_t + (1 + u_x + u_y)^2/2 = F, so that
+  F = sin x + sin y + (1 + t cos x + t cos y)^2/2
+    = [sin x + sin y + 1/2] + t [cos x + cos y] + t^2 [(cos x + cos y)^2/2].
 """
 import numpy as np
 
@@ -146,3 +153,40 @@ def mlp_initial_params(seed=SEED_MLP):
 def mlp_positions(count, nx, ny, seed=SEED_MLP):
     """`count` flat indices drawn uniformly from an ny x nx grid (int64)."""
     return rng(seed).integers(0, nx * ny, size=count, dtype=np.int64)
+
+
+def paper_grid(n):
+    """x_i = 2 pi i / n, i < n, as a (y, x) pair of broadcastable arrays."""
+    x = 2 * np.pi * np.arange(n) / n
+    return x[None, :], x[:, None]
+
+
+def advection_initial(n):
+    x, y = paper_grid(n)
+    return 0.25 * (1 - np.cos(x)) * (1 - np.cos(y))
+
+
+def advection_solution(n, t):
+    """u0(x - t, y - t) of u_t + u_x + u_y = 0."""
+    x, y = paper_grid(n)
+    return 0.25 * (1 - np.cos(x - t)) * (1 - np.cos(y - t))
+
+
+def diffusion_initial(n):
+    x, y = paper_grid(n)
+    return np.sin(x) + np.sin(y) + 0.0 * x * y
+
+
+def diffusion_solution(n, t):
+    return np.exp(-t) * diffusion_initial(n)
+
+
+def manufactured_hj_solution(n, t):
+    return t * diffusion_initial(n)
+
+
+def manufactured_hj_source(n):
+    """The coefficients (F_0, F_1, F_2) of the Example 3 source, shape (3, n, n)."""
+    x, y = paper_grid(n)
+    c = np.cos(x) + np.cos(y)
+    return np.stack([np.sin(x) + np.sin(y) + 0.5, c, 0.5 * c * c])
