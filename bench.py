@@ -383,12 +383,24 @@ CONFIGS = {
                    bytes_per_dof=20, bound="hbm", dtype="f32"),
     "hj8192_learned": dict(metric="DOF updates/sec (2-D Hamilton-Jacobi, 8192^2, learned WENO weights, FP32) on GB300",
                            bytes_per_dof=20, bound="tensor+alu", dtype="f32"),
+    # the paper's own test problems (Sec. 5.1) on its 5277^2 grid: P = 1,
+    # 6-point linear quadrature, forward Euler, FP64
+    "paper_ex1_advection": dict(metric="DOF updates/sec (Sec. 5.1 Example 1, 2-D linear advection, 5277^2, FP64) on GB300",
+                                bytes_per_dof=40, bound="hbm", dtype="f64"),
+    "paper_ex2_diffusion": dict(metric="DOF updates/sec (Sec. 5.1 Example 2, 2-D diffusion, 5277^2, FP64) on GB300",
+                                bytes_per_dof=40, bound="hbm", dtype="f64"),
+    "paper_ex3_hj": dict(metric="DOF updates/sec (Sec. 5.1 Example 3, 2-D Hamilton-Jacobi with source, 5277^2, FP64) on GB300",
+                         bytes_per_dof=80, bound="hbm", dtype="f64"),
 }
+# Sec. 4.5 / Sec. 5: the paper's sustained rate on one CPU node (2 x Xeon Gold
+# 6148) for these test problems; a context figure from other hardware
+PAPER_NODE_DOF_PER_S = 1e8
 
 
 def _problem(config, prec=None):
     """(descs, initial states as numpy arrays, u_prev needed) of a config."""
     import math
+    import numpy as np
     from paper_2007_03041_gb300 import molt as M
     from paper_2007_03041_gb300 import workloads
     if config == "heat256":
@@ -396,6 +408,18 @@ def _problem(config, prec=None):
         d = M.make_desc((n, n), P=3, quad_points=3, beta=0.6, pde=M.PDE_HEAT, dt=0.5 / n,
                         prec=M.PREC_F64 if prec is None else prec)
         return [d], [workloads.heat_modes(n)]
+    if config.startswith("paper_ex"):
+        n = 5277
+        h = 2 * math.pi / n
+        if config == "paper_ex2_diffusion":
+            d = M.make_desc((n, n), lo=[0, 0], hi=[2 * math.pi] * 2, P=1, quad_points=6, beta=1.0, pde=M.PDE_HEAT,
+                            dt=h, prec=M.PREC_F64, integrator=M.INT_EULER)
+            return [d], [workloads.diffusion_initial(n)]
+        ex1 = config == "paper_ex1_advection"
+        d = M.make_desc((n, n), lo=[0, 0], hi=[2 * math.pi] * 2, P=1, quad_points=6, beta=1.0, pde=M.PDE_HJ,
+                        cfl=1.0, dt=0.0, prec=M.PREC_F64, hamiltonian=M.H_LINEAR if ex1 else M.H_AFFINE_SQ,
+                        velocity=(1.0, 1.0), h0=0.0 if ex1 else 1.0)
+        return [d], [workloads.advection_initial(n) if ex1 else np.zeros((n, n))]
     if config == "batch64":
         sides = workloads.batched_sides()
         descs = [M.make_desc((n, n), P=3, quad_points=3, beta=0.6, pde=M.PDE_HEAT, dt=0.5 / n,
@@ -424,6 +448,10 @@ def _timed_steps(config, steps, warmup, prec=None, blob=None, profile_kinds=()):
         try:
             if blob is not None and descs[0].weights == M.W_LEARNED:
                 M.molt_set_mlp(ctx, blob)
+            if config == "paper_ex3_hj":
+                from paper_2007_03041_gb300 import workloads
+                M.molt_set_source(ctx, 0, torch.tensor(workloads.manufactured_hj_source(int(descs[0].n[0])),
+                                                       device="cuda"))
             us = [torch.tensor(a, dtype=torch.float32 if f32 else torch.float64, device="cuda") for a in u0]
             t = M.molt_step(ctx, us, None, nsteps=warmup, t=[0.0] * len(us)) if warmup else [0.0] * len(us)
             if blob is not None and descs[0].weights == M.W_LEARNED:
@@ -453,6 +481,46 @@ def _timed_steps(config, steps, warmup, prec=None, blob=None, profile_kinds=()):
     return ms, us, kinds, stats
 
 
+# Sec. 5.1 figure caption: L-infinity errors on the 5277^2 grid
+PAPER_LINF = {"paper_ex1_advection": 2.874e-3, "paper_ex2_diffusion": 4.010e-4, "paper_ex3_hj": 2.674e-4}
+
+
+def _paper_final_error(config):
+    """Runs a Sec. 5.1 test problem from t = 0 to its final time (2 pi, 1,
+    0.5) and returns (L-infinity error against the exact solution, final t,
+    steps)."""
+    import math
+    import torch
+    from paper_2007_03041_gb300 import molt as M
+    from paper_2007_03041_gb300 import workloads
+    descs, u0 = _problem(config)
+    n = int(descs[0].n[0])
+    h = 2 * math.pi / n
+    ctx = M.molt_create(descs)
+    try:
+        if config == "paper_ex3_hj":
+            M.molt_set_source(ctx, 0, torch.tensor(workloads.manufactured_hj_source(n), device="cuda"))
+        u = torch.tensor(u0[0], device="cuda")
+        if config == "paper_ex3_hj":
+            t, steps = [0.0], 0
+            while t[0] < 0.5:
+                t = M.molt_step(ctx, [u], None, nsteps=1, t=t)
+                steps += 1
+            exact = workloads.manufactured_hj_solution(n, t[0])
+        elif config == "paper_ex1_advection":
+            steps = n                                # dt = h: T = 2 pi
+            t = M.molt_step(ctx, [u], None, nsteps=steps, t=[0.0])
+            exact = workloads.advection_solution(n, t[0])
+        else:
+            steps = round(1.0 / h)
+            t = M.molt_step(ctx, [u], None, nsteps=steps, t=[0.0])
+            exact = workloads.diffusion_solution(n, t[0])
+        err = float((u - torch.tensor(exact, device="cuda")).abs().max())
+    finally:
+        M.molt_destroy(ctx)
+    return err, t[0], steps
+
+
 def run_config(args):
     import torch
     from paper_2007_03041_gb300 import molt as M
@@ -477,7 +545,11 @@ def run_config(args):
     kinds = {"heat256": (("sweep_final", M.KERNEL_HEAT_FINAL), ("sweep_acc", M.KERNEL_ACC_SET)),
              "batch64": (("batch_step", M.KERNEL_BATCH),),
              "hj4096": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y)),
-             "hj8192_learned": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y))}[args.config]
+             "hj8192_learned": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y)),
+             "paper_ex1_advection": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y),
+                                     ("transpose", M.KERNEL_TRANSPOSE)),
+             "paper_ex2_diffusion": (("sweep_final", M.KERNEL_HEAT_FINAL), ("sweep_acc", M.KERNEL_ACC_SET)),
+             "paper_ex3_hj": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y))}[args.config]
     ms, us, per_kind, stats = _timed_steps(args.config, args.steps, args.warmup, blob=blob, profile_kinds=kinds)
     value = dof / (ms / 1e3)
     peaks = measured_peaks()
@@ -494,6 +566,13 @@ def run_config(args):
                      "per_kind_ms_per_step": per_kind,
                      "peak_source": "measured" if peaks else "fallback"},
     }
+    if args.config.startswith("paper_ex"):
+        err, tf, nst = _paper_final_error(args.config)
+        extra["final_error"] = {"linf_vs_exact": err, "t_final": tf, "steps": nst,
+                                "paper_linf_5277": PAPER_LINF[args.config]}
+        line["vs_baseline"] = value / PAPER_NODE_DOF_PER_S
+        extra["vs_baseline_note"] = ("value / the paper's sustained 1e8 DOF/node/s for its Sec. 5.1 test problems "
+                                     "on one CPU node (2 x Xeon Gold 6148); other hardware, context only")
     if stats is not None:
         extra["learned_stats"] = {"stencils": stats[0], "fallbacks": stats[1],
                                   "fallback_fraction": stats[1] / max(stats[0], 1)}

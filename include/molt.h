@@ -63,6 +63,21 @@ typedef enum {
 } molt_prec;
 typedef enum { MOLT_PDE_HEAT = 0, MOLT_PDE_WAVE = 1, MOLT_PDE_HJ = 2 } molt_pde;
 typedef enum { MOLT_W_LINEAR = 0, MOLT_W_WENOZ = 1, MOLT_W_LEARNED = 2 } molt_weights;
+/* Hamiltonian of the Hamilton-Jacobi step (Sec. 2.5, and the test problems
+ * of Sec. 5.1: Example 1 is H = u_x + u_y, Example 3 H = (1 + u_x + u_y)^2/2),
+ * a_d = velocity[d]:
+ *   MOLT_H_HALF_SQ    H = |grad u|^2 / 2
+ *   MOLT_H_LINEAR     H = sum_d a_d u_d                  (linear advection)
+ *   MOLT_H_AFFINE_SQ  H = (h0 + sum_d a_d u_d)^2 / 2
+ * The numerical Hamiltonian is local Lax-Friedrichs with r_d the largest
+ * |dH/du_d| over the box of one-sided derivatives; the wave speed of axis d
+ * is the grid maximum of r_d. */
+typedef enum { MOLT_H_HALF_SQ = 0, MOLT_H_LINEAR = 1, MOLT_H_AFFINE_SQ = 2 } molt_hamiltonian;
+/* Time integrator: MOLT_INT_DEFAULT (heat: 3-stage SSP Runge-Kutta; wave:
+ * leapfrog; Hamilton-Jacobi: forward Euler) or MOLT_INT_EULER (forward
+ * Euler; heat and Hamilton-Jacobi, the first-order coupling of the paper's
+ * test problems, Sec. 5.1). */
+typedef enum { MOLT_INT_DEFAULT = 0, MOLT_INT_EULER = 1 } molt_integrator;
 
 /* One problem: a grid, its boundary types, the quadrature and the PDE whose
  * time step molt_step advances.  Enumerations are stored as int. */
@@ -81,6 +96,10 @@ typedef struct {
   double cfl;            /* CFL number (Hamilton-Jacobi)                         */
   double dt;             /* fixed time step; <= 0 selects the adaptive rule (HJ) */
   int prec;              /* molt_prec                                            */
+  int hamiltonian;       /* molt_hamiltonian (Hamilton-Jacobi)                   */
+  double velocity[3];    /* a_d of MOLT_H_LINEAR / MOLT_H_AFFINE_SQ              */
+  double h0;             /* constant of MOLT_H_AFFINE_SQ                         */
+  int integrator;        /* molt_integrator                                      */
 } molt_desc;
 
 typedef struct molt_ctx molt_ctx;
@@ -112,12 +131,27 @@ molt_status molt_apply_D(molt_ctx* ctx, int problem, int axis, int op, int P, do
  *              second-order Taylor step and ignores u_prev[i] on entry.
  * Heat: 3-stage SSP Runge-Kutta on dt*F = -beta^2 sum_d S_{P,d}, alpha =
  * beta/sqrt(kappa dt).  Wave: u^{n+1} = 2u^n - u^{n-1} - beta^2 sum_d S_{P,d},
- * alpha = beta/(c dt).  Hamilton-Jacobi (H = |grad u|^2/2, periodic, 1-D or 2-D):
- * forward Euler with the local Lax-Friedrichs numerical Hamiltonian, one-
- * sided derivatives alpha D_R, -alpha D_L, alpha = beta/(cfl h), dt from the
- * wave speeds of the previous step (Algorithm 1; the speeds of u^0 on the
- * first step).  Synchronous at the end (reads t and the device status). */
+ * alpha = beta/(c dt); heat with MOLT_INT_EULER: u^{n+1} = u^n - beta^2
+ * sum_d S_{P,d}[u^n].  Hamilton-Jacobi (H from desc.hamiltonian, periodic,
+ * 1-D or 2-D): forward Euler u^{n+1} = u^n - dt (H^ - F(x, t_n)) with the
+ * local Lax-Friedrichs numerical Hamiltonian H^, one-sided derivatives
+ * alpha D_R, -alpha D_L, alpha = beta/(cfl min_d h_d), dt = cfl min_d h_d / c_d
+ * with the wave speeds c_d of the previous step (Eq. "adaptive time rule",
+ * Algorithm 1; the speeds of u^0 on the first step; at most 10 min_d h_d), and
+ * the source F of molt_set_source (0 if none).
+ * Synchronous at the end (reads t and the device status). */
 molt_status molt_step(molt_ctx* ctx, void* const* u, void* const* u_prev, int nsteps, double* t_inout);
+
+/* Source term of a Hamilton-Jacobi problem, polynomial in time:
+ *   F(x, t) = sum_{k=0}^{degree} t^k F_k(x),
+ * as for a manufactured solution (Sec. 5.1, Example 3: u = t (sin x + sin y)
+ * gives F = sin x + sin y + (1 + t cos x + t cos y)^2 / 2, degree 2).
+ * coef: device array of degree+1 consecutive state-shaped arrays F_0 ..
+ * F_degree (state element type, C order), copied into the context before
+ * the call returns (the caller keeps ownership); coef == NULL removes the
+ * source.  degree in 0..4.  MOLT_EINVAL: bad problem index, degree or
+ * alignment, or a problem that is not Hamilton-Jacobi.  Synchronous. */
+molt_status molt_set_source(molt_ctx* ctx, int problem, const void* coef, int degree);
 
 /* Context options.
  *   MOLT_OPT_TMA      1 (default): sweeps whose lines are an exact fit and

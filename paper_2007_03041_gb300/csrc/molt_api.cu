@@ -30,7 +30,10 @@ struct Problem {
   void* acc = nullptr;      // compute-type accumulator (total elements)
   void* stage1 = nullptr;   // heat RK stages (state type)
   void* stage2 = nullptr;
-  void* hx = nullptr;       // HJ H^_x (state type)
+  void* hx = nullptr;       // HJ H^_x, or sigma_x of AFFINE_SQ (state type)
+  void* hx2 = nullptr;      // HJ AFFINE_SQ: delta_x (state type)
+  void* src = nullptr;      // HJ source coefficients F_0..F_src_deg (state type), or null
+  int src_deg = 0;
   void* tu = nullptr;       // HJ, transposed y pass: u^T and (H^_x)^T / u^{n+1}^T
   void* thx = nullptr;
   float* shadow = nullptr;  // FP32 copy of the state the sweeps read (mixed precision)
@@ -63,6 +66,7 @@ struct molt_ctx {
   int* status_dev = nullptr;       // device status word
   unsigned long long* speed_dev = nullptr;  // per problem: 2 speed slots (double bits)
   double* t_dev = nullptr;         // per problem time (HJ)
+  double* tnow_dev = nullptr;      // per problem time at the start of the step (HJ source)
   bool no_tma = false;             // force the plain kernels (molt_set_option)
   void* mlp_blob = nullptr;        // learned weights: the BF16 network (MlpBlob)
   unsigned long long* mlp_stats = nullptr;  // [stencils evaluated, fallbacks]
@@ -111,6 +115,12 @@ std::string validate(const molt_desc& d) {
   if (d.prec < 0 || d.prec > 2) return "unknown precision";
   if (d.pde < 0 || d.pde > 2) return "unknown pde";
   if (!(d.beta > 0)) return "beta must be positive";
+  if (d.hamiltonian < MOLT_H_HALF_SQ || d.hamiltonian > MOLT_H_AFFINE_SQ) return "unknown hamiltonian";
+  for (int ax = 0; ax < 3; ++ax)
+    if (!std::isfinite(d.velocity[ax])) return "velocity must be finite";
+  if (!std::isfinite(d.h0)) return "h0 must be finite";
+  if (d.integrator != MOLT_INT_DEFAULT && d.integrator != MOLT_INT_EULER) return "unknown integrator";
+  if (d.integrator == MOLT_INT_EULER && d.pde == MOLT_PDE_WAVE) return "forward Euler is for heat and Hamilton-Jacobi";
   return "";
 }
 
@@ -234,6 +244,14 @@ molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, do
   a.qf = float(a.q);
   a.qEf = float(a.qE);
   a.alphaf = float(a.alpha);
+  if (mode == MODE_RL) {
+    a.ham = p.d.hamiltonian;
+    a.vel = p.d.velocity[ax];
+    a.velf = float(a.vel);
+    a.h0 = p.d.h0;
+    for (int d = 0; d < p.d.ndim; ++d) a.vmax = std::max(a.vmax, std::fabs(p.d.velocity[d]) / p.h[d]);
+    a.two_out = a.ham == MOLT_H_AFFINE_SQ ? 1 : 0;
+  }
   if (a.g.nlines >= (1LL << 31)) return fail(c, MOLT_EUNSUPPORTED, "more than 2^31 lines along an axis");
   const int N = a.bc == MOLT_BC_PERIODIC ? n : n - 1;  // intervals
   a.mu = std::exp(-nu * double(N));
@@ -260,6 +278,7 @@ molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, do
   const size_t tb = compute_bytes(p.d);
   size_t off = (size_t(4 * W) * 8 + size_t(W * nwl * 4) * tb + 15) & ~size_t(15);
   out->smem = off + size_t(W) * LS * tb;
+  if (a.two_out) out->smem += 16 + size_t(W) * LS * tb;   // second line buffer (carve order)
   if (p.d.weights == MOLT_W_LEARNED) {
     if (!c->mlp_ready) return fail(c, MOLT_EINVAL, "learned weights: call molt_set_mlp first");
     out->smem += learned_extra_bytes(W, LS);
@@ -358,6 +377,8 @@ cudaError_t dispatch_same(int jq, int epi, const Plan& pl, cudaStream_t s) {
     if (epi == EPI_STORE) return launch_sweep<T, T, T, JQ_WENOZ, EPI_STORE>(a, TMA, pl.grid, pl.block, pl.smem, s);
     if (epi == EPI_HJ_X) return launch_sweep<T, T, T, JQ_WENOZ, EPI_HJ_X>(a, TMA, pl.grid, pl.block, pl.smem, s);
     if (epi == EPI_HJ_Y) return launch_sweep<T, T, T, JQ_WENOZ, EPI_HJ_Y>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    if (epi == EPI_HJ_XG) return launch_sweep<T, T, T, JQ_WENOZ, EPI_HJ_XG>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    if (epi == EPI_HJ_YG) return launch_sweep<T, T, T, JQ_WENOZ, EPI_HJ_YG>(a, TMA, pl.grid, pl.block, pl.smem, s);
     return cudaErrorNotSupported;
   }
   if (jq == JQ_LEARNED) {
@@ -370,6 +391,8 @@ cudaError_t dispatch_same(int jq, int epi, const Plan& pl, cudaStream_t s) {
   }
   if (epi == EPI_HJ_X) return launch_sweep<T, T, T, JQ_LINEAR, EPI_HJ_X>(a, TMA, pl.grid, pl.block, pl.smem, s);
   if (epi == EPI_HJ_Y) return launch_sweep<T, T, T, JQ_LINEAR, EPI_HJ_Y>(a, TMA, pl.grid, pl.block, pl.smem, s);
+  if (epi == EPI_HJ_XG) return launch_sweep<T, T, T, JQ_LINEAR, EPI_HJ_XG>(a, TMA, pl.grid, pl.block, pl.smem, s);
+  if (epi == EPI_HJ_YG) return launch_sweep<T, T, T, JQ_LINEAR, EPI_HJ_YG>(a, TMA, pl.grid, pl.block, pl.smem, s);
   return dispatch_lin<T, T, T>(epi, pl, s);
 }
 
@@ -398,7 +421,8 @@ molt_status run(molt_ctx* c, const Problem& p, int epi, Plan& pl, bool from_stat
   // element size of the sweep input: FP64 except FP32 state or the FP32 copy
   const size_t in_bytes = is_f32_state(p.d) || (is_mixed(p.d) && from_state_copy) ? 4 : 8;
   if (!c->no_tma && p.d.weights != MOLT_W_LEARNED) plan_tma(p, pl.ax, pl.a.in, in_bytes, &pl);
-  molt_ctx::Rec rec{epi, nullptr, nullptr};
+  // profiling kind: the general Hamilton-Jacobi passes count as HJ_X / HJ_Y
+  molt_ctx::Rec rec{epi_hj_x(epi) ? int(EPI_HJ_X) : (epi_hj_y(epi) ? int(EPI_HJ_Y) : epi), nullptr, nullptr};
   if (c->profile) {
     cudaEventCreate(&rec.start);
     cudaEventCreate(&rec.stop);
@@ -477,12 +501,17 @@ molt_status molt_create(const molt_desc* descs, int count, void* cuda_stream, mo
       delete c;
       return fail(nullptr, MOLT_EUNSUPPORTED, "learned weights run with MOLT_PREC_F32");
     }
+    if (p.d.weights == MOLT_W_LEARNED && p.d.hamiltonian != MOLT_H_HALF_SQ) {
+      delete c;
+      return fail(nullptr, MOLT_EUNSUPPORTED, "learned weights run with H = |grad u|^2/2");
+    }
     c->probs.push_back(p);
   }
   cudaError_t e;
   if ((e = cudaMalloc(&c->status_dev, sizeof(int))) != cudaSuccess ||
       (e = cudaMalloc(&c->speed_dev, sizeof(unsigned long long) * 2 * count)) != cudaSuccess ||
-      (e = cudaMalloc(&c->t_dev, sizeof(double) * count)) != cudaSuccess) {
+      (e = cudaMalloc(&c->t_dev, sizeof(double) * count)) != cudaSuccess ||
+      (e = cudaMalloc(&c->tnow_dev, sizeof(double) * count)) != cudaSuccess) {
     molt_destroy(c);
     return fail(nullptr, MOLT_ENOMEM, std::string("workspace: ") + cudaGetErrorString(e));
   }
@@ -504,11 +533,13 @@ molt_status molt_create(const molt_desc* descs, int count, void* cuda_stream, mo
     bool ok = true;
     if ((p.d.ndim > 1 || is_mixed(p.d)) && p.d.pde != MOLT_PDE_HJ)
       ok = ok && cudaMalloc(&p.acc, cb * tot) == cudaSuccess;
-    if (p.d.pde == MOLT_PDE_HEAT) {
+    if (p.d.pde == MOLT_PDE_HEAT && p.d.integrator != MOLT_INT_EULER) {
       ok = ok && cudaMalloc(&p.stage1, sb * tot) == cudaSuccess;
       ok = ok && cudaMalloc(&p.stage2, sb * tot) == cudaSuccess;
     }
     if (p.d.pde == MOLT_PDE_HJ && p.d.ndim > 1) ok = ok && cudaMalloc(&p.hx, sb * tot) == cudaSuccess;
+    if (p.d.pde == MOLT_PDE_HJ && p.d.ndim > 1 && p.d.hamiltonian == MOLT_H_AFFINE_SQ)
+      ok = ok && cudaMalloc(&p.hx2, sb * tot) == cudaSuccess;
     if (ok && hj_transposed_y(c, p)) {
       ok = cudaMalloc(&p.tu, sb * tot) == cudaSuccess && cudaMalloc(&p.thx, sb * tot) == cudaSuccess;
     }
@@ -689,9 +720,12 @@ molt_status heat_step(molt_ctx* c, Problem& p, void* u) {
   const double alpha = step_alpha(p);
   const double coefS = -p.d.beta * p.d.beta;
   static const double rk[3][2] = {{0.0, 1.0}, {0.75, 0.25}, {1.0 / 3.0, 2.0 / 3.0}};
+  // forward Euler is the first stage written straight into u (pointwise, and
+  // every tile reads its lines before writing them)
+  const bool euler = p.d.integrator == MOLT_INT_EULER;
   void* ins[3] = {u, p.stage1, p.stage2};
-  void* dsts[3] = {p.stage1, p.stage2, u};
-  for (int s = 0; s < 3; ++s) {
+  void* dsts[3] = {euler ? u : p.stage1, p.stage2, u};
+  for (int s = 0; s < (euler ? 1 : 3); ++s) {
     for (int ax = 0; ax < p.d.ndim; ++ax) {
       Plan pl;
       molt_status st = plan_axis(c, p, ax, MODE_0, p.d.P, alpha, &pl);
@@ -824,6 +858,8 @@ molt_status transpose(molt_ctx* c, const Problem& p, const void* in, void* out, 
 // are rows.
 bool hj_transposed_y(molt_ctx* c, const Problem& p) {
   if (p.d.pde != MOLT_PDE_HJ || p.d.ndim != 2) return false;
+  // sigma/delta of AFFINE_SQ and source terms stay in the natural layout
+  if (p.d.hamiltonian == MOLT_H_AFFINE_SQ || p.src) return false;
   Problem q = p;                     // the tile shape does not depend on the weights
   q.d.weights = MOLT_W_WENOZ;
   Plan pl;
@@ -846,8 +882,10 @@ Problem transposed(const Problem& p) {
   return t;
 }
 
+// dst == nullptr: u is the destination; speed_only: the last pass only
+// measures the wave speeds (no store, no time advance).
 molt_status hj_pass(molt_ctx* c, Problem& p, int idx, void* u, int ax, int epi, unsigned long long* speed,
-                    const unsigned long long* lag, void* hx, void* dst = nullptr) {
+                    const unsigned long long* lag, void* hx, void* dst = nullptr, bool speed_only = false) {
   Plan pl;
   molt_status st = plan_axis(c, p, ax, MODE_RL, 1, step_alpha(p), &pl);
   if (st != MOLT_OK) return st;
@@ -859,9 +897,25 @@ molt_status hj_pass(molt_ctx* c, Problem& p, int idx, void* u, int ax, int epi, 
   pl.a.dst = dst ? dst : u;
   pl.a.speed = speed;
   pl.a.lag = lag;
-  pl.a.cfl_h = p.d.cfl * hmin;
+  pl.a.cfl = p.d.cfl;
+  pl.a.inv_h = 1.0 / p.h[ax];
   pl.a.dt_max = 10.0 * hmin;
   pl.a.t_dev = c->t_dev + idx;
+  if (hx && p.d.hamiltonian == MOLT_H_AFFINE_SQ) pl.a.out2 = p.hx2;
+  // the general kernels: other Hamiltonians, a source, speed-only passes
+  const bool general = p.d.hamiltonian != MOLT_H_HALF_SQ || (epi == EPI_HJ_Y && (p.src || speed_only));
+  if (epi == EPI_HJ_Y && p.src && !speed_only) {
+    pl.a.src = p.src;
+    pl.a.src_deg = p.src_deg;
+    pl.a.src_stride = p.total;
+    pl.a.t_now = c->tnow_dev + idx;
+  }
+  if (speed_only) {
+    pl.a.dst = nullptr;
+    pl.a.lag = nullptr;
+    pl.a.t_dev = nullptr;
+  }
+  if (general) epi = epi == EPI_HJ_X ? EPI_HJ_XG : EPI_HJ_YG;
   return run(c, p, epi, pl);
 }
 
@@ -872,13 +926,18 @@ molt_status hj_step(molt_ctx* c, Problem& p, int idx, void* u) {
   Problem pt;
   if (ty) pt = transposed(p);
   const long long ny = p.n[1], nx = p.n[0];
+  void* hxp = p.d.ndim > 1 ? p.hx : nullptr;
   if (!p.hj_lag_ready) {
     // speeds of u^0 serve as the lagged speeds of the first step (Algorithm 1)
     if ((e = cudaMemsetAsync(slots + 1, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "memset");
     for (int ax = 0; ax < p.d.ndim; ++ax) {
       molt_status st;
-      if (ty && ax == 1) {
+      if (p.d.hamiltonian == MOLT_H_AFFINE_SQ) {
+        // the speed needs every axis: the x pass, then a last pass that only measures
+        const bool last = ax + 1 == p.d.ndim;
+        st = hj_pass(c, p, idx, u, ax, last ? EPI_HJ_Y : EPI_HJ_X, slots + 1, nullptr, hxp, nullptr, last);
+      } else if (ty && ax == 1) {
         if ((st = transpose(c, p, u, p.tu, ny, nx)) != MOLT_OK) return st;
         st = hj_pass(c, pt, idx, p.tu, 0, EPI_HJ_X, slots + 1, nullptr, nullptr);
       } else {
@@ -898,6 +957,10 @@ molt_status hj_step(molt_ctx* c, Problem& p, int idx, void* u) {
     const bool last = ax + 1 == p.d.ndim;
     const int epi = last ? EPI_HJ_Y : EPI_HJ_X;
     molt_status st;
+    if (last && p.src &&
+        (e = cudaMemcpyAsync(c->tnow_dev + idx, c->t_dev + idx, sizeof(double), cudaMemcpyDeviceToDevice,
+                             c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "time copy");
     if (ty && ax == 1) {
       // y pass on the transposed state: rows of u^T; H^_x^T is read and
       // u^{n+1 T} written in its place, then transposed back into u
@@ -906,7 +969,7 @@ molt_status hj_step(molt_ctx* c, Problem& p, int idx, void* u) {
       if ((st = hj_pass(c, pt, idx, p.tu, 0, epi, slot, lag, p.thx, p.thx)) != MOLT_OK) return st;
       st = transpose(c, p, p.thx, u, nx, ny);
     } else {
-      st = hj_pass(c, p, idx, u, ax, epi, slot, lag, p.d.ndim > 1 ? p.hx : nullptr);
+      st = hj_pass(c, p, idx, u, ax, epi, slot, lag, hxp);
     }
     if (st != MOLT_OK) return st;
   }
@@ -927,7 +990,8 @@ bool batch_supported(const molt_ctx* c) {
   if (c->probs.size() < 2) return false;
   for (const auto& p : c->probs) {
     const molt_desc& d = p.d;
-    if (d.pde != MOLT_PDE_HEAT || d.prec != MOLT_PREC_F32_F64UPDATE || d.ndim != 2 || d.weights != MOLT_W_LINEAR)
+    if (d.pde != MOLT_PDE_HEAT || d.prec != MOLT_PREC_F32_F64UPDATE || d.ndim != 2 || d.weights != MOLT_W_LINEAR ||
+        d.integrator != MOLT_INT_DEFAULT)
       return false;
     for (int ax = 0; ax < 2; ++ax)
       if (!shape_ok(p.n[ax], 16) && !shape_ok(p.n[ax], 8) && !shape_ok(p.n[ax], 4)) return false;
@@ -1226,6 +1290,38 @@ molt_status molt_step(molt_ctx* c, void* const* u, void* const* u_prev, int nste
   return MOLT_OK;
 }
 
+molt_status molt_set_source(molt_ctx* c, int problem, const void* coef, int degree) {
+  if (!c) return fail(nullptr, MOLT_EINVAL, "null context");
+  if (problem < 0 || problem >= int(c->probs.size())) return fail(c, MOLT_EINVAL, "problem index out of range");
+  Problem& p = c->probs[problem];
+  if (p.d.pde != MOLT_PDE_HJ) return fail(c, MOLT_EINVAL, "source terms are for Hamilton-Jacobi problems");
+  if (coef && p.d.weights == MOLT_W_LEARNED)
+    return fail(c, MOLT_EUNSUPPORTED, "source terms run with linear or WENO-Z weights");
+  cudaError_t e;
+  if (!coef) {
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "source sync");
+    cudaFree(p.src);
+    p.src = nullptr;
+    p.src_deg = 0;
+    return MOLT_OK;
+  }
+  if (degree < 0 || degree > 4) return fail(c, MOLT_EINVAL, "source degree must be in 0..4");
+  if (reinterpret_cast<uintptr_t>(coef) & 15) return fail(c, MOLT_EINVAL, "source array must be 16-byte aligned");
+  const size_t bytes = size_t(degree + 1) * size_t(p.total) * state_bytes(p.d);
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "source sync");
+  cudaFree(p.src);
+  p.src = nullptr;
+  if ((e = cudaMalloc(&p.src, bytes)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, MOLT_ENOMEM, "source allocation failed");
+  }
+  if ((e = cudaMemcpyAsync(p.src, coef, bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "source copy");
+  p.src_deg = degree;
+  return MOLT_OK;
+}
+
 molt_status molt_set_option(molt_ctx* c, int option, int64_t value) {
   if (!c) return fail(nullptr, MOLT_EINVAL, "null context");
   if (option == MOLT_OPT_WAIT_LIMIT) {
@@ -1294,6 +1390,8 @@ molt_status molt_destroy(molt_ctx* c) {
     cudaFree(p.stage1);
     cudaFree(p.stage2);
     cudaFree(p.hx);
+    cudaFree(p.hx2);
+    cudaFree(p.src);
     cudaFree(p.tu);
     cudaFree(p.thx);
     cudaFree(p.shadow);
@@ -1305,6 +1403,7 @@ molt_status molt_destroy(molt_ctx* c) {
   cudaFree(c->status_dev);
   cudaFree(c->speed_dev);
   cudaFree(c->t_dev);
+  cudaFree(c->tnow_dev);
   cudaFree(c->mlp_blob);
   cudaFree(c->mlp_stats);
   delete c;

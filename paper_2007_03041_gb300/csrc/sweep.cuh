@@ -57,8 +57,24 @@ enum Epi {
   EPI_HEAT_FINAL = 3,  // dst = a0*un + a1*(us + coefS*(acc + S))
   EPI_WAVE_FINAL = 4,  // dst = 2u - uprev + coefS*(acc+S)  (or from rest)
   EPI_HJ_X = 5,        // hx = H^_x(D_R, D_L); speed max
-  EPI_HJ_Y = 6         // u -= dt*(hx + H^_y); speed max
+  EPI_HJ_Y = 6,        // u -= dt*H^; speed max
+  EPI_HJ_XG = 7,       // EPI_HJ_X for every Hamiltonian (HamKind)
+  EPI_HJ_YG = 8        // EPI_HJ_Y for every Hamiltonian, a source F(x, t), speed-only passes
 };
+// The general Hamilton-Jacobi kernels (XG/YG) carry more operands per point;
+// the |grad u|^2/2 kernels without a source keep their own instantiations.
+__host__ __device__ constexpr bool epi_hj_x(int e) { return e == EPI_HJ_X || e == EPI_HJ_XG; }
+__host__ __device__ constexpr bool epi_hj_y(int e) { return e == EPI_HJ_Y || e == EPI_HJ_YG; }
+__host__ __device__ constexpr bool epi_hj_gen(int e) { return e == EPI_HJ_XG || e == EPI_HJ_YG; }
+// Hamiltonian of the Hamilton-Jacobi step (values of molt_hamiltonian).
+//   HALF_SQ:   H = |grad u|^2/2, separable: each pass adds its axis's part of
+//              the local Lax-Friedrichs Hamiltonian
+//   LINEAR:    H = sum_d a_d u_d, separable (upwind: H^_d = a_d v^-_d for
+//              a_d > 0, a_d v^+_d for a_d < 0)
+//   AFFINE_SQ: H = (h0 + sum_d a_d u_d)^2/2, not separable: the x pass leaves
+//              sigma_x = a_x mean_x and delta_x = |a_x| (v^+_x - v^-_x)/2, the
+//              last pass forms H^ from all axes
+enum HamKind { HAM_HALF_SQ = 0, HAM_LINEAR = 1, HAM_AFFINE_SQ = 2 };
 enum Mode { MODE_L = 0, MODE_R = 1, MODE_0 = 2, MODE_RL = 3 };
 enum StatusBits { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
 
@@ -106,8 +122,19 @@ struct SweepArgs {
   // Hamilton-Jacobi
   const unsigned long long* lag;  // lagged speed (double bits)
   unsigned long long* speed;      // this pass's speed slot (double bits)
-  double cfl_h, dt_max;
+  // adaptive step (Eq. "adaptive time rule"): dt = cfl min_d h_d / c_d =
+  // cfl / max_d (c_d / h_d); the passes publish c_d / h_d
+  double cfl, dt_max, inv_h;   // inv_h = 1 / h of this pass's axis
   double* t_dev;            // time accumulator (HJ_Y, block 0)
+  int ham;                  // HamKind
+  int two_out;              // MODE_RL with AFFINE_SQ: a second line buffer (delta)
+  double vel, h0, vmax;     // a_d of this axis, h0, max_d |a_d| / h_d
+  float velf;
+  void* out2;               // AFFINE_SQ: delta_x (state type; written by the x pass, read by the last)
+  const void* src;          // source coefficients F_k, k = 0..src_deg (state type) or null
+  int src_deg;
+  long long src_stride;     // elements between F_k and F_{k+1}
+  const double* t_now;      // time of the state being advanced (read with a source)
   int* status;
   // learned weights (JQ_LEARNED kernels)
   const MlpBlob* mlp;               // BF16 network
@@ -344,6 +371,7 @@ struct TileSmem {
   double* carries;   // [W][4] compute-type (hi, lo) carry pairs (room for FP64)
   void* totals;      // [W][nwl][4] of T
   void* lines;       // [W][LS] of T
+  void* lines2;      // two_out: [W][LS] of T (delta of AFFINE_SQ)
   float* jloc;       // JQ_LEARNED: [W][2][LS] local integrals J_R, J_L
   MlpNet* net;       // JQ_LEARNED: the network
 };
@@ -362,6 +390,12 @@ __device__ __forceinline__ TileSmem carve(unsigned char* smem, const SweepArgs& 
   const size_t off = (size_t(4 * a.W) * sizeof(double) + size_t(a.W * a.nwl * 4) * sizeof(T) + 15) & ~size_t(15);
   t.lines = smem + off;
   *used = off + size_t(a.W) * a.LS * sizeof(T);
+  t.lines2 = nullptr;
+  if (a.two_out) {
+    const size_t l2 = (*used + 15) & ~size_t(15);
+    t.lines2 = smem + l2;
+    *used = l2 + size_t(a.W) * a.LS * sizeof(T);
+  }
   t.jloc = nullptr;
   t.net = nullptr;
   if constexpr (JQ == JQ_LEARNED) {
@@ -571,7 +605,8 @@ __device__ __forceinline__ void learned_local_integrals(const SweepArgs& a, cons
 // application needs no CTA-wide barrier: ghosts, line totals and the FP64
 // boundary solve stay inside the warp (the solve runs on lane 0 and its
 // result is broadcast by shuffles).
-template <typename T, int JQ, bool RAGGED, bool WL, int E = kE>
+// GEN: MODE_RL supports every HamKind (else |grad u|^2/2 only).
+template <typename T, int JQ, bool RAGGED, bool WL, int E = kE, bool GEN = false>
 __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSmem& sm, bool line_ok) {
   static_assert(JQ != JQ_LEARNED || sizeof(T) == 4, "learned weights run in FP32");
   const int nwl = a.nwl, n = a.g.n;
@@ -811,14 +846,34 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
       // one-sided derivatives v^- = alpha D_R, v^+ = -alpha D_L and the
       // per-axis part of the Lax-Friedrichs Hamiltonian (Sec. 2.5)
       const T al = pick<T>(a.alpha, a.alphaf);
+      if (!GEN || a.ham == HAM_HALF_SQ) {
 #pragma unroll
-      for (int k = 0; k < E; ++k) {
-        const T vm = al * (v[k] - Y[k].x);
-        const T vp = -al * (v[k] - Y[E - 1 - (k)].y);
-        const T r = fmax(fabs(vm), fabs(vp));
-        const T mean = T(0.5) * (vm + vp);
-        S[k] = T(0.5) * mean * mean + r * T(0.5) * (vm - vp);
-        if (line_ok && e0 + k < n) rmax = fmax(rmax, r);
+        for (int k = 0; k < E; ++k) {
+          const T vm = al * (v[k] - Y[k].x);
+          const T vp = -al * (v[k] - Y[E - 1 - (k)].y);
+          const T r = fmax(fabs(vm), fabs(vp));
+          const T mean = T(0.5) * (vm + vp);
+          S[k] = T(0.5) * mean * mean + r * T(0.5) * (vm - vp);
+          if (line_ok && e0 + k < n) rmax = fmax(rmax, r);
+        }
+      } else if constexpr (GEN) {
+        // H_d' = a_d (LINEAR) has |H_d'| = |a_d| everywhere; AFFINE_SQ
+        // leaves (sigma, delta) and the last pass takes the box maximum
+        const T av = pick<T>(a.vel, a.velf), aa = fabs(av);
+        T* cbase2 = static_cast<T*>(sm.lines2) + (cbase - lines);
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+          const T vm = al * (v[k] - Y[k].x);
+          const T vp = -al * (v[k] - Y[E - 1 - (k)].y);
+          const T mean = T(0.5) * (vm + vp);
+          if (a.ham == HAM_LINEAR) {
+            S[k] = av * mean + aa * T(0.5) * (vm - vp);
+          } else {
+            S[k] = av * mean;
+            if (RAGGED ? e0 + k < n : true) cbase2[chunk_off<E>(k)] = aa * T(0.5) * (vp - vm);
+          }
+        }
+        if (a.ham == HAM_LINEAR && line_ok) rmax = aa;
       }
     } else {
 #pragma unroll
@@ -863,15 +918,15 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
 #ifndef MOLT_WL_MODE
 #define MOLT_WL_MODE 0
 #endif
-template <typename T, int JQ, bool RAGGED, int E = kE>
+template <typename T, int JQ, bool RAGGED, int E = kE, bool GEN = false>
 __device__ __forceinline__ double compute_lines_any(const SweepArgs& a, const TileSmem& sm, bool line_ok) {
 #if MOLT_WL_MODE == 0
-  return compute_lines<T, JQ, RAGGED, false, E>(a, sm, line_ok);
+  return compute_lines<T, JQ, RAGGED, false, E, GEN>(a, sm, line_ok);
 #elif MOLT_WL_MODE == 2
-  return compute_lines<T, JQ, RAGGED, true, E>(a, sm, line_ok);
+  return compute_lines<T, JQ, RAGGED, true, E, GEN>(a, sm, line_ok);
 #else
-  if (a.nwl == 1) return compute_lines<T, JQ, RAGGED, true, E>(a, sm, line_ok);
-  return compute_lines<T, JQ, RAGGED, false, E>(a, sm, line_ok);
+  if (a.nwl == 1) return compute_lines<T, JQ, RAGGED, true, E, GEN>(a, sm, line_ok);
+  return compute_lines<T, JQ, RAGGED, false, E, GEN>(a, sm, line_ok);
 #endif
 }
 
@@ -888,6 +943,7 @@ template <typename T, typename TST, int EPI, bool CG = false>
 struct Epilogue {
   const SweepArgs& a;
   double dt;
+  double tn;   // general HJ_Y with a source: time of the state being advanced
 
   __device__ __forceinline__ EpiOps<T, TST> load(long long gidx) const {
     EpiOps<T, TST> o{T(0), TST(0), TST(0)};
@@ -897,7 +953,7 @@ struct Epilogue {
       if (a.acc) o.acc = gload<CG>(static_cast<const T*>(a.acc) + gidx);
       o.x = gload<CG>(static_cast<const TST*>(a.un) + gidx);
       if (EPI == EPI_HEAT_FINAL || !a.from_rest) o.y = gload<CG>(static_cast<const TST*>(a.us) + gidx);
-    } else if constexpr (EPI == EPI_HJ_Y) {
+    } else if constexpr (epi_hj_y(EPI)) {
       o.x = gload<CG>(static_cast<const TST*>(a.un) + gidx);
       if (a.out) o.y = gload<CG>(static_cast<const TST*>(a.out) + gidx);
     }
@@ -925,12 +981,62 @@ struct Epilogue {
       static_cast<TST*>(a.dst)[gidx] = r;
       if (a.shadow) a.shadow[gidx] = cvt<float>(r);
       if (nonfinite(r)) atomicOr(a.status, ST_NONFINITE);
-    } else if constexpr (EPI == EPI_HJ_X) {
+    } else if constexpr (epi_hj_x(EPI)) {
       if (a.out) static_cast<TST*>(a.out)[gidx] = TST(s);
-    } else if constexpr (EPI == EPI_HJ_Y) {
+    } else if constexpr (epi_hj_y(EPI)) {
       const TST r = o.x - TST(dt) * (o.y + TST(s));
       static_cast<TST*>(a.dst)[gidx] = r;
       if (nonfinite(r)) atomicOr(a.status, ST_NONFINITE);
+    }
+  }
+
+  // ---- general Hamilton-Jacobi passes (EPI_HJ_XG / EPI_HJ_YG)
+  // z: delta_x of AFFINE_SQ from the x pass (last pass), 0 otherwise
+  __device__ __forceinline__ TST load_z(long long gidx) const {
+    if constexpr (EPI == EPI_HJ_YG)
+      if (a.out2) return gload<CG>(static_cast<const TST*>(a.out2) + gidx);
+    return TST(0);
+  }
+
+  // F(x, t_n) = sum_k t_n^k F_k(x) (Horner)
+  __device__ __forceinline__ TST source(long long gidx) const {
+    const TST* f = static_cast<const TST*>(a.src) + gidx;
+    const TST t = TST(tn);
+    TST F = f[a.src_deg * a.src_stride];
+    for (int k = a.src_deg - 1; k >= 0; --k) F = fma(F, t, f[k * a.src_stride]);
+    return F;
+  }
+
+  // s2: the second line buffer's value (two_out).  Returns the point's
+  // scaled wave speed where the last pass determines it (AFFINE_SQ), else 0.
+  __device__ __forceinline__ T store_general(long long gidx, T s, const EpiOps<T, TST>& o, TST z, T s2) const {
+    if constexpr (EPI == EPI_HJ_XG) {
+      if (a.out) static_cast<TST*>(a.out)[gidx] = TST(s);
+      if (a.out2) static_cast<TST*>(a.out2)[gidx] = TST(s2);
+      return T(0);
+    } else {
+      TST H;
+      T speed = T(0);
+      if (a.ham == HAM_AFFINE_SQ) {
+        // local Lax-Friedrichs over the box of one-sided derivatives:
+        // |dH/dp_d| = |a_d| |h0 + a.p| is largest at a corner, where
+        // |h0 + a.p| reaches m = |sbar| + sum_d |delta_d|; then
+        // H^ = H(means) - sum_d |a_d| m (v^+_d - v^-_d)/2 = sbar^2/2 - m sum_d delta_d;
+        // the speeds c_d = |a_d| m enter as max_d c_d / h_d = m vmax
+        const TST sbar = TST(a.h0) + o.y + TST(s);
+        const TST m = fabs(sbar) + fabs(z) + fabs(TST(s2));
+        H = TST(0.5) * sbar * sbar - m * (z + TST(s2));
+        speed = T(TST(a.vmax) * m);
+      } else {
+        H = o.y + TST(s);
+      }
+      if (a.src) H -= source(gidx);
+      if (a.dst) {
+        const TST r = o.x - TST(dt) * H;
+        static_cast<TST*>(a.dst)[gidx] = r;
+        if (nonfinite(r)) atomicOr(a.status, ST_NONFINITE);
+      }
+      return speed;
     }
   }
 };
@@ -943,9 +1049,45 @@ struct Epilogue {
 #endif
 constexpr int kEpiBatch = MOLT_EPI_BATCH;
 
+// The epilogue of the general Hamilton-Jacobi passes over one thread's points
+// p0, p0 + pstep, ... of a line: shared values sp[k*pdelta] and sp2[k*pdelta]
+// (second line buffer, or null), global index g + k*gstep, B points per
+// batch with all loads of a batch issued before its stores.  Returns the
+// largest scaled wave speed it determined.
+template <typename T, typename TST, int EPI, bool CG, int B>
+__device__ __forceinline__ double epilogue_general(const Epilogue<T, TST, EPI, CG>& ep, const T* sp, const T* sp2,
+                                                   long long g, int p0, int n, int pstep, long long gstep,
+                                                   int pdelta) {
+  T rmax = T(0);
+  for (int pb = p0; pb < n; pb += B * pstep) {
+    EpiOps<T, TST> ops[B];
+    T sv[B], sv2[B];
+    TST oz[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      if (pb + k * pstep < n) {
+        ops[k] = ep.load(g + k * gstep);
+        oz[k] = ep.load_z(g + k * gstep);
+        sv[k] = sp[k * pdelta];
+        sv2[k] = sp2 ? sp2[k * pdelta] : T(0);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k)
+      if (pb + k * pstep < n) rmax = fmax(rmax, ep.store_general(g + k * gstep, sv[k], ops[k], oz[k], sv2[k]));
+    g += B * gstep;
+    sp += B * pdelta;
+    if (sp2) sp2 += B * pdelta;
+  }
+  return cvt<double>(rmax);
+}
+
+// Returns the largest wave speed the epilogue determined (HJ_Y with
+// AFFINE_SQ), else 0.  lines2: the second line buffer (two_out) or null.
 template <typename T, typename TST, int EPI, int E = kE, bool CG = false>
-__device__ __forceinline__ void epilogue_tile(const SweepArgs& a, const T* lines, long long line0, double dt) {
-  const Epilogue<T, TST, EPI, CG> ep{a, dt};
+__device__ __forceinline__ double epilogue_tile(const SweepArgs& a, const T* lines, long long line0, double dt,
+                                                const T* lines2 = nullptr) {
+  const Epilogue<T, TST, EPI, CG> ep{a, dt, (epi_hj_y(EPI) && epi_hj_gen(EPI) && a.src) ? *a.t_now : 0.0};
   const int W = a.W, n = a.g.n, nwl = a.nwl;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   long long g0;
@@ -954,7 +1096,7 @@ __device__ __forceinline__ void epilogue_tile(const SweepArgs& a, const T* lines
   long long gstep;
   if (a.contiguous) {
     const int lw = warp / nwl, tl = (warp - lw * nwl) * 32 + lane;
-    if (line0 + lw >= a.g.nlines) return;
+    if (line0 + lw >= a.g.nlines) return 0.0;
     p0 = tl;
     pstep = nwl * 32;
     g0 = line_base(a.g, line0 + lw) + p0;
@@ -964,7 +1106,7 @@ __device__ __forceinline__ void epilogue_tile(const SweepArgs& a, const T* lines
   } else {
     const int w = tid % W;
     const long long gl = line0 + w;
-    if (gl >= a.g.nlines) return;
+    if (gl >= a.g.nlines) return 0.0;
     p0 = tid / W;
     pstep = blockDim.x / W;
     g0 = line_base(a.g, gl) + p0 * a.g.stride;
@@ -977,40 +1119,48 @@ __device__ __forceinline__ void epilogue_tile(const SweepArgs& a, const T* lines
   // constant in both cases
   const int pdelta = pstep + pstep / E;
   const T* sp = src0 + phys<E>(p0);
-  long long g = g0;
-  for (int pb = p0; pb < n; pb += kEpiBatch * pstep) {
-    EpiOps<T, TST> ops[kEpiBatch];
-    T sv[kEpiBatch];
-#pragma unroll
-    for (int k = 0; k < kEpiBatch; ++k) {
-      if (pb + k * pstep < n) {
-        ops[k] = ep.load(g + k * gstep);
-        sv[k] = sp[k * pdelta];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kEpiBatch; ++k)
-      if (pb + k * pstep < n) ep.store(g + k * gstep, sv[k], ops[k]);
-    g += kEpiBatch * gstep;
-    sp += kEpiBatch * pdelta;
-  }
   (void)sstep;
+  if constexpr (epi_hj_gen(EPI)) {
+    // more operands per point: a smaller batch
+    return epilogue_general<T, TST, EPI, CG, 4>(ep, sp, lines2 ? lines2 + (sp - lines) : nullptr, g0, p0, n, pstep,
+                                                 gstep, pdelta);
+  } else {
+    long long g = g0;
+    for (int pb = p0; pb < n; pb += kEpiBatch * pstep) {
+      EpiOps<T, TST> ops[kEpiBatch];
+      T sv[kEpiBatch];
+#pragma unroll
+      for (int k = 0; k < kEpiBatch; ++k) {
+        if (pb + k * pstep < n) {
+          ops[k] = ep.load(g + k * gstep);
+          sv[k] = sp[k * pdelta];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kEpiBatch; ++k)
+        if (pb + k * pstep < n) ep.store(g + k * gstep, sv[k], ops[k]);
+      g += kEpiBatch * gstep;
+      sp += kEpiBatch * pdelta;
+    }
+    return 0.0;
+  }
 }
 
 template <int EPI>
 __device__ __forceinline__ double hj_dt(const SweepArgs& a) {
   double dt = 0.0;
-  if constexpr (EPI == EPI_HJ_Y) {
+  if constexpr (epi_hj_y(EPI)) {
+    if (!a.lag) return 0.0;   // a pass that only measures speeds
     const double cl = __longlong_as_double((long long)a.lag[0]);
     dt = a.dt_max;
-    if (cl > 0.0 && a.cfl_h / cl < dt) dt = a.cfl_h / cl;
+    if (cl > 0.0 && a.cfl / cl < dt) dt = a.cfl / cl;
   }
   return dt;
 }
 
 template <int EPI>
 __device__ __forceinline__ void publish_speed(const SweepArgs& a, double rmax) {
-  if constexpr (EPI == EPI_HJ_X || EPI == EPI_HJ_Y) {
+  if constexpr (epi_hj_x(EPI) || epi_hj_y(EPI)) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
     if ((threadIdx.x & 31) == 0 && rmax > 0.0 && a.speed)
@@ -1031,11 +1181,19 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) sweep_kernel(const Sw
   const int tl = (warp - lw * a.nwl) * 32 + (threadIdx.x & 31);
   load_tile<T, TIN, E>(a, static_cast<const TIN*>(a.in), lines, line0, lw, tl);
   __syncthreads();
-  const double rmax = compute_lines_any<T, JQ, RAGGED, E>(a, sm, line0 + lw < a.g.nlines);
-  publish_speed<EPI>(a, rmax);
-  const double dt = hj_dt<EPI>(a);
-  if (EPI == EPI_HJ_Y && blockIdx.x == 0 && threadIdx.x == 0 && a.t_dev) *a.t_dev += dt;
-  epilogue_tile<T, TST, EPI, E>(a, lines, line0, dt);
+  if constexpr (epi_hj_x(EPI) || epi_hj_y(EPI)) {
+    const double rmax =
+        compute_lines_any<T, JQ, RAGGED, E, epi_hj_gen(EPI)>(a, sm, line0 + lw < a.g.nlines) * a.inv_h;
+    // the general last pass finds its speeds in the epilogue
+    if constexpr (!epi_hj_gen(EPI)) publish_speed<EPI>(a, rmax);
+    const double dt = hj_dt<EPI>(a);
+    if (epi_hj_y(EPI) && blockIdx.x == 0 && threadIdx.x == 0 && a.t_dev) *a.t_dev += dt;
+    const double re = epilogue_tile<T, TST, EPI, E>(a, lines, line0, dt, static_cast<const T*>(sm.lines2));
+    if constexpr (epi_hj_gen(EPI)) publish_speed<EPI>(a, fmax(rmax, re));
+  } else {
+    compute_lines_any<T, JQ, RAGGED, E>(a, sm, line0 + lw < a.g.nlines);
+    epilogue_tile<T, TST, EPI, E>(a, lines, line0, 0.0);
+  }
 }
 
 }  // namespace molt

@@ -135,7 +135,7 @@ __device__ __forceinline__ void prefetch_operands(const SweepArgs& a, long long 
     ops[1] = a.un; es[1] = sizeof(TST);
     if (EPI == EPI_HEAT_FINAL || !a.from_rest) { ops[2] = a.us; es[2] = sizeof(TST); }
   }
-  if constexpr (EPI == EPI_HJ_Y) {
+  if constexpr (epi_hj_y(EPI)) {
     ops[0] = a.un; es[0] = sizeof(TST);
     ops[1] = a.out; es[1] = sizeof(TST);
   }
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
   const long long ntiles = (a.g.nlines + a.W - 1) / a.W;
   const int warp = threadIdx.x >> 5, lw = warp / a.nwl;
   const double dt = hj_dt<EPI>(a);
-  if (EPI == EPI_HJ_Y && blockIdx.x == 0 && threadIdx.x == 0 && a.t_dev) *a.t_dev += dt;
+  if (epi_hj_y(EPI) && blockIdx.x == 0 && threadIdx.x == 0 && a.t_dev) *a.t_dev += dt;
 
   long long tile = blockIdx.x;
   if (threadIdx.x == 0) {
@@ -249,8 +249,9 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
       }
       prefetch_operands<T, TST, EPI>(a, next * a.W);
     }
-    rmax = fmax(rmax, compute_lines_any<T, JQ, false>(a, sm, line0 + lw < a.g.nlines));
-    epilogue_tile<T, TST, EPI>(a, lines, line0, dt);
+    rmax = fmax(rmax, compute_lines_any<T, JQ, false, kE, epi_hj_gen(EPI)>(a, sm, line0 + lw < a.g.nlines) *
+                          a.inv_h);
+    rmax = fmax(rmax, epilogue_tile<T, TST, EPI>(a, lines, line0, dt, static_cast<const T*>(sm.lines2)));
     __syncthreads();
   }
   publish_speed<EPI>(a, rmax);

@@ -17,11 +17,13 @@ OP_L, OP_R, OP_0 = 0, 1, 2
 PREC_F64, PREC_F32_F64UPDATE, PREC_F32 = 0, 1, 2
 PDE_HEAT, PDE_WAVE, PDE_HJ = 0, 1, 2
 W_LINEAR, W_WENOZ, W_LEARNED = 0, 1, 2
+H_HALF_SQ, H_LINEAR, H_AFFINE_SQ = 0, 1, 2
+INT_DEFAULT, INT_EULER = 0, 1
 
 EXPORTS = ("molt_create", "molt_apply_D", "molt_step", "molt_set_option", "molt_profile_read", "molt_destroy",
            "molt_last_error", "molt_wave_step_noalloc", "molt_batch_tile_shape", "molt_set_mlp", "molt_mlp_stats",
            "molt_weno_linear_weights", "molt_mlp_pack", "molt_mlp_forward", "molt_mlp_loss_grad", "molt_mlp_adam",
-           "molt_mlp_harvest", "molt_quadrature_weights")
+           "molt_mlp_harvest", "molt_quadrature_weights", "molt_set_source")
 MLP_PARAMS = 1347
 MLP_BLOB_BYTES = 3728
 OPT_TMA, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_TEST_SKIP_ARRIVE = 0, 1, 2, 3
@@ -46,6 +48,10 @@ class molt_desc(ctypes.Structure):
         ("cfl", ctypes.c_double),
         ("dt", ctypes.c_double),
         ("prec", ctypes.c_int),
+        ("hamiltonian", ctypes.c_int),
+        ("velocity", ctypes.c_double * 3),
+        ("h0", ctypes.c_double),
+        ("integrator", ctypes.c_int),
     ]
 
 
@@ -83,6 +89,7 @@ def load_library(path=LIB_PATH):
         lib.molt_wave_step_noalloc.restype = ctypes.c_int
         vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
         lib.molt_set_mlp.argtypes = [vp, vp, ctypes.c_size_t]
+        lib.molt_set_source.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
         lib.molt_mlp_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.c_int]
         lib.molt_weno_linear_weights.argtypes = [dbl, ctypes.POINTER(dbl)]
         lib.molt_quadrature_weights.argtypes = [ctypes.c_int, dbl, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
@@ -93,7 +100,7 @@ def load_library(path=LIB_PATH):
         lib.molt_mlp_adam.argtypes = [vp, vp, vp, vp, i64, dbl, dbl, dbl, dbl, vp, vp]
         lib.molt_mlp_harvest.argtypes = [vp, i64, i64, vp, i64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl), vp,
                                          vp, i64, vp]
-        for f in ("molt_set_mlp", "molt_mlp_stats", "molt_weno_linear_weights", "molt_quadrature_weights",
+        for f in ("molt_set_mlp", "molt_set_source", "molt_mlp_stats", "molt_weno_linear_weights", "molt_quadrature_weights",
                   "molt_mlp_pack", "molt_mlp_forward",
                   "molt_mlp_loss_grad", "molt_mlp_adam", "molt_mlp_harvest"):
             getattr(lib, f).restype = ctypes.c_int
@@ -106,7 +113,8 @@ def load_library(path=LIB_PATH):
 
 
 def make_desc(shape_xyz, lo=None, hi=None, bc=None, P=1, quad_points=6, weights=W_LINEAR, beta=1.0,
-              pde=PDE_HEAT, c=1.0, diffusivity=1.0, cfl=1.0, dt=0.0, prec=PREC_F64):
+              pde=PDE_HEAT, c=1.0, diffusivity=1.0, cfl=1.0, dt=0.0, prec=PREC_F64, hamiltonian=H_HALF_SQ,
+              velocity=(0.0, 0.0, 0.0), h0=0.0, integrator=INT_DEFAULT):
     """Descriptor for a grid whose sizes are given x first (n_x, n_y, n_z)."""
     nd = len(shape_xyz)
     d = molt_desc()
@@ -118,6 +126,9 @@ def make_desc(shape_xyz, lo=None, hi=None, bc=None, P=1, quad_points=6, weights=
         d.bc[i] = (bc[i] if bc is not None and i < nd else BC_PERIODIC)
     d.P, d.quad_points, d.weights, d.beta = P, quad_points, weights, beta
     d.pde, d.c, d.diffusivity, d.cfl, d.dt, d.prec = pde, c, diffusivity, cfl, dt, prec
+    d.hamiltonian, d.h0, d.integrator = hamiltonian, h0, integrator
+    for i in range(3):
+        d.velocity[i] = velocity[i] if i < len(velocity) else 0.0
     return d
 
 
@@ -239,6 +250,20 @@ def molt_set_mlp(ctx, blob):
     if not blob.is_contiguous():
         raise ValueError("network blob must be contiguous")
     _check(lib, ctx, lib.molt_set_mlp(ctx, ctypes.c_void_p(blob.data_ptr()), blob.numel() * blob.element_size()))
+
+
+def molt_set_source(ctx, problem, coef, degree=None):
+    """Source F(x, t) = sum_k t^k coef[k] of a Hamilton-Jacobi problem: coef
+    is a CUDA tensor of shape (degree+1, *state shape) in the state dtype
+    (copied by the library), or None to remove the source."""
+    lib = load_library()
+    if coef is None:
+        _check(lib, ctx, lib.molt_set_source(ctx, problem, None, 0))
+        return
+    if not coef.is_contiguous():
+        raise ValueError("source coefficients must be contiguous")
+    deg = coef.shape[0] - 1 if degree is None else degree
+    _check(lib, ctx, lib.molt_set_source(ctx, problem, ctypes.c_void_p(coef.data_ptr()), deg))
 
 
 def molt_mlp_stats(ctx, reset=False):
