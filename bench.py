@@ -411,14 +411,16 @@ def _problem(config, prec=None):
     if config.startswith("paper_ex"):
         n = 5277
         h = 2 * math.pi / n
+        # prec: FP64 as the paper, or the reduced-precision form (FP32 state
+        # for Hamilton-Jacobi, FP32 sweeps with the FP64 update for heat)
         if config == "paper_ex2_diffusion":
             d = M.make_desc((n, n), lo=[0, 0], hi=[2 * math.pi] * 2, P=1, quad_points=6, beta=1.0, pde=M.PDE_HEAT,
-                            dt=h, prec=M.PREC_F64, integrator=M.INT_EULER)
+                            dt=h, prec=M.PREC_F64 if prec is None else prec, integrator=M.INT_EULER)
             return [d], [workloads.diffusion_initial(n)]
         ex1 = config == "paper_ex1_advection"
         d = M.make_desc((n, n), lo=[0, 0], hi=[2 * math.pi] * 2, P=1, quad_points=6, beta=1.0, pde=M.PDE_HJ,
-                        cfl=1.0, dt=0.0, prec=M.PREC_F64, hamiltonian=M.H_LINEAR if ex1 else M.H_AFFINE_SQ,
-                        velocity=(1.0, 1.0), h0=0.0 if ex1 else 1.0)
+                        cfl=1.0, dt=0.0, prec=M.PREC_F64 if prec is None else prec,
+                        hamiltonian=M.H_LINEAR if ex1 else M.H_AFFINE_SQ, velocity=(1.0, 1.0), h0=0.0 if ex1 else 1.0)
         return [d], [workloads.advection_initial(n) if ex1 else np.zeros((n, n))]
     if config == "batch64":
         sides = workloads.batched_sides()
@@ -451,7 +453,7 @@ def _timed_steps(config, steps, warmup, prec=None, blob=None, profile_kinds=()):
             if config == "paper_ex3_hj":
                 from paper_2007_03041_gb300 import workloads
                 M.molt_set_source(ctx, 0, torch.tensor(workloads.manufactured_hj_source(int(descs[0].n[0])),
-                                                       device="cuda"))
+                                                       device="cuda", dtype=torch.float32 if f32 else torch.float64))
             us = [torch.tensor(a, dtype=torch.float32 if f32 else torch.float64, device="cuda") for a in u0]
             t = M.molt_step(ctx, us, None, nsteps=warmup, t=[0.0] * len(us)) if warmup else [0.0] * len(us)
             if blob is not None and descs[0].weights == M.W_LEARNED:
@@ -485,7 +487,7 @@ def _timed_steps(config, steps, warmup, prec=None, blob=None, profile_kinds=()):
 PAPER_LINF = {"paper_ex1_advection": 2.874e-3, "paper_ex2_diffusion": 4.010e-4, "paper_ex3_hj": 2.674e-4}
 
 
-def _paper_final_error(config):
+def _paper_final_error(config, prec=None):
     """Runs a Sec. 5.1 test problem from t = 0 to its final time (2 pi, 1,
     0.5) and returns (L-infinity error against the exact solution, final t,
     steps)."""
@@ -493,14 +495,15 @@ def _paper_final_error(config):
     import torch
     from paper_2007_03041_gb300 import molt as M
     from paper_2007_03041_gb300 import workloads
-    descs, u0 = _problem(config)
+    descs, u0 = _problem(config, prec)
+    dt_ = torch.float32 if descs[0].prec == M.PREC_F32 else torch.float64
     n = int(descs[0].n[0])
     h = 2 * math.pi / n
     ctx = M.molt_create(descs)
     try:
         if config == "paper_ex3_hj":
-            M.molt_set_source(ctx, 0, torch.tensor(workloads.manufactured_hj_source(n), device="cuda"))
-        u = torch.tensor(u0[0], device="cuda")
+            M.molt_set_source(ctx, 0, torch.tensor(workloads.manufactured_hj_source(n), device="cuda", dtype=dt_))
+        u = torch.tensor(u0[0], device="cuda", dtype=dt_)
         if config == "paper_ex3_hj":
             t, steps = [0.0], 0
             while t[0] < 0.5:
@@ -515,7 +518,7 @@ def _paper_final_error(config):
             steps = round(1.0 / h)
             t = M.molt_step(ctx, [u], None, nsteps=steps, t=[0.0])
             exact = workloads.diffusion_solution(n, t[0])
-        err = float((u - torch.tensor(exact, device="cuda")).abs().max())
+        err = float((u.double() - torch.tensor(exact, device="cuda")).abs().max())
     finally:
         M.molt_destroy(ctx)
     return err, t[0], steps
@@ -576,7 +579,16 @@ def run_config(args):
     if stats is not None:
         extra["learned_stats"] = {"stencils": stats[0], "fallbacks": stats[1],
                                   "fallback_fraction": stats[1] / max(stats[0], 1)}
-    if args.compare:
+    if args.compare and args.config.startswith("paper_ex"):
+        # the reduced-precision form of the same problem: speed and final error
+        rp = M.PREC_F32_F64UPDATE if args.config == "paper_ex2_diffusion" else M.PREC_F32
+        ms_r, _, _, _ = _timed_steps(args.config, args.steps, args.warmup, prec=rp)
+        err_r, tf_r, _ = _paper_final_error(args.config, rp)
+        extra["reduced_precision_form"] = {
+            "prec": "f32 sweeps + f64 update" if rp == M.PREC_F32_F64UPDATE else "f32",
+            "value": dof / (ms_r / 1e3), "ms_per_step": ms_r, "speedup_vs_fp64": ms / ms_r,
+            "linf_vs_exact": err_r, "t_final": tf_r}
+    elif args.compare:
         ms64, us64, _, _ = _timed_steps(args.config, args.steps, args.warmup, prec=M.PREC_F64)
         num = sum(float(torch.linalg.norm(a.double() - b.double()) ** 2) for a, b in zip(us, us64))
         den = sum(float(torch.linalg.norm(b.double()) ** 2) for b in us64)

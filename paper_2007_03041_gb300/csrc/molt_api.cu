@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "coeffs.h"
+#include "line_constants.h"
 #include "molt.h"
 #include "sweep_launch.h"
 #include "batch.cuh"
@@ -228,22 +229,8 @@ molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, do
   if (!(nu > 0) || !std::isfinite(nu)) return fail(c, MOLT_EINVAL, "alpha*h must be positive and finite");
   QuadTable qt;
   if (!build_quadrature(p.d.quad_points, nu, &qt)) return fail(c, MOLT_EINVAL, "quadrature table construction failed");
-  for (int i = 0; i < 6; ++i) a.c[i] = qt.c[i];
-  for (int r = 0; r < 3; ++r) {
-    for (int j = 0; j < 4; ++j) a.sub[r][j] = qt.sub[r][j];
-    a.d[r] = qt.d[r];
-  }
-  a.q = qt.q;
-  a.qE = std::exp(-nu * double(E));
-  a.invq = std::exp(nu);
-  for (int i = 0; i < 6; ++i) a.cf[i] = float(a.c[i]);
-  for (int r = 0; r < 3; ++r) {
-    for (int j = 0; j < 3; ++j) a.subf[r][j] = float(a.sub[r][j]);
-    a.df[r] = float(a.d[r]);
-  }
-  a.qf = float(a.q);
-  a.qEf = float(a.qE);
-  a.alphaf = float(a.alpha);
+  const int N = a.bc == MOLT_BC_PERIODIC ? n : n - 1;  // intervals
+  set_line_constants(a, qt, N, E, compute_bytes(p.d) == 4);
   if (mode == MODE_RL) {
     a.ham = p.d.hamiltonian;
     a.vel = p.d.velocity[ax];
@@ -253,12 +240,6 @@ molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, do
     a.two_out = a.ham == MOLT_H_AFFINE_SQ ? 1 : 0;
   }
   if (a.g.nlines >= (1LL << 31)) return fail(c, MOLT_EUNSUPPORTED, "more than 2^31 lines along an axis");
-  const int N = a.bc == MOLT_BC_PERIODIC ? n : n - 1;  // intervals
-  a.mu = std::exp(-nu * double(N));
-  a.inv1mmu = 1.0 / (-std::expm1(-nu * double(N)));
-  a.invdet = 1.0 / (-std::expm1(-2.0 * nu * double(N)));
-  a.k2det = 2.0 * a.invdet;
-  a.k2detq = a.k2det * a.invq;
   // tile shape: nwl warps per line, W lines per CTA, <= kMaxThreads threads
   const int nwl = (n + 32 * E - 1) / (32 * E);
   if (nwl > kMaxThreads / 32) return fail(c, MOLT_EUNSUPPORTED, "line longer than 8192 points");

@@ -16,6 +16,7 @@
 #include <cstring>
 
 #include "coeffs.h"
+#include "line_constants.h"
 #include "molt.h"
 #include "sweep_launch.h"
 
@@ -70,27 +71,7 @@ bool plan(const molt_desc& d, int ax, double alpha, int* status, SweepArgs* a, i
   const double nu = alpha * h;
   QuadTable qt;
   if (!(nu > 0) || !std::isfinite(nu) || !build_quadrature(d.quad_points, nu, &qt)) return false;
-  for (int i = 0; i < 6; ++i) a->c[i] = qt.c[i];
-  for (int r = 0; r < 3; ++r) {
-    for (int j = 0; j < 4; ++j) a->sub[r][j] = qt.sub[r][j];
-    a->d[r] = qt.d[r];
-  }
-  a->q = qt.q;
-  a->qE = std::exp(-nu * double(kE));
-  a->invq = std::exp(nu);
-  for (int i = 0; i < 6; ++i) a->cf[i] = float(a->c[i]);
-  for (int r = 0; r < 3; ++r) {
-    for (int j = 0; j < 3; ++j) a->subf[r][j] = float(a->sub[r][j]);
-    a->df[r] = float(a->d[r]);
-  }
-  a->qf = float(a->q);
-  a->qEf = float(a->qE);
-  a->alphaf = float(a->alpha);
-  a->mu = std::exp(-nu * double(N));
-  a->inv1mmu = 1.0 / (-std::expm1(-nu * double(N)));
-  a->invdet = 1.0 / (-std::expm1(-2.0 * nu * double(N)));
-  a->k2det = 2.0 * a->invdet;
-  a->k2detq = a->k2det * a->invq;
+  set_line_constants(*a, qt, N, kE, true);   // FP32 sweeps
   const int nwl = (n + 32 * kE - 1) / (32 * kE);
   if (nwl > kMaxThreads / 32) return false;
   int W = 1;

@@ -267,3 +267,37 @@ def test_example3_manufactured_hj_5277():
     assert 0.5 <= t < 0.51
     ref = _paper_numbers()["linf_5277_hj"]
     assert ref / 2 < linf < ref * 2, linf
+
+
+@pytest.mark.parametrize("prec", [M.PREC_F32, M.PREC_F32_F64UPDATE])
+@pytest.mark.parametrize("npts", [3, 5, 6])
+def test_fp32_sweeps_keep_constants_in_the_kernel_of_D(npts, prec):
+    """sum_l c_l = 1 - q (App. C moments) makes D[const] = 0.  The FP32
+    sweeps run their recurrences with q rounded to FP32; their weights and
+    boundary constants are fitted to that q, so D[const] stays at the FP32
+    rounding floor of the sweep (measured up to 9.5e-7 relative, about 16
+    ulps, from the local sums and carries) for small nu as well; with the
+    weights rounded one by one it would be off by (q - q32)/(1 - q) on top,
+    up to 3e-6 at nu = 0.01."""
+    need_gpu()
+    import torch
+    n = 1000
+    h = 1.0 / n
+    worst = 0.0
+    for nu in (0.01, 0.013, 0.02, 0.031, 0.047, 0.07, 0.11, 0.3):
+        for bc in (M.BC_PERIODIC, M.BC_DIRICHLET):
+            d = M.make_desc((n,), bc=[bc], quad_points=npts, prec=prec)
+            hh = 1.0 / (n if bc == M.BC_PERIODIC else n - 1)
+            ctx = M.molt_create(d)
+            try:
+                dt_ = state_dtype(prec)
+                x = torch.full((n,), 0.75, dtype=dt_, device="cuda")
+                out = torch.empty_like(x)
+                M.molt_apply_D(ctx, 0, 0, M.OP_0 if bc == M.BC_DIRICHLET else M.OP_R, 1, nu / hh, x, out)
+                o = out.double().cpu().numpy()
+            finally:
+                M.molt_destroy(ctx)
+            # constants: J = (1 - q) v, I_R = (1 - q^i) v, and the periodic
+            # closure or the Dirichlet solve (A = B = v/2) give L^{-1} v = v
+            worst = max(worst, float(np.abs(o).max()) / 0.75)
+    assert worst < 1.5e-6, worst
