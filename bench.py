@@ -386,12 +386,23 @@ CONFIGS = {
     # the paper's own test problems (Sec. 5.1) on its 5277^2 grid: P = 1,
     # 6-point linear quadrature, forward Euler, FP64
     "paper_ex1_advection": dict(metric="DOF updates/sec (Sec. 5.1 Example 1, 2-D linear advection, 5277^2, FP64) on GB300",
-                                bytes_per_dof=40, bound="hbm", dtype="f64"),
+                                bytes_per_dof=40, bound="fp64", dtype="f64", fp64_inst_per_dof=54.2,
+                                dram_per_dof=41.0),
     "paper_ex2_diffusion": dict(metric="DOF updates/sec (Sec. 5.1 Example 2, 2-D diffusion, 5277^2, FP64) on GB300",
-                                bytes_per_dof=40, bound="hbm", dtype="f64"),
+                                bytes_per_dof=40, bound="fp64", dtype="f64", fp64_inst_per_dof=45.6,
+                                dram_per_dof=48.0),
     "paper_ex3_hj": dict(metric="DOF updates/sec (Sec. 5.1 Example 3, 2-D Hamilton-Jacobi with source, 5277^2, FP64) on GB300",
-                         bytes_per_dof=80, bound="hbm", dtype="f64"),
+                         bytes_per_dof=80, bound="fp64", dtype="f64", fp64_inst_per_dof=65.2, dram_per_dof=104.4),
 }
+# FP64-bound lines: FP64 thread-instructions (DFMA + DADD + DMUL) and DRAM bytes
+# per DOF per step from one ncu capture of the step's sweeps at 4096^2 (both
+# scale with the points); peak = the nominal 1.25 TFLOP/s FP64 rate as thread-
+# instructions: 2 per SM per cycle, 304 over the GPU, at the 2070 MHz maximum
+# SM clock
+FP64_PEAK_GINST = 304 * 2.070
+# grid side of the paper_ex* configs: the paper's 5277 (--size overrides it for
+# profiling at other sizes; the final-time errors are reported at 5277 only)
+PAPER_N = 5277
 # Sec. 4.5 / Sec. 5: the paper's sustained rate on one CPU node (2 x Xeon Gold
 # 6148) for these test problems; a context figure from other hardware
 PAPER_NODE_DOF_PER_S = 1e8
@@ -409,7 +420,7 @@ def _problem(config, prec=None):
                         prec=M.PREC_F64 if prec is None else prec)
         return [d], [workloads.heat_modes(n)]
     if config.startswith("paper_ex"):
-        n = 5277
+        n = PAPER_N
         h = 2 * math.pi / n
         # prec: FP64 as the paper, or the reduced-precision form (FP32 state
         # for Hamilton-Jacobi, FP32 sweeps with the FP64 update for heat)
@@ -527,7 +538,12 @@ def _paper_final_error(config, prec=None):
 def run_config(args):
     import torch
     from paper_2007_03041_gb300 import molt as M
-    cfg = CONFIGS[args.config]
+    global PAPER_N
+    if args.size:
+        PAPER_N = args.size
+    cfg = dict(CONFIGS[args.config])
+    if args.config.startswith("paper_ex"):
+        cfg["metric"] = cfg["metric"].replace("5277^2", "%d^2" % PAPER_N)
     descs, _ = _problem(args.config)
     dof = sum(int(d.n[0] * d.n[1] * d.n[2]) for d in descs)
     extra = {}
@@ -558,6 +574,14 @@ def run_config(args):
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = cfg["bytes_per_dof"] * dof / (ms / 1e3) / 1e9
+    if cfg["bound"] == "fp64":
+        ach = cfg["fp64_inst_per_dof"] * dof / (ms / 1e3) / 1e9
+        roof = {"bound": "fp64", "achieved": ach, "peak": FP64_PEAK_GINST,
+                "unit": "G FP64 thread-instructions/s", "frac": ach / FP64_PEAK_GINST,
+                "traffic": cfg["dram_per_dof"] * dof, "scope": "whole step",
+                "fp64_inst_per_dof_step": cfg["fp64_inst_per_dof"],
+                "hbm_gbs_algorithmic": achieved, "per_kind_ms_per_step": None,
+                "peak_source": "nominal (ncu sustained FP64 rate x maximum SM clock)"}
     line = {
         "metric": cfg["metric"], "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -569,7 +593,10 @@ def run_config(args):
                      "per_kind_ms_per_step": per_kind,
                      "peak_source": "measured" if peaks else "fallback"},
     }
-    if args.config.startswith("paper_ex"):
+    if cfg["bound"] == "fp64":
+        roof["per_kind_ms_per_step"] = per_kind
+        line["roofline"] = roof
+    if args.config.startswith("paper_ex") and PAPER_N == 5277:
         err, tf, nst = _paper_final_error(args.config)
         extra["final_error"] = {"linf_vs_exact": err, "t_final": tf, "steps": nst,
                                 "paper_linf_5277": PAPER_LINF[args.config]}
@@ -583,11 +610,12 @@ def run_config(args):
         # the reduced-precision form of the same problem: speed and final error
         rp = M.PREC_F32_F64UPDATE if args.config == "paper_ex2_diffusion" else M.PREC_F32
         ms_r, _, _, _ = _timed_steps(args.config, args.steps, args.warmup, prec=rp)
-        err_r, tf_r, _ = _paper_final_error(args.config, rp)
         extra["reduced_precision_form"] = {
             "prec": "f32 sweeps + f64 update" if rp == M.PREC_F32_F64UPDATE else "f32",
-            "value": dof / (ms_r / 1e3), "ms_per_step": ms_r, "speedup_vs_fp64": ms / ms_r,
-            "linf_vs_exact": err_r, "t_final": tf_r}
+            "value": dof / (ms_r / 1e3), "ms_per_step": ms_r, "speedup_vs_fp64": ms / ms_r}
+        if PAPER_N == 5277:
+            err_r, tf_r, _ = _paper_final_error(args.config, rp)
+            extra["reduced_precision_form"].update(linf_vs_exact=err_r, t_final=tf_r)
     elif args.compare:
         ms64, us64, _, _ = _timed_steps(args.config, args.steps, args.warmup, prec=M.PREC_F64)
         num = sum(float(torch.linalg.norm(a.double() - b.double()) ** 2) for a, b in zip(us, us64))
@@ -611,6 +639,8 @@ def main():
                     help="nx,ny,nz (smaller grids are for profiler captures; the metric is quoted at 512^3)")
     ap.add_argument("--config", default="wave512", choices=["wave512"] + sorted(CONFIGS),
                     help="workload (default: the 3-D wave step the metric is quoted on)")
+    ap.add_argument("--size", type=int, default=None,
+                    help="grid side of the paper_ex* configs (default: the paper's 5277)")
     ap.add_argument("--compare", action="store_true",
                     help="also time the plain FP64 GPU form and report the speedup and the difference")
     args = ap.parse_args()
