@@ -51,3 +51,23 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert r.returncode == 0, r.stderr[-2000:]
     lines = _json_lines(r.stdout)
     assert len(lines) == 1 and lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2
+
+
+def test_paper_configs_build_the_sec51_problems():
+    """The paper_ex* bench workloads are the Sec. 5.1 test problems on the
+    paper's 5277^2 grid (FP64, P = 1, 6-point rule, CFL 1, beta 1)."""
+    import math
+    import bench
+    from paper_2007_03041_gb300 import molt as M
+    d1, u1 = bench._problem("paper_ex1_advection")
+    d2, u2 = bench._problem("paper_ex2_diffusion")
+    d3, u3 = bench._problem("paper_ex3_hj")
+    for d in (d1[0], d2[0], d3[0]):
+        assert (d.n[0], d.n[1], d.P, d.quad_points, d.beta, d.prec) == (5277, 5277, 1, 6, 1.0, M.PREC_F64)
+        assert abs(d.hi[0] - 2 * math.pi) < 1e-15
+    assert (d1[0].pde, d1[0].hamiltonian, tuple(d1[0].velocity)[:2], d1[0].cfl) == (M.PDE_HJ, M.H_LINEAR, (1.0, 1.0), 1.0)
+    assert (d2[0].pde, d2[0].integrator) == (M.PDE_HEAT, M.INT_EULER)
+    assert abs(d2[0].dt - 2 * math.pi / 5277) < 1e-18
+    assert (d3[0].hamiltonian, d3[0].h0) == (M.H_AFFINE_SQ, 1.0)
+    assert u1[0].shape == (5277, 5277) and float(abs(u3[0]).max()) == 0.0
+    assert abs(float(u2[0][5277 // 4, 0]) - 1.0) < 1e-3      # sin(x) + sin(y) at y ~ pi/2, x = 0 ([y][x])
