@@ -114,3 +114,17 @@ def test_errors_are_reported():
         assert ei.value.status == M.MOLT_EINVAL
     finally:
         M.molt_destroy(ctx)
+
+
+@pytest.mark.parametrize("bc", [M.BC_PERIODIC, M.BC_DIRICHLET])
+def test_fp64_multiwarp_tile_shapes(bc):
+    """FP64 sweeps take the fewest points per lane that fit a line exactly
+    (4 or 8), so lines of 256..4096 points run 2-16 warps per line: contiguous
+    and strided lines of those lengths against the oracle."""
+    need_gpu()
+    # numpy shapes; axis 0 = x (the last numpy axis, contiguous), 1 = y (strided)
+    for shape, axis in (((256,), 0), ((512,), 0), ((1536,), 0), ((4096,), 0), ((256, 3), 1), ((512, 6), 1),
+                        ((1024, 4), 1), ((4, 1024), 0)):
+        for op in (M.OP_0, M.OP_R):
+            got, want = run_apply(shape, axis, op, 2, 0.21, bc, 6, M.PREC_F64, seed=len(shape) + shape[0])
+            assert rel_l2(got, want) < 1e-12, (shape, axis, op)
