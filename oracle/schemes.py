@@ -175,3 +175,50 @@ def heat_euler_step(u, dxs, dt, kappa=1.0, beta=1.0, bc=None, npts=6, P=1):
     bc = bc or [BC_PERIODIC] * u.ndim
     un = np.asarray(u, dtype=np.float64)
     return un + heat_rhs_dt(un, dxs, dt, kappa, beta, bc, npts, P)
+
+
+# ---------------------------------------------------------------- advection-diffusion
+# Sec. 2.5: u_t + sum_d d_d g(u) = kappa Lap u, the flux split by global
+# Lax-Friedrichs, g = g^+ + g^-, g^{+-} = (g(u) +- c u)/2 with c >= max |g'(u)|
+# (reading: the paper's r = max g1' taken as a bound c given with the
+# problem, so the operators' alpha stays fixed), the upwind derivatives
+# d^- g^+ = alpha sum_p D_R^p[g^+] and d^+ g^- = -alpha sum_p D_L^p[g^-]
+# (Sec. 2.2), alpha = beta/(c dt), and the diffusion -kappa alpha_nu^2
+# sum_p D_0^p[u] with alpha_nu = beta/sqrt(kappa dt).  Hence
+#   dt F(u) = -(beta/c) sum_d (S_R[g_d^+] - S_L[g_d^-]) - beta^2 sum_d S_0[u].
+FLUX_LINEAR, FLUX_BURGERS = "linear", "burgers"
+
+
+def flux(kind, u, a=1.0):
+    """g(u): a u (linear) or u^2/2 (Burgers)."""
+    return a * u if kind == FLUX_LINEAR else 0.5 * u * u
+
+
+def advdiff_rhs_dt(u, dxs, dt, kind, a, c, kappa, beta, npts, P, bc=None):
+    """dt * F(u); a[d] per array axis (linear flux), c the splitting bound."""
+    bc = bc or [BC_PERIODIC] * u.ndim
+    alpha = beta / (c * dt)
+    out = np.zeros_like(u)
+    for ax in range(u.ndim):
+        g = flux(kind, u, a[ax] if kind == FLUX_LINEAR else 1.0)
+        gp = 0.5 * (g + c * u)
+        gm = 0.5 * (g - c * u)
+        dminus = alpha * partial_sum(gp, ax, alpha, dxs[ax], "R", bc[ax], npts, P)
+        dplus = -alpha * partial_sum(gm, ax, alpha, dxs[ax], "L", bc[ax], npts, P)
+        out = out - dt * (dminus + dplus)
+    if kappa > 0:
+        an = beta / np.sqrt(kappa * dt)
+        for ax in range(u.ndim):
+            out = out - kappa * dt * an * an * partial_sum(u, ax, an, dxs[ax], "0", bc[ax], npts, P)
+    return out
+
+
+def advdiff_step(u, dxs, dt, kind, a, c, kappa=0.0, beta=1.0, npts=6, P=1, rk3=False):
+    """One step: forward Euler, or the 3-stage SSP Runge-Kutta method (Shu-Osher form)."""
+    un = np.asarray(u, dtype=np.float64)
+    if not rk3:
+        return un + advdiff_rhs_dt(un, dxs, dt, kind, a, c, kappa, beta, npts, P)
+    us = un
+    for a0, a1 in SSPRK3:
+        us = a0 * un + a1 * (us + advdiff_rhs_dt(us, dxs, dt, kind, a, c, kappa, beta, npts, P))
+    return us
