@@ -391,6 +391,12 @@ CONFIGS = {
     "paper_ex2_diffusion": dict(metric="DOF updates/sec (Sec. 5.1 Example 2, 2-D diffusion, 5277^2, FP64) on GB300",
                                 bytes_per_dof=40, bound="fp64", dtype="f64", fp64_inst_per_dof=45.6,
                                 dram_per_dof=48.0),
+    # Sec. 2.5 flux-split advection-diffusion: 2-D viscous Burgers, FP32,
+    # WENO-Z, forward Euler with P = 1; per step and axis: split fluxes (read
+    # u, write g+, g-), three accumulating sweeps (12 B each), plus the memset
+    # of acc and the update (read acc + u, write u)
+    "advdiff_burgers4096": dict(metric="DOF updates/sec (2-D viscous Burgers, 4096^2, flux-split, WENO-Z, FP32) on GB300",
+                                bytes_per_dof=112, bound="hbm", dtype="f32"),
     "paper_ex3_hj": dict(metric="DOF updates/sec (Sec. 5.1 Example 3, 2-D Hamilton-Jacobi with source, 5277^2, FP64) on GB300",
                          bytes_per_dof=80, bound="fp64", dtype="f64", fp64_inst_per_dof=65.2, dram_per_dof=104.4),
 }
@@ -433,6 +439,13 @@ def _problem(config, prec=None):
                         cfl=1.0, dt=0.0, prec=M.PREC_F64 if prec is None else prec,
                         hamiltonian=M.H_LINEAR if ex1 else M.H_AFFINE_SQ, velocity=(1.0, 1.0), h0=0.0 if ex1 else 1.0)
         return [d], [workloads.advection_initial(n) if ex1 else np.zeros((n, n))]
+    if config == "advdiff_burgers4096":
+        n = 4096
+        h = 2 * math.pi / n
+        d = M.make_desc((n, n), lo=[0, 0], hi=[2 * math.pi] * 2, P=1, quad_points=5, weights=M.W_WENOZ, beta=0.6,
+                        pde=M.PDE_ADVDIFF, c=1.2, diffusivity=2e-3, dt=0.5 * h / 1.2,
+                        prec=M.PREC_F32 if prec is None else prec, flux=M.FLUX_BURGERS, integrator=M.INT_EULER)
+        return [d], [workloads.burgers_initial(n)]
     if config == "batch64":
         sides = workloads.batched_sides()
         descs = [M.make_desc((n, n), P=3, quad_points=3, beta=0.6, pde=M.PDE_HEAT, dt=0.5 / n,
@@ -568,6 +581,8 @@ def run_config(args):
              "paper_ex1_advection": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y),
                                      ("transpose", M.KERNEL_TRANSPOSE)),
              "paper_ex2_diffusion": (("sweep_final", M.KERNEL_HEAT_FINAL), ("sweep_acc", M.KERNEL_ACC_SET)),
+             "advdiff_burgers4096": (("flux", M.KERNEL_FLUX), ("sweeps", M.KERNEL_ACC_ADD),
+                                     ("update", M.KERNEL_UPDATE)),
              "paper_ex3_hj": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y))}[args.config]
     ms, us, per_kind, stats = _timed_steps(args.config, args.steps, args.warmup, blob=blob, profile_kinds=kinds)
     value = dof / (ms / 1e3)

@@ -61,7 +61,11 @@ typedef enum {
   MOLT_PREC_F32_F64UPDATE = 1,  /* FP64 state, FP32 sweeps, FP64 A/B and update    */
   MOLT_PREC_F32 = 2             /* FP32 state and sweeps, FP64 A/B                 */
 } molt_prec;
-typedef enum { MOLT_PDE_HEAT = 0, MOLT_PDE_WAVE = 1, MOLT_PDE_HJ = 2 } molt_pde;
+typedef enum { MOLT_PDE_HEAT = 0, MOLT_PDE_WAVE = 1, MOLT_PDE_HJ = 2, MOLT_PDE_ADVDIFF = 3 } molt_pde;
+/* Flux of the advection-diffusion problem u_t + sum_d d_d g_d(u) = kappa Lap u
+ * (Sec. 2.5): MOLT_FLUX_LINEAR g_d = a_d u (a_d = velocity[d]),
+ * MOLT_FLUX_BURGERS g_d = u^2/2 on every axis. */
+typedef enum { MOLT_FLUX_LINEAR = 0, MOLT_FLUX_BURGERS = 1 } molt_flux;
 typedef enum { MOLT_W_LINEAR = 0, MOLT_W_WENOZ = 1, MOLT_W_LEARNED = 2 } molt_weights;
 /* Hamiltonian of the Hamilton-Jacobi step (Sec. 2.5, and the test problems
  * of Sec. 5.1: Example 1 is H = u_x + u_y, Example 3 H = (1 + u_x + u_y)^2/2),
@@ -100,6 +104,7 @@ typedef struct {
   double velocity[3];    /* a_d of MOLT_H_LINEAR / MOLT_H_AFFINE_SQ              */
   double h0;             /* constant of MOLT_H_AFFINE_SQ                         */
   int integrator;        /* molt_integrator                                      */
+  int flux;              /* molt_flux (advection-diffusion)                      */
 } molt_desc;
 
 typedef struct molt_ctx molt_ctx;
@@ -139,6 +144,14 @@ molt_status molt_apply_D(molt_ctx* ctx, int problem, int axis, int op, int P, do
  * with the wave speeds c_d of the previous step (Eq. "adaptive time rule",
  * Algorithm 1; the speeds of u^0 on the first step; at most 10 min_d h_d), and
  * the source F of molt_set_source (0 if none).
+ * Advection-diffusion (periodic, 1-3 D, fixed dt): the flux split by global
+ * Lax-Friedrichs, g = g^+ + g^-, g^{+-} = (g(u) +- c u)/2 with desc.c >=
+ * max |g'(u)| over the run, upwind sums d^- g^+ = alpha sum_p D_R^p[g^+],
+ * d^+ g^- = -alpha sum_p D_L^p[g^-] with alpha = beta/(c dt), and the
+ * diffusion -kappa alpha_nu^2 sum_p D_0^p[u], alpha_nu = beta/sqrt(kappa dt),
+ * so dt F = -(beta/c) sum_d (S_R[g_d^+] - S_L[g_d^-]) - beta^2 sum_d S_0[u];
+ * 3-stage SSP Runge-Kutta (MOLT_INT_DEFAULT) or forward Euler.  Linear or
+ * WENO-Z weights (WENO-Z: 5 points, MOLT_PREC_F64 or MOLT_PREC_F32).
  * Synchronous at the end (reads t and the device status). */
 molt_status molt_step(molt_ctx* ctx, void* const* u, void* const* u_prev, int nsteps, double* t_inout);
 
@@ -184,8 +197,9 @@ typedef enum {
   MOLT_KERNEL_HJ_Y = 6,        /* Hamilton-Jacobi: last axis + update         */
   MOLT_KERNEL_UPDATE = 7,      /* FP64 state update of the FP32-sweep forms   */
   MOLT_KERNEL_BATCH = 8,       /* one persistent batched heat step            */
-  MOLT_KERNEL_TRANSPOSE = 9    /* state transposes of the 2-D Hamilton-Jacobi
+  MOLT_KERNEL_TRANSPOSE = 9,   /* state transposes of the 2-D Hamilton-Jacobi
                                   y pass on long lines                        */
+  MOLT_KERNEL_FLUX = 10        /* advection-diffusion: split fluxes g^+, g^-  */
 } molt_kernel_kind;
 
 /* With MOLT_OPT_PROFILE on: synchronises the stream, returns the summed

@@ -15,7 +15,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmolt.so")
 
-SOURCES = ["molt_api.cu", "sweep_f64.cu", "sweep_mixed.cu", "sweep_f32.cu", "sweep_hj_general.cu", "noalloc.cu", "mlp.cu",
+SOURCES = ["molt_api.cu", "sweep_f64.cu", "sweep_mixed.cu", "sweep_f32.cu", "sweep_hj_general.cu", "sweep_advdiff.cu",
+           "noalloc.cu", "mlp.cu",
            "coeffs.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]

@@ -38,6 +38,8 @@ struct Problem {
   void* tu = nullptr;       // HJ, transposed y pass: u^T and (H^_x)^T / u^{n+1}^T
   void* thx = nullptr;
   float* shadow = nullptr;  // FP32 copy of the state the sweeps read (mixed precision)
+  void* gp = nullptr;       // advection-diffusion: split fluxes g^+, g^- (compute type)
+  void* gm = nullptr;
   int64_t hj_steps = 0;     // HJ steps taken (rotates the speed slots)
   bool hj_lag_ready = false;
 };
@@ -114,7 +116,8 @@ std::string validate(const molt_desc& d) {
     return "unknown weights";
   if (d.weights != MOLT_W_LINEAR && d.quad_points != 5) return "WENO weights need quad_points = 5";
   if (d.prec < 0 || d.prec > 2) return "unknown precision";
-  if (d.pde < 0 || d.pde > 2) return "unknown pde";
+  if (d.pde < 0 || d.pde > 3) return "unknown pde";
+  if (d.flux != MOLT_FLUX_LINEAR && d.flux != MOLT_FLUX_BURGERS) return "unknown flux";
   if (!(d.beta > 0)) return "beta must be positive";
   if (d.hamiltonian < MOLT_H_HALF_SQ || d.hamiltonian > MOLT_H_AFFINE_SQ) return "unknown hamiltonian";
   for (int ax = 0; ax < 3; ++ax)
@@ -360,6 +363,7 @@ cudaError_t dispatch_lin(int epi, const Plan& pl, cudaStream_t s) {
     case EPI_ACC_ADD: return launch_sweep<T, TIN, TST, JQ_LINEAR, EPI_ACC_ADD>(a, TMA, pl.grid, pl.block, pl.smem, s);
     case EPI_HEAT_FINAL: return launch_sweep<T, TIN, TST, JQ_LINEAR, EPI_HEAT_FINAL>(a, TMA, pl.grid, pl.block, pl.smem, s);
     case EPI_WAVE_FINAL: return launch_sweep<T, TIN, TST, JQ_LINEAR, EPI_WAVE_FINAL>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    case EPI_ACC_AXPY: return launch_sweep<T, TIN, TST, JQ_LINEAR, EPI_ACC_AXPY>(a, TMA, pl.grid, pl.block, pl.smem, s);
     default: return cudaErrorNotSupported;
   }
 }
@@ -373,6 +377,7 @@ cudaError_t dispatch_same(int jq, int epi, const Plan& pl, cudaStream_t s) {
     if (epi == EPI_HJ_Y) return launch_sweep<T, T, T, JQ_WENOZ, EPI_HJ_Y>(a, TMA, pl.grid, pl.block, pl.smem, s);
     if (epi == EPI_HJ_XG) return launch_sweep<T, T, T, JQ_WENOZ, EPI_HJ_XG>(a, TMA, pl.grid, pl.block, pl.smem, s);
     if (epi == EPI_HJ_YG) return launch_sweep<T, T, T, JQ_WENOZ, EPI_HJ_YG>(a, TMA, pl.grid, pl.block, pl.smem, s);
+    if (epi == EPI_ACC_AXPY) return launch_sweep<T, T, T, JQ_WENOZ, EPI_ACC_AXPY>(a, TMA, pl.grid, pl.block, pl.smem, s);
     return cudaErrorNotSupported;
   }
   if (jq == JQ_LEARNED) {
@@ -416,7 +421,10 @@ molt_status run(molt_ctx* c, const Problem& p, int epi, Plan& pl, bool from_stat
   const size_t in_bytes = is_f32_state(p.d) || (is_mixed(p.d) && from_state_copy) ? 4 : 8;
   if (!c->no_tma && p.d.weights != MOLT_W_LEARNED) plan_tma(p, pl.ax, pl.a.in, in_bytes, &pl);
   // profiling kind: the general Hamilton-Jacobi passes count as HJ_X / HJ_Y
-  molt_ctx::Rec rec{epi_hj_x(epi) ? int(EPI_HJ_X) : (epi_hj_y(epi) ? int(EPI_HJ_Y) : epi), nullptr, nullptr};
+  // (the advection-diffusion accumulations count as ACC_ADD)
+  molt_ctx::Rec rec{epi_hj_x(epi) ? int(EPI_HJ_X)
+                                   : (epi_hj_y(epi) ? int(EPI_HJ_Y) : (epi == EPI_ACC_AXPY ? int(EPI_ACC_ADD) : epi)),
+                    nullptr, nullptr};
   if (c->profile) {
     cudaEventCreate(&rec.start);
     cudaEventCreate(&rec.stop);
@@ -499,6 +507,19 @@ molt_status molt_create(const molt_desc* descs, int count, void* cuda_stream, mo
       delete c;
       return fail(nullptr, MOLT_EUNSUPPORTED, "learned weights run with H = |grad u|^2/2");
     }
+    if (p.d.pde == MOLT_PDE_ADVDIFF) {
+      std::string why;
+      for (int ax = 0; ax < p.d.ndim; ++ax)
+        if (p.d.bc[ax] != MOLT_BC_PERIODIC) why = "advection-diffusion needs periodic axes";
+      if (!(p.d.c > 0) || !std::isfinite(p.d.c)) why = "advection-diffusion needs the splitting bound c > 0";
+      if (!(p.d.diffusivity >= 0) || !std::isfinite(p.d.diffusivity)) why = "diffusivity must be >= 0";
+      if (p.d.weights == MOLT_W_LEARNED || (p.d.weights == MOLT_W_WENOZ && is_mixed(p.d)))
+        why = "advection-diffusion runs linear weights, or WENO-Z in MOLT_PREC_F64 / MOLT_PREC_F32";
+      if (!why.empty()) {
+        delete c;
+        return fail(nullptr, MOLT_EUNSUPPORTED, why);
+      }
+    }
     c->probs.push_back(p);
   }
   cudaError_t e;
@@ -525,8 +546,13 @@ molt_status molt_create(const molt_desc* descs, int count, void* cuda_stream, mo
     const size_t cb = compute_bytes(p.d), sb = state_bytes(p.d);
     const size_t tot = size_t(p.total);
     bool ok = true;
-    if ((p.d.ndim > 1 || is_mixed(p.d)) && p.d.pde != MOLT_PDE_HJ)
+    if ((p.d.ndim > 1 || is_mixed(p.d) || p.d.pde == MOLT_PDE_ADVDIFF) && p.d.pde != MOLT_PDE_HJ)
       ok = ok && cudaMalloc(&p.acc, cb * tot) == cudaSuccess;
+    if (p.d.pde == MOLT_PDE_ADVDIFF) {
+      ok = ok && cudaMalloc(&p.gp, cb * tot) == cudaSuccess && cudaMalloc(&p.gm, cb * tot) == cudaSuccess;
+      if (p.d.integrator != MOLT_INT_EULER)
+        ok = ok && cudaMalloc(&p.stage1, sb * tot) == cudaSuccess && cudaMalloc(&p.stage2, sb * tot) == cudaSuccess;
+    }
     if (p.d.pde == MOLT_PDE_HEAT && p.d.integrator != MOLT_INT_EULER) {
       ok = ok && cudaMalloc(&p.stage1, sb * tot) == cudaSuccess;
       ok = ok && cudaMalloc(&p.stage2, sb * tot) == cudaSuccess;
@@ -752,6 +778,106 @@ molt_status heat_step(molt_ctx* c, Problem& p, void* u) {
         if (e != cudaSuccess) return cuda_fail(c, e, "heat update");
       }
     }
+  }
+  return MOLT_OK;
+}
+
+// ---------------------------------------------------------------- advection-diffusion
+// Split fluxes of one axis from the state (Sec. 2.5): g^{+-} = (g(u) +- c u)/2,
+// g = a u or u^2/2, evaluated in the state's precision and stored in the
+// sweeps' compute type.
+template <typename TS, typename TC>
+__global__ void flux_kernel(const TS* __restrict__ u, TC* __restrict__ gp, TC* __restrict__ gm, int burgers, double a,
+                            double c, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const TS v = u[i];
+    const TS g = burgers ? TS(0.5) * v * v : TS(a) * v;
+    const TS cu = TS(c) * v;
+    gp[i] = TC(TS(0.5) * (g + cu));
+    gm[i] = TC(TS(0.5) * (g - cu));
+  }
+}
+
+// Runge-Kutta stage (or Euler step) of the advection-diffusion problem:
+// dst = a0 u^n + a1 (u_s + dt F), dt F accumulated in acc; FP32 copy for
+// mixed precision.
+template <typename TC, typename TS>
+__global__ void advdiff_update_kernel(const TC* __restrict__ acc, const TS* un, const TS* us, TS* dst,
+                                      float* __restrict__ shadow, double a0, double a1, long long n, int* status) {
+  bool bad = false;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const TS r = fma(TS(a0), un[i], TS(a1) * (us[i] + TS(acc[i])));
+    dst[i] = r;
+    if (shadow) shadow[i] = float(r);
+    bad |= nonfinite(r);
+  }
+  if (bad) atomicOr(status, ST_NONFINITE);
+}
+
+molt_status advdiff_step(molt_ctx* c, Problem& p, void* u) {
+  static const double rk[3][2] = {{0.0, 1.0}, {0.75, 0.25}, {1.0 / 3.0, 2.0 / 3.0}};
+  const bool euler = p.d.integrator == MOLT_INT_EULER;
+  void* ins[3] = {u, p.stage1, p.stage2};
+  void* dsts[3] = {euler ? u : p.stage1, p.stage2, u};
+  const double dt = p.d.dt, cb = p.d.c, beta = p.d.beta, kappa = p.d.diffusivity;
+  const double alpha = beta / (cb * dt);
+  const double alpha_nu = kappa > 0 ? beta / std::sqrt(kappa * dt) : 0.0;
+  const bool f64 = is_f64_sweep(p.d), f32s = is_f32_state(p.d);
+  cudaError_t e;
+  for (int s = 0; s < (euler ? 1 : 3); ++s) {
+    if ((e = cudaMemsetAsync(p.acc, 0, compute_bytes(p.d) * size_t(p.total), c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "memset");
+    for (int ax = 0; ax < p.d.ndim; ++ax) {
+      molt_ctx::Rec rec;
+      record_begin(c, &rec, MOLT_KERNEL_FLUX);
+      const int burgers = p.d.flux == MOLT_FLUX_BURGERS ? 1 : 0;
+      const double av = p.d.velocity[ax];
+      if (f64)
+        flux_kernel<double, double><<<stream_grid(p.total), 256, 0, c->stream>>>(
+            static_cast<const double*>(ins[s]), static_cast<double*>(p.gp), static_cast<double*>(p.gm), burgers, av,
+            cb, p.total);
+      else if (f32s)
+        flux_kernel<float, float><<<stream_grid(p.total), 256, 0, c->stream>>>(
+            static_cast<const float*>(ins[s]), static_cast<float*>(p.gp), static_cast<float*>(p.gm), burgers, av, cb,
+            p.total);
+      else
+        flux_kernel<double, float><<<stream_grid(p.total), 256, 0, c->stream>>>(
+            static_cast<const double*>(ins[s]), static_cast<float*>(p.gp), static_cast<float*>(p.gm), burgers, av,
+            cb, p.total);
+      record_end(c, &rec);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "flux");
+      // -dt alpha S_R[g^+] + dt alpha S_L[g^-]  (dt alpha = beta / c)
+      const struct { int mode; const void* in; double coef; double al; } terms[3] = {
+          {MODE_R, p.gp, -beta / cb, alpha}, {MODE_L, p.gm, beta / cb, alpha},
+          {MODE_0, sweep_input(p, ins[s]), -beta * beta, alpha_nu}};
+      for (int t = 0; t < (kappa > 0 ? 3 : 2); ++t) {
+        Plan pl;
+        molt_status st = plan_axis(c, p, ax, terms[t].mode, p.d.P, terms[t].al, &pl);
+        if (st != MOLT_OK) return st;
+        pl.a.in = terms[t].in;
+        pl.a.acc = p.acc;
+        pl.a.coefS = terms[t].coef;
+        if ((st = run(c, p, EPI_ACC_AXPY, pl)) != MOLT_OK) return st;
+      }
+    }
+    molt_ctx::Rec rec;
+    record_begin(c, &rec, MOLT_KERNEL_UPDATE);
+    if (f64)
+      advdiff_update_kernel<double, double><<<stream_grid(p.total), 256, 0, c->stream>>>(
+          static_cast<const double*>(p.acc), static_cast<const double*>(u), static_cast<const double*>(ins[s]),
+          static_cast<double*>(dsts[s]), nullptr, rk[s][0], rk[s][1], p.total, c->status_dev);
+    else if (f32s)
+      advdiff_update_kernel<float, float><<<stream_grid(p.total), 256, 0, c->stream>>>(
+          static_cast<const float*>(p.acc), static_cast<const float*>(u), static_cast<const float*>(ins[s]),
+          static_cast<float*>(dsts[s]), nullptr, rk[s][0], rk[s][1], p.total, c->status_dev);
+    else
+      advdiff_update_kernel<float, double><<<stream_grid(p.total), 256, 0, c->stream>>>(
+          static_cast<const float*>(p.acc), static_cast<const double*>(u), static_cast<const double*>(ins[s]),
+          static_cast<double*>(dsts[s]), p.shadow, rk[s][0], rk[s][1], p.total, c->status_dev);
+    record_end(c, &rec);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "advection-diffusion update");
   }
   return MOLT_OK;
 }
@@ -1257,6 +1383,9 @@ molt_status molt_step(molt_ctx* c, void* const* u, void* const* u_prev, int nste
         const bool variant = (k == nsteps - 1) && even;   // keep u = newest on return
         st = wave_step(c, p, cur, prev, from_rest, variant);
         t_inout[i] += p.d.dt;
+      } else if (p.d.pde == MOLT_PDE_ADVDIFF) {
+        st = advdiff_step(c, p, u[i]);
+        t_inout[i] += p.d.dt;
       } else {
         st = hj_step(c, p, i, u[i]);
       }
@@ -1386,6 +1515,8 @@ molt_status molt_destroy(molt_ctx* c) {
     cudaFree(p.hx);
     cudaFree(p.hx2);
     cudaFree(p.src);
+    cudaFree(p.gp);
+    cudaFree(p.gm);
     cudaFree(p.tu);
     cudaFree(p.thx);
     cudaFree(p.shadow);

@@ -59,7 +59,8 @@ enum Epi {
   EPI_HJ_X = 5,        // hx = H^_x(D_R, D_L); speed max
   EPI_HJ_Y = 6,        // u -= dt*H^; speed max
   EPI_HJ_XG = 7,       // EPI_HJ_X for every Hamiltonian (HamKind)
-  EPI_HJ_YG = 8        // EPI_HJ_Y for every Hamiltonian, a source F(x, t), speed-only passes
+  EPI_HJ_YG = 8,       // EPI_HJ_Y for every Hamiltonian, a source F(x, t), speed-only passes
+  EPI_ACC_AXPY = 9     // acc += coefS * S (advection-diffusion terms)
 };
 // The general Hamilton-Jacobi kernels (XG/YG) carry more operands per point;
 // the |grad u|^2/2 kernels without a source keep their own instantiations.
@@ -947,7 +948,7 @@ struct Epilogue {
 
   __device__ __forceinline__ EpiOps<T, TST> load(long long gidx) const {
     EpiOps<T, TST> o{T(0), TST(0), TST(0)};
-    if constexpr (EPI == EPI_ACC_ADD) {
+    if constexpr (EPI == EPI_ACC_ADD || EPI == EPI_ACC_AXPY) {
       o.acc = gload<CG>(static_cast<const T*>(a.acc) + gidx);
     } else if constexpr (EPI == EPI_HEAT_FINAL || EPI == EPI_WAVE_FINAL) {
       if (a.acc) o.acc = gload<CG>(static_cast<const T*>(a.acc) + gidx);
@@ -967,6 +968,8 @@ struct Epilogue {
       static_cast<T*>(a.acc)[gidx] = s;
     } else if constexpr (EPI == EPI_ACC_ADD) {
       static_cast<T*>(a.acc)[gidx] = o.acc + s;
+    } else if constexpr (EPI == EPI_ACC_AXPY) {
+      static_cast<T*>(a.acc)[gidx] = fma(T(a.coefS), s, o.acc);
     } else if constexpr (EPI == EPI_HEAT_FINAL) {
       // u_s = a0 u^n + a1 (u_{s-1} + dt F), dt F = coefS (acc + S)
       const TST r = fma(TST(a.a0), o.x, TST(a.a1) * fma(TST(a.coefS), cvt<TST>(o.acc + s), o.y));

@@ -129,7 +129,7 @@ template <typename T, typename TST, int EPI>
 __device__ __forceinline__ void prefetch_operands(const SweepArgs& a, long long line0) {
   const void* ops[3] = {nullptr, nullptr, nullptr};
   int es[3] = {0, 0, 0};
-  if constexpr (EPI == EPI_ACC_ADD) { ops[0] = a.acc; es[0] = sizeof(T); }
+  if constexpr (EPI == EPI_ACC_ADD || EPI == EPI_ACC_AXPY) { ops[0] = a.acc; es[0] = sizeof(T); }
   if constexpr (EPI == EPI_HEAT_FINAL || EPI == EPI_WAVE_FINAL) {
     ops[0] = a.acc; es[0] = sizeof(T);
     ops[1] = a.un; es[1] = sizeof(TST);

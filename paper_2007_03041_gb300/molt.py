@@ -15,7 +15,8 @@ MOLT_OK, MOLT_EINVAL, MOLT_ENOMEM, MOLT_ECUDA, MOLT_ETIMEOUT, MOLT_ENONFINITE, M
 BC_PERIODIC, BC_DIRICHLET = 0, 1
 OP_L, OP_R, OP_0 = 0, 1, 2
 PREC_F64, PREC_F32_F64UPDATE, PREC_F32 = 0, 1, 2
-PDE_HEAT, PDE_WAVE, PDE_HJ = 0, 1, 2
+PDE_HEAT, PDE_WAVE, PDE_HJ, PDE_ADVDIFF = 0, 1, 2, 3
+FLUX_LINEAR, FLUX_BURGERS = 0, 1
 W_LINEAR, W_WENOZ, W_LEARNED = 0, 1, 2
 H_HALF_SQ, H_LINEAR, H_AFFINE_SQ = 0, 1, 2
 INT_DEFAULT, INT_EULER = 0, 1
@@ -28,7 +29,7 @@ MLP_PARAMS = 1347
 MLP_BLOB_BYTES = 3728
 OPT_TMA, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_TEST_SKIP_ARRIVE = 0, 1, 2, 3
 (KERNEL_STORE, KERNEL_ACC_SET, KERNEL_ACC_ADD, KERNEL_HEAT_FINAL, KERNEL_WAVE_FINAL, KERNEL_HJ_X, KERNEL_HJ_Y,
- KERNEL_UPDATE, KERNEL_BATCH, KERNEL_TRANSPOSE) = range(10)
+ KERNEL_UPDATE, KERNEL_BATCH, KERNEL_TRANSPOSE, KERNEL_FLUX) = range(11)
 
 
 class molt_desc(ctypes.Structure):
@@ -52,6 +53,7 @@ class molt_desc(ctypes.Structure):
         ("velocity", ctypes.c_double * 3),
         ("h0", ctypes.c_double),
         ("integrator", ctypes.c_int),
+        ("flux", ctypes.c_int),
     ]
 
 
@@ -114,7 +116,7 @@ def load_library(path=LIB_PATH):
 
 def make_desc(shape_xyz, lo=None, hi=None, bc=None, P=1, quad_points=6, weights=W_LINEAR, beta=1.0,
               pde=PDE_HEAT, c=1.0, diffusivity=1.0, cfl=1.0, dt=0.0, prec=PREC_F64, hamiltonian=H_HALF_SQ,
-              velocity=(0.0, 0.0, 0.0), h0=0.0, integrator=INT_DEFAULT):
+              velocity=(0.0, 0.0, 0.0), h0=0.0, integrator=INT_DEFAULT, flux=FLUX_LINEAR):
     """Descriptor for a grid whose sizes are given x first (n_x, n_y, n_z)."""
     nd = len(shape_xyz)
     d = molt_desc()
@@ -126,7 +128,7 @@ def make_desc(shape_xyz, lo=None, hi=None, bc=None, P=1, quad_points=6, weights=
         d.bc[i] = (bc[i] if bc is not None and i < nd else BC_PERIODIC)
     d.P, d.quad_points, d.weights, d.beta = P, quad_points, weights, beta
     d.pde, d.c, d.diffusivity, d.cfl, d.dt, d.prec = pde, c, diffusivity, cfl, dt, prec
-    d.hamiltonian, d.h0, d.integrator = hamiltonian, h0, integrator
+    d.hamiltonian, d.h0, d.integrator, d.flux = hamiltonian, h0, integrator, flux
     for i in range(3):
         d.velocity[i] = velocity[i] if i < len(velocity) else 0.0
     return d

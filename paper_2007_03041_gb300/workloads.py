@@ -30,6 +30,8 @@ boundary nodes, h = (hi-lo)/(n-1)):
   u = t (sin x + sin y) for u_t + (1 + u_x + u_y)^2/2 = F, so that
   F = sin x + sin y + (1 + t cos x + t cos y)^2/2
     = [sin x + sin y + 1/2] + t [cos x + cos y] + t^2 [(cos x + cos y)^2/2].
+* ``burgers_initial`` -- 2-D viscous Burgers (Sec. 2.5 flux splitting):
+  [0,2pi]^2 periodic, u0 = 0.3 + 0.5 sin x sin y (|u| <= 0.8).
 """
 import numpy as np
 
@@ -190,3 +192,8 @@ def manufactured_hj_source(n):
     x, y = paper_grid(n)
     c = np.cos(x) + np.cos(y)
     return np.stack([np.sin(x) + np.sin(y) + 0.5, c, 0.5 * c * c])
+
+
+def burgers_initial(n):
+    x, y = paper_grid(n)
+    return 0.3 + 0.5 * np.sin(x) * np.sin(y)
