@@ -77,12 +77,13 @@ def wave_step(u, u_prev, dxs, dt, c=1.0, beta=0.8, bc=None, npts=6, P=2, from_re
     return 2.0 * u - u_prev - beta * beta * S
 
 
-def hj_derivatives(u, alpha, dxs, npts=5, weights="wenoz", weight_fn=None):
-    """(v_d^-, v_d^+) for every axis d: v^- = alpha D_R[u], v^+ = -alpha D_L[u]."""
+def hj_derivatives(u, alpha, dxs, npts=5, weights="wenoz", weight_fn=None, P=1):
+    """(v_d^-, v_d^+) for every axis d: v^- = alpha sum_{p<=P} D_R^p[u],
+    v^+ = -alpha sum_{p<=P} D_L^p[u] (Sec. 2.5; P = 1 for forward Euler)."""
     out = []
     for ax in range(u.ndim):
-        dm = alpha * partial_sum(u, ax, alpha, dxs[ax], "R", BC_PERIODIC, npts, 1, weights, weight_fn)
-        dp = -alpha * partial_sum(u, ax, alpha, dxs[ax], "L", BC_PERIODIC, npts, 1, weights, weight_fn)
+        dm = alpha * partial_sum(u, ax, alpha, dxs[ax], "R", BC_PERIODIC, npts, P, weights, weight_fn)
+        dp = -alpha * partial_sum(u, ax, alpha, dxs[ax], "L", BC_PERIODIC, npts, P, weights, weight_fn)
         out.append((dm, dp))
     return out
 
@@ -223,3 +224,34 @@ def advdiff_step(u, dxs, dt, kind, a, c, kappa=0.0, beta=1.0, npts=6, P=1, rk3=F
     for a0, a1 in SSPRK3:
         us = a0 * un + a1 * (us + advdiff_rhs_dt(us, dxs, dt, kind, a, c, kappa, beta, npts, P, None, weights))
     return us
+
+
+def hj_step_rk3(u, dxs, lagged_speeds, t=0.0, cfl=1.5, beta=1.0, npts=5, weights="wenoz", P=3,
+                hamiltonian=H_HALF_SQ, a=None, h0=0.0, source=None):
+    """One step of the 3-stage SSP Runge-Kutta method on u_t = -H^ + F with
+    P-term one-sided sums (Sec. 2.5: an s-stage method with s-term sums):
+        u1 = u + dt L(u, t), u2 = 3/4 u + 1/4 (u1 + dt L(u1, t + dt)),
+        u^{n+1} = 1/3 u + 2/3 (u2 + dt L(u2, t + dt/2)),  L = -(H^ - F).
+    dt from the lagged speeds (Algorithm 1) for the whole step; returns
+    (u^{n+1}, dt, speeds of u^n)."""
+    alpha = beta / (cfl * min(dxs))
+    dt = hj_dt(lagged_speeds, dxs, cfl)
+    stage_t = (t, t + dt, t + 0.5 * dt)
+    un = np.asarray(u, dtype=np.float64)
+    us, speeds0 = un, None
+    for (a0, a1), ts in zip(SSPRK3, stage_t):
+        Hh, sp = hj_hamiltonian(hj_derivatives(us, alpha, dxs, npts, weights, None, P), hamiltonian, a, h0)
+        if speeds0 is None:
+            speeds0 = sp
+        if source is not None:
+            Hh = Hh - source_at(source, ts)
+        us = a0 * un + a1 * (us - dt * Hh)
+    return us, dt, speeds0
+
+
+def hj_initial_speeds_P(u, dxs, cfl=1.5, beta=1.0, npts=5, weights="wenoz", P=3, hamiltonian=H_HALF_SQ, a=None,
+                        h0=0.0):
+    """Speeds of u^0 with P-term one-sided sums (the first step's lagged speeds)."""
+    alpha = beta / (cfl * min(dxs))
+    _, speeds = hj_hamiltonian(hj_derivatives(u, alpha, dxs, npts, weights, None, P), hamiltonian, a, h0)
+    return speeds

@@ -168,3 +168,55 @@ def test_closed_form_errors_at_5277_near_printed_values():
     dif = abs(amp - math.exp(-steps * h)) * 2.0
     for got, key in ((adv, "linf_5277_advection"), (dif, "linf_5277_diffusion")):
         assert ref[key] / 1.5 < got < ref[key] * 1.5, (key, got, ref[key])
+
+
+def test_hj_rk3_linear_advection_matches_closed_form():
+    """SSP-RK3 with three-term one-sided sums (Sec. 2.5) for H = a.grad u:
+    each mode is multiplied per step by R(z), R the RK3 polynomial and
+    z = -dt sum_d a_d * (symbol of the upwind three-term sum)."""
+    n, steps = 32, 5
+    h = 2 * math.pi / n
+    a = (1.0, -0.5)                      # (a_x, a_y)
+    beta, cfl = 0.3, 1.0
+    u = workloads.advection_initial(n)
+    kw = dict(cfl=cfl, beta=beta, npts=6, weights="linear", P=3, hamiltonian=schemes.H_LINEAR, a=a[::-1])
+    sp = schemes.hj_initial_speeds_P(u, [h, h], **kw)
+    for _ in range(steps):
+        u, dt, sp = schemes.hj_step_rk3(u, [h, h], sp, **kw)
+    alpha = beta / (cfl * h)
+    nu = alpha * h
+    modes = {(0, 0): 0.25, (1, 0): -0.125, (-1, 0): -0.125, (0, 1): -0.125, (0, -1): -0.125,
+             (1, 1): 1 / 16, (1, -1): 1 / 16, (-1, 1): 1 / 16, (-1, -1): 1 / 16}
+    x, y = workloads.paper_grid(n)
+    want = np.zeros((n, n), dtype=complex)
+    for (kx, ky), am in modes.items():
+        H = 0.0
+        for ad, k in zip(a, (kx, ky)):
+            if ad > 0:
+                H = H + ad * alpha * stability.partial_sum_symbol(k * h, nu, "R", 6, 3)
+            else:
+                H = H + ad * (-alpha) * stability.partial_sum_symbol(k * h, nu, "L", 6, 3)
+        z = -dt * H
+        G = 1 + z + z * z / 2 + z ** 3 / 6
+        want += am * G ** steps * np.exp(1j * (kx * x + ky * y))
+    assert abs(dt - h) < 1e-15
+    assert np.abs(u - want.real).max() < 1e-13
+
+
+def test_hj_rk3_manufactured_source_is_third_order_in_time_per_step():
+    """With the manufactured source, the step error of SSP-RK3 with P = 3 is
+    smaller than forward Euler's at the same dt (one step from the exact
+    solution at t = 0.2, on a fine grid)."""
+    n = 128
+    h = 2 * math.pi / n
+    F = workloads.manufactured_hj_source(n)
+    t0 = 0.2
+    u0 = workloads.manufactured_hj_solution(n, t0)
+    kw = dict(cfl=1.0, npts=6, weights="linear", hamiltonian=schemes.H_AFFINE_SQ, a=(1.0, 1.0), h0=1.0)
+    sp = schemes.hj_initial_speeds_P(u0, [h, h], P=3, **kw)
+    u_rk, dt, _ = schemes.hj_step_rk3(u0, [h, h], sp, t=t0, P=3, source=F, **kw)
+    u_fe, dt_fe, _ = schemes.hj_step(u0, [h, h], sp, source=F, t=t0, **kw)
+    assert abs(dt - dt_fe) < 1e-15
+    e_rk = np.abs(u_rk - workloads.manufactured_hj_solution(n, t0 + dt)).max()
+    e_fe = np.abs(u_fe - workloads.manufactured_hj_solution(n, t0 + dt)).max()
+    assert e_rk < 0.2 * e_fe, (e_rk, e_fe)
