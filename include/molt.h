@@ -77,11 +77,14 @@ typedef enum { MOLT_W_LINEAR = 0, MOLT_W_WENOZ = 1, MOLT_W_LEARNED = 2 } molt_we
  * |dH/du_d| over the box of one-sided derivatives; the wave speed of axis d
  * is the grid maximum of r_d. */
 typedef enum { MOLT_H_HALF_SQ = 0, MOLT_H_LINEAR = 1, MOLT_H_AFFINE_SQ = 2 } molt_hamiltonian;
-/* Time integrator: MOLT_INT_DEFAULT (heat: 3-stage SSP Runge-Kutta; wave:
- * leapfrog; Hamilton-Jacobi: forward Euler) or MOLT_INT_EULER (forward
- * Euler; heat and Hamilton-Jacobi, the first-order coupling of the paper's
- * test problems, Sec. 5.1). */
-typedef enum { MOLT_INT_DEFAULT = 0, MOLT_INT_EULER = 1 } molt_integrator;
+/* Time integrator: MOLT_INT_DEFAULT (heat, advection-diffusion: 3-stage SSP
+ * Runge-Kutta; wave: leapfrog; Hamilton-Jacobi: forward Euler),
+ * MOLT_INT_EULER (forward Euler; heat, advection-diffusion and
+ * Hamilton-Jacobi, the first-order coupling of the paper's test problems,
+ * Sec. 5.1) or MOLT_INT_RK3 (3-stage SSP Runge-Kutta; for Hamilton-Jacobi
+ * with P-term one-sided sums alpha sum_{p<=P} D_R^p, -alpha sum_{p<=P} D_L^p,
+ * Sec. 2.5's coupling of an s-stage method with s-term sums). */
+typedef enum { MOLT_INT_DEFAULT = 0, MOLT_INT_EULER = 1, MOLT_INT_RK3 = 2 } molt_integrator;
 
 /* One problem: a grid, its boundary types, the quadrature and the PDE whose
  * time step molt_step advances.  Enumerations are stored as int. */

@@ -40,6 +40,7 @@ struct Problem {
   float* shadow = nullptr;  // FP32 copy of the state the sweeps read (mixed precision)
   void* gp = nullptr;       // advection-diffusion: split fluxes g^+, g^- (compute type)
   void* gm = nullptr;
+  void* hv[4] = {nullptr, nullptr, nullptr, nullptr};  // HJ with RK3: S_R, S_L per axis (state type)
   int64_t hj_steps = 0;     // HJ steps taken (rotates the speed slots)
   bool hj_lag_ready = false;
 };
@@ -123,8 +124,8 @@ std::string validate(const molt_desc& d) {
   for (int ax = 0; ax < 3; ++ax)
     if (!std::isfinite(d.velocity[ax])) return "velocity must be finite";
   if (!std::isfinite(d.h0)) return "h0 must be finite";
-  if (d.integrator != MOLT_INT_DEFAULT && d.integrator != MOLT_INT_EULER) return "unknown integrator";
-  if (d.integrator == MOLT_INT_EULER && d.pde == MOLT_PDE_WAVE) return "forward Euler is for heat and Hamilton-Jacobi";
+  if (d.integrator < MOLT_INT_DEFAULT || d.integrator > MOLT_INT_RK3) return "unknown integrator";
+  if (d.integrator != MOLT_INT_DEFAULT && d.pde == MOLT_PDE_WAVE) return "the wave equation runs leapfrog";
   return "";
 }
 
@@ -560,6 +561,10 @@ molt_status molt_create(const molt_desc* descs, int count, void* cuda_stream, mo
     if (p.d.pde == MOLT_PDE_HJ && p.d.ndim > 1) ok = ok && cudaMalloc(&p.hx, sb * tot) == cudaSuccess;
     if (p.d.pde == MOLT_PDE_HJ && p.d.ndim > 1 && p.d.hamiltonian == MOLT_H_AFFINE_SQ)
       ok = ok && cudaMalloc(&p.hx2, sb * tot) == cudaSuccess;
+    if (p.d.pde == MOLT_PDE_HJ && p.d.integrator == MOLT_INT_RK3) {
+      for (int k = 0; k < 2 * p.d.ndim; ++k) ok = ok && cudaMalloc(&p.hv[k], sb * tot) == cudaSuccess;
+      ok = ok && cudaMalloc(&p.stage1, sb * tot) == cudaSuccess && cudaMalloc(&p.stage2, sb * tot) == cudaSuccess;
+    }
     if (ok && hj_transposed_y(c, p)) {
       ok = cudaMalloc(&p.tu, sb * tot) == cudaSuccess && cudaMalloc(&p.thx, sb * tot) == cudaSuccess;
     }
@@ -1039,7 +1044,195 @@ molt_status hj_pass(molt_ctx* c, Problem& p, int idx, void* u, int ax, int epi, 
   return run(c, p, epi, pl);
 }
 
+// ---------------------------------------------------------------- HJ, SSP-RK3
+// One Runge-Kutta stage of the Hamilton-Jacobi step from the P-term sums
+// S_R, S_L of every axis (v^- = alpha S_R, v^+ = -alpha S_L): the local
+// Lax-Friedrichs Hamiltonian (r_d the largest |dH/dp_d| over the box of
+// one-sided derivatives), the source at the stage time, and
+// dst = a0 u^n + a1 (u_s - dt (H^ - F)); dt from the lagged speed (as the
+// Euler passes); the first stage publishes the speeds max_d r_d / h_d.
+struct HjStageArgs {
+  const void* sr[2];
+  const void* sl[2];
+  const void* un;
+  const void* us;
+  void* dst;            // null: a pass that only measures speeds
+  int ndim, ham;
+  double alpha, vel[2], inv_h[2], h0, a0, a1, cstage;
+  const void* src;
+  int src_deg;
+  long long src_stride, n;
+  const unsigned long long* lag;   // null: dt = 0 (speed-only pass)
+  unsigned long long* speed;       // null: no speed published
+  double cfl, dt_max;
+  const double* t_now;             // time of u^n
+  double* t_next;                  // block 0 of the last stage writes t^n + dt (or null)
+  int* status;
+};
+
+template <typename T>
+__global__ void hj_rk3_stage_kernel(const HjStageArgs g) {
+  double dt = 0.0;
+  if (g.lag) {
+    const double cl = __longlong_as_double((long long)g.lag[0]);
+    dt = g.dt_max;
+    if (cl > 0.0 && g.cfl / cl < dt) dt = g.cfl / cl;
+  }
+  const double tn = g.t_now ? *g.t_now : 0.0;
+  if (g.t_next && blockIdx.x == 0 && threadIdx.x == 0) *g.t_next = tn + dt;
+  const T tst = T(tn + g.cstage * dt);
+  const T al = T(g.alpha);
+  double rmax = 0.0;
+  bool bad = false;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += stride) {
+    T vm[2], vp[2];
+    for (int d = 0; d < g.ndim; ++d) {
+      vm[d] = al * static_cast<const T*>(g.sr[d])[i];
+      vp[d] = -al * static_cast<const T*>(g.sl[d])[i];
+    }
+    T H = T(0), r[2] = {T(0), T(0)};
+    if (g.ham == HAM_AFFINE_SQ) {
+      T sbar = T(g.h0), dsum = T(0), dabs = T(0), delta[2];
+      for (int d = 0; d < g.ndim; ++d) {
+        const T ad = T(g.vel[d]);
+        sbar += ad * T(0.5) * (vm[d] + vp[d]);
+        delta[d] = fabs(ad) * T(0.5) * (vp[d] - vm[d]);
+        dsum += delta[d];
+        dabs += fabs(delta[d]);
+      }
+      const T m = fabs(sbar) + dabs;
+      H = T(0.5) * sbar * sbar - m * dsum;
+      for (int d = 0; d < g.ndim; ++d) r[d] = fabs(T(g.vel[d])) * m;
+    } else {
+      for (int d = 0; d < g.ndim; ++d) {
+        const T mean = T(0.5) * (vm[d] + vp[d]);
+        if (g.ham == HAM_LINEAR) {
+          r[d] = fabs(T(g.vel[d]));
+          H += T(g.vel[d]) * mean;
+        } else {
+          r[d] = fmax(fabs(vm[d]), fabs(vp[d]));
+          H += T(0.5) * mean * mean;
+        }
+        H -= r[d] * T(0.5) * (vp[d] - vm[d]);
+      }
+    }
+    for (int d = 0; d < g.ndim; ++d) rmax = fmax(rmax, double(r[d]) * g.inv_h[d]);
+    if (g.src) {
+      const T* f = static_cast<const T*>(g.src) + i;
+      T F = f[g.src_deg * g.src_stride];
+      for (int k = g.src_deg - 1; k >= 0; --k) F = fma(F, tst, f[k * g.src_stride]);
+      H -= F;
+    }
+    if (g.dst) {
+      const T res = fma(T(g.a0), static_cast<const T*>(g.un)[i],
+                        T(g.a1) * fma(-T(dt), H, static_cast<const T*>(g.us)[i]));
+      static_cast<T*>(g.dst)[i] = res;
+      bad |= nonfinite(res);
+    }
+  }
+  if (g.speed) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    if ((threadIdx.x & 31) == 0 && rmax > 0.0) atomicMax(g.speed, (unsigned long long)__double_as_longlong(rmax));
+  }
+  if (bad) atomicOr(g.status, ST_NONFINITE);
+}
+
+// The P-term sums S_R, S_L of every axis of `in` into p.hv.
+molt_status hj_rk3_sums(molt_ctx* c, Problem& p, const void* in) {
+  for (int ax = 0; ax < p.d.ndim; ++ax) {
+    for (int side = 0; side < 2; ++side) {
+      Plan pl;
+      molt_status st = plan_axis(c, p, ax, side == 0 ? MODE_R : MODE_L, p.d.P, step_alpha(p), &pl);
+      if (st != MOLT_OK) return st;
+      pl.a.in = in;
+      pl.a.out = p.hv[2 * ax + side];
+      if ((st = run(c, p, EPI_STORE, pl)) != MOLT_OK) return st;
+    }
+  }
+  return MOLT_OK;
+}
+
+molt_status hj_rk3_stage(molt_ctx* c, const Problem& p, HjStageArgs g) {
+  molt_ctx::Rec rec;
+  record_begin(c, &rec, MOLT_KERNEL_UPDATE);
+  if (state_bytes(p.d) == 4) hj_rk3_stage_kernel<float><<<stream_grid(p.total), 256, 0, c->stream>>>(g);
+  else hj_rk3_stage_kernel<double><<<stream_grid(p.total), 256, 0, c->stream>>>(g);
+  record_end(c, &rec);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MOLT_OK : cuda_fail(c, e, "Hamilton-Jacobi stage");
+}
+
+molt_status hj_rk3_step(molt_ctx* c, Problem& p, int idx, void* u) {
+  static const double rk[3][2] = {{0.0, 1.0}, {0.75, 0.25}, {1.0 / 3.0, 2.0 / 3.0}};
+  static const double cst[3] = {0.0, 1.0, 0.5};   // stage times t^n + c dt
+  unsigned long long* slots = c->speed_dev + 2 * idx;
+  double hmin = p.h[0];
+  for (int a = 1; a < p.d.ndim; ++a) hmin = std::min(hmin, p.h[a]);
+  HjStageArgs g{};
+  g.ndim = p.d.ndim;
+  g.ham = p.d.hamiltonian;
+  g.alpha = step_alpha(p);
+  g.h0 = p.d.h0;
+  for (int d = 0; d < p.d.ndim; ++d) {
+    g.sr[d] = p.hv[2 * d];
+    g.sl[d] = p.hv[2 * d + 1];
+    g.vel[d] = p.d.velocity[d];
+    g.inv_h[d] = 1.0 / p.h[d];
+  }
+  g.cfl = p.d.cfl;
+  g.dt_max = 10.0 * hmin;
+  g.n = p.total;
+  g.status = c->status_dev;
+  cudaError_t e;
+  molt_status st;
+  if (!p.hj_lag_ready) {
+    // speeds of u^0 serve as the lagged speeds of the first step (Algorithm 1)
+    if ((e = cudaMemsetAsync(slots + 1, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "memset");
+    if ((st = hj_rk3_sums(c, p, u)) != MOLT_OK) return st;
+    HjStageArgs s0 = g;
+    s0.speed = slots + 1;
+    if ((st = hj_rk3_stage(c, p, s0)) != MOLT_OK) return st;
+    p.hj_lag_ready = true;
+    p.hj_steps = 0;
+  }
+  const int cur = int(p.hj_steps & 1);
+  if ((e = cudaMemsetAsync(slots + cur, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "memset");
+  void* ins[3] = {u, p.stage1, p.stage2};
+  void* dsts[3] = {p.stage1, p.stage2, u};
+  for (int s = 0; s < 3; ++s) {
+    if ((st = hj_rk3_sums(c, p, ins[s])) != MOLT_OK) return st;
+    HjStageArgs gs = g;
+    gs.un = u;
+    gs.us = ins[s];
+    gs.dst = dsts[s];
+    gs.a0 = rk[s][0];
+    gs.a1 = rk[s][1];
+    gs.cstage = cst[s];
+    gs.lag = slots + (cur ^ 1);
+    gs.speed = s == 0 ? slots + cur : nullptr;
+    gs.t_now = c->t_dev + idx;
+    gs.t_next = s == 2 ? c->tnow_dev + idx : nullptr;
+    if (p.src) {
+      gs.src = p.src;
+      gs.src_deg = p.src_deg;
+      gs.src_stride = p.total;
+    }
+    if ((st = hj_rk3_stage(c, p, gs)) != MOLT_OK) return st;
+  }
+  // t^{n+1} = t^n + dt (written apart from t^n, which every stage reads)
+  if ((e = cudaMemcpyAsync(c->t_dev + idx, c->tnow_dev + idx, sizeof(double), cudaMemcpyDeviceToDevice,
+                           c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "time copy");
+  p.hj_steps++;
+  return MOLT_OK;
+}
+
 molt_status hj_step(molt_ctx* c, Problem& p, int idx, void* u) {
+  if (p.d.integrator == MOLT_INT_RK3) return hj_rk3_step(c, p, idx, u);
   unsigned long long* slots = c->speed_dev + 2 * idx;
   cudaError_t e;
   const bool ty = p.tu && p.thx && hj_transposed_y(c, p);
@@ -1111,7 +1304,7 @@ bool batch_supported(const molt_ctx* c) {
   for (const auto& p : c->probs) {
     const molt_desc& d = p.d;
     if (d.pde != MOLT_PDE_HEAT || d.prec != MOLT_PREC_F32_F64UPDATE || d.ndim != 2 || d.weights != MOLT_W_LINEAR ||
-        d.integrator != MOLT_INT_DEFAULT)
+        d.integrator == MOLT_INT_EULER)
       return false;
     for (int ax = 0; ax < 2; ++ax)
       if (!shape_ok(p.n[ax], 16) && !shape_ok(p.n[ax], 8) && !shape_ok(p.n[ax], 4)) return false;
@@ -1517,6 +1710,7 @@ molt_status molt_destroy(molt_ctx* c) {
     cudaFree(p.src);
     cudaFree(p.gp);
     cudaFree(p.gm);
+    for (void* v : p.hv) cudaFree(v);
     cudaFree(p.tu);
     cudaFree(p.thx);
     cudaFree(p.shadow);

@@ -19,7 +19,7 @@ PDE_HEAT, PDE_WAVE, PDE_HJ, PDE_ADVDIFF = 0, 1, 2, 3
 FLUX_LINEAR, FLUX_BURGERS = 0, 1
 W_LINEAR, W_WENOZ, W_LEARNED = 0, 1, 2
 H_HALF_SQ, H_LINEAR, H_AFFINE_SQ = 0, 1, 2
-INT_DEFAULT, INT_EULER = 0, 1
+INT_DEFAULT, INT_EULER, INT_RK3 = 0, 1, 2
 
 EXPORTS = ("molt_create", "molt_apply_D", "molt_step", "molt_set_option", "molt_profile_read", "molt_destroy",
            "molt_last_error", "molt_wave_step_noalloc", "molt_batch_tile_shape", "molt_set_mlp", "molt_mlp_stats",

@@ -301,3 +301,57 @@ def test_fp32_sweeps_keep_constants_in_the_kernel_of_D(npts, prec):
             # closure or the Dirichlet solve (A = B = v/2) give L^{-1} v = v
             worst = max(worst, float(np.abs(o).max()) / 0.75)
     assert worst < 1.5e-6, worst
+
+
+RK3_CASES = [(M.H_LINEAR, (1.0, -0.5), 0.0, False, 3, M.W_LINEAR, 6), (M.H_AFFINE_SQ, (1.0, 1.0), 1.0, True, 3, M.W_LINEAR, 6),
+             (M.H_HALF_SQ, (0.0, 0.0), 0.0, False, 2, M.W_WENOZ, 5)]
+
+
+@pytest.mark.parametrize("prec", [M.PREC_F64, M.PREC_F32])
+@pytest.mark.parametrize("shape", [(96, 80), (128, 1)])
+@pytest.mark.parametrize("ham,vel,h0,with_source,P,weights,npts", RK3_CASES)
+def test_hj_rk3_matches_oracle(ham, vel, h0, with_source, P, weights, npts, shape, prec):
+    """SSP-RK3 with P-term one-sided sums (Sec. 2.5) against the oracle, step by step."""
+    need_gpu()
+    import torch
+    nx, ny = shape
+    dims = (nx,) if ny == 1 else (nx, ny)
+    u0 = _smooth(nx, ny, 13)
+    src = np.stack([_smooth(nx, ny, 22 + k) for k in range(3)]) if with_source else None
+    if ny == 1:
+        u0 = u0[0]
+        src = src[:, 0] if src is not None else None
+        vel = vel[:1]
+    dt_ = state_dtype(prec)
+    if prec == M.PREC_F32:
+        u0 = u0.astype(np.float32).astype(np.float64)
+        src = src.astype(np.float32).astype(np.float64) if src is not None else None
+    nd = len(dims)
+    d = M.make_desc(dims, lo=[0.0] * nd, hi=[2 * np.pi] * nd, P=P, quad_points=npts, weights=weights, beta=0.3,
+                    pde=M.PDE_HJ, cfl=1.0, dt=0.0, prec=prec, hamiltonian=ham, velocity=vel, h0=h0,
+                    integrator=M.INT_RK3)
+    ctx = M.molt_create(d)
+    steps = 3
+    try:
+        if src is not None:
+            M.molt_set_source(ctx, 0, to_dev(src, dt_))
+        u = to_dev(u0, dt_)
+        got, ts = [], []
+        t = [0.1]
+        for _ in range(steps):
+            t = M.molt_step(ctx, u, None, nsteps=1, t=t)
+            got.append(u.double().cpu().numpy())
+            ts.append(t[0])
+    finally:
+        M.molt_destroy(ctx)
+    hs = [2 * np.pi / n for n in dims][::-1]
+    wname = "wenoz" if weights == M.W_WENOZ else "linear"
+    kw = dict(cfl=1.0, beta=0.3, npts=npts, weights=wname, P=P, hamiltonian=ORACLE_H[ham], a=tuple(vel)[::-1], h0=h0)
+    uu = u0
+    sp = schemes.hj_initial_speeds_P(uu, hs, **kw)
+    tt = 0.1
+    for k in range(steps):
+        uu, dt, sp = schemes.hj_step_rk3(uu, hs, sp, t=tt, source=src, **kw)
+        tt += dt
+        assert rel_l2(got[k], uu) < tol_for(prec), k
+        assert abs(ts[k] - tt) < (1e-10 if prec == M.PREC_F64 else 1e-5) * tt, k
