@@ -169,6 +169,18 @@ molt_status molt_step(molt_ctx* ctx, void* const* u, void* const* u_prev, int ns
  * alignment, or a problem that is not Hamilton-Jacobi.  Synchronous. */
 molt_status molt_set_source(molt_ctx* ctx, int problem, const void* coef, int degree);
 
+/* Non-uniform periodic axis: the n = desc.n[axis] nodes of one period, host
+ * array, strictly increasing, x[n-1] - x[0] < hi - lo (the period); copied.
+ * molt_apply_D along that axis then uses point-local quadrature weights
+ * (each point's stencil nodes integrated against the exponential kernel,
+ * the non-uniform case of Sec. 2.4) and cell decays e^{-alpha (x_i - x_{i-1})},
+ * closed over the period with mu = e^{-alpha (hi - lo)} (Sec. 2.3); linear
+ * weights only (MOLT_EUNSUPPORTED otherwise).  x == NULL makes the axis
+ * uniform again.  molt_step on a problem with a non-uniform axis returns
+ * MOLT_EUNSUPPORTED.  MOLT_EINVAL: bad index, count or nodes;
+ * MOLT_EUNSUPPORTED: a Dirichlet axis.  Synchronous. */
+molt_status molt_set_grid_axis(molt_ctx* ctx, int problem, int axis, const double* x, int64_t n);
+
 /* Context options.
  *   MOLT_OPT_TMA      1 (default): sweeps whose lines are an exact fit and
  *                     whose arrays meet the tensor-copy alignment rules run

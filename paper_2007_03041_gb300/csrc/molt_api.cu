@@ -13,6 +13,7 @@
 
 #include "coeffs.h"
 #include "line_constants.h"
+#include "nonuniform.cuh"
 #include "molt.h"
 #include "sweep_launch.h"
 #include "batch.cuh"
@@ -41,6 +42,14 @@ struct Problem {
   void* gp = nullptr;       // advection-diffusion: split fluxes g^+, g^- (compute type)
   void* gm = nullptr;
   void* hv[4] = {nullptr, nullptr, nullptr, nullptr};  // HJ with RK3: S_R, S_L per axis (state type)
+  // non-uniform periodic axes: the nodes of one period (empty = uniform) and
+  // the device tables of the last (alpha, rule) applied
+  std::vector<double> nodes[3];
+  struct NuCache {
+    double alpha = 0.0;
+    int npts = 0;
+    void* dev = nullptr;         // cR[6n], cL[6n], q[n] of the compute type
+  } nu[3];
   int64_t hj_steps = 0;     // HJ steps taken (rotates the speed slots)
   bool hj_lag_ready = false;
 };
@@ -455,6 +464,11 @@ bool hj_transposed_y(molt_ctx* c, const Problem& p);
 
 }  // namespace
 
+namespace {
+molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int P, double alpha,
+                               const void* in, void* out);
+}  // namespace
+
 extern "C" {
 
 molt_status molt_create(const molt_desc* descs, int count, void* cuda_stream, molt_ctx** out) {
@@ -595,6 +609,7 @@ molt_status molt_apply_D(molt_ctx* c, int problem, int axis, int op, int P, doub
   if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15)
     return fail(c, MOLT_EINVAL, "arrays must be 16-byte aligned");
   const int mode = op == MOLT_OP_L ? MODE_L : (op == MOLT_OP_R ? MODE_R : MODE_0);
+  if (!p.nodes[axis].empty()) return apply_D_nonuniform(c, c->probs[problem], axis, mode, P, alpha, in, out);
   Plan pl;
   molt_status st = plan_axis(c, p, axis, mode, P, alpha, &pl);
   if (st != MOLT_OK) return st;
@@ -724,6 +739,77 @@ void record_end(molt_ctx* c, molt_ctx::Rec* rec) {
     c->recs.push_back(*rec);
   }
 }
+
+// sum_{p<=P} D^p along a non-uniform periodic axis (point-local weights).
+molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int P, double alpha, const void* in,
+                               void* out) {
+  if (p.d.weights != MOLT_W_LINEAR) return fail(c, MOLT_EUNSUPPORTED, "non-uniform axes run linear weights");
+  if (!(alpha > 0) || !std::isfinite(alpha)) return fail(c, MOLT_EINVAL, "alpha must be positive and finite");
+  const std::vector<double>& x = p.nodes[axis];
+  const int n = int(x.size());
+  const double L = p.d.hi[axis] - p.d.lo[axis];
+  const bool f64 = is_f64_sweep(p.d);
+  const size_t tb = f64 ? 8 : 4;
+  Problem::NuCache& cch = p.nu[axis];
+  cudaError_t e;
+  if (!cch.dev || cch.alpha != alpha || cch.npts != p.d.quad_points) {
+    std::vector<double> cR, cL, q;
+    build_nonuniform_tables(x, L, alpha, p.d.quad_points, &cR, &cL, &q);
+    std::vector<double> all(cR);
+    all.insert(all.end(), cL.begin(), cL.end());
+    all.insert(all.end(), q.begin(), q.end());
+    if (!cch.dev && (e = cudaMalloc(&cch.dev, all.size() * tb)) != cudaSuccess) {
+      cch.dev = nullptr;
+      return fail(c, MOLT_ENOMEM, "non-uniform tables");
+    }
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "table sync");
+    if (f64) {
+      e = cudaMemcpy(cch.dev, all.data(), all.size() * 8, cudaMemcpyHostToDevice);
+    } else {
+      std::vector<float> f(all.begin(), all.end());
+      e = cudaMemcpy(cch.dev, f.data(), f.size() * 4, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "table upload");
+    cch.alpha = alpha;
+    cch.npts = p.d.quad_points;
+  }
+  NuArgs a{};
+  a.g = geom(p, axis);
+  a.mode = mode;
+  a.P = P;
+  a.inv1mmu = 1.0 / (-std::expm1(-alpha * L));
+  a.in = in;
+  a.out = out;
+  a.status = c->status_dev;
+  const size_t per = size_t(3 * n + 6) * tb;
+  int warps = int(std::min<size_t>(8, std::max<size_t>(1, (200 * 1024) / per)));
+  if (per > 200 * 1024) return fail(c, MOLT_EUNSUPPORTED, "non-uniform line too long for shared memory");
+  while (warps > 1 && (a.g.nlines + warps - 1) / warps < 2LL * device_sms()) warps /= 2;
+  const long long blocks = (a.g.nlines + warps - 1) / warps;
+  const size_t smem = per * warps;
+  molt_ctx::Rec rec;
+  record_begin(c, &rec, MOLT_KERNEL_STORE);
+  if (f64) {
+    NuTables<double> t{static_cast<const double*>(cch.dev), static_cast<const double*>(cch.dev) + 6 * size_t(n),
+                       static_cast<const double*>(cch.dev) + 12 * size_t(n)};
+    cudaFuncSetAttribute(nonuniform_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    nonuniform_kernel<double, double><<<unsigned(blocks), 32 * warps, smem, c->stream>>>(a, t);
+  } else {
+    NuTables<float> t{static_cast<const float*>(cch.dev), static_cast<const float*>(cch.dev) + 6 * size_t(n),
+                      static_cast<const float*>(cch.dev) + 12 * size_t(n)};
+    if (is_f32_state(p.d)) {
+      cudaFuncSetAttribute(nonuniform_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+      nonuniform_kernel<float, float><<<unsigned(blocks), 32 * warps, smem, c->stream>>>(a, t);
+    } else {
+      cudaFuncSetAttribute(nonuniform_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+      nonuniform_kernel<float, double><<<unsigned(blocks), 32 * warps, smem, c->stream>>>(a, t);
+    }
+  }
+  record_end(c, &rec);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? MOLT_OK : cuda_fail(c, e, "non-uniform sweep");
+}
+
 
 molt_status refresh_shadow(molt_ctx* c, Problem& p, const void* u) {
   if (!p.shadow) return MOLT_OK;
@@ -1544,6 +1630,9 @@ molt_status molt_step(molt_ctx* c, void* const* u, void* const* u_prev, int nste
       return fail(c, MOLT_EINVAL, "wave problems need u_prev");
     if (c->probs[i].d.pde != MOLT_PDE_HJ && !(c->probs[i].d.dt > 0))
       return fail(c, MOLT_EINVAL, "heat and wave steps need dt > 0");
+    for (int ax = 0; ax < 3; ++ax)
+      if (!c->probs[i].nodes[ax].empty())
+        return fail(c, MOLT_EUNSUPPORTED, "molt_step runs uniform grids (non-uniform axes: molt_apply_D)");
   }
   cudaError_t e;
   std::vector<double> t0(np);
@@ -1638,6 +1727,31 @@ molt_status molt_set_source(molt_ctx* c, int problem, const void* coef, int degr
   return MOLT_OK;
 }
 
+molt_status molt_set_grid_axis(molt_ctx* c, int problem, int axis, const double* x, int64_t n) {
+  if (!c) return fail(nullptr, MOLT_EINVAL, "null context");
+  if (problem < 0 || problem >= int(c->probs.size())) return fail(c, MOLT_EINVAL, "problem index out of range");
+  Problem& p = c->probs[problem];
+  if (axis < 0 || axis >= p.d.ndim) return fail(c, MOLT_EINVAL, "axis out of range");
+  cudaError_t e;
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "grid sync");
+  cudaFree(p.nu[axis].dev);
+  p.nu[axis] = Problem::NuCache{};
+  if (!x) {
+    p.nodes[axis].clear();
+    return MOLT_OK;
+  }
+  if (p.d.bc[axis] != MOLT_BC_PERIODIC) return fail(c, MOLT_EUNSUPPORTED, "non-uniform axes are periodic");
+  if (n != p.n[axis]) return fail(c, MOLT_EINVAL, "node count differs from the axis size");
+  const double L = p.d.hi[axis] - p.d.lo[axis];
+  for (int64_t i = 0; i < n; ++i) {
+    if (!std::isfinite(x[i])) return fail(c, MOLT_EINVAL, "nodes must be finite");
+    if (i > 0 && !(x[i] > x[i - 1])) return fail(c, MOLT_EINVAL, "nodes must increase strictly");
+  }
+  if (!(x[n - 1] - x[0] < L)) return fail(c, MOLT_EINVAL, "nodes must lie within one period");
+  p.nodes[axis].assign(x, x + n);
+  return MOLT_OK;
+}
+
 molt_status molt_set_option(molt_ctx* c, int option, int64_t value) {
   if (!c) return fail(nullptr, MOLT_EINVAL, "null context");
   if (option == MOLT_OPT_WAIT_LIMIT) {
@@ -1710,6 +1824,7 @@ molt_status molt_destroy(molt_ctx* c) {
     cudaFree(p.src);
     cudaFree(p.gp);
     cudaFree(p.gm);
+    for (auto& cch : p.nu) cudaFree(cch.dev);
     for (void* v : p.hv) cudaFree(v);
     cudaFree(p.tu);
     cudaFree(p.thx);

@@ -1,0 +1,223 @@
+// Fast summation on non-uniform periodic lines (the point-local quadrature
+// that Sec. 2.4 describes for non-uniform meshes): per point i the J_R / J_L
+// weights of its own stencil nodes and the cell decay q_i = e^{-alpha (x_i -
+// x_{i-1})}; the recurrences I_R(x_i) = q_i I_R(x_{i-1}) + J_R(x_i),
+// I_L(x_i) = q_{i+1} I_L(x_{i+1}) + J_L(x_i) close over the period with
+// mu = prod q_i = e^{-alpha L} (Sec. 2.3).
+//
+// Host side: build_nonuniform_tables() integrates the Lagrange basis of each
+// point's stencil against the exponential by 16-point Gauss-Legendre
+// quadrature (FP64).  Device side: one warp per line, the line staged in
+// shared memory; each D application scans the line in chunks of 32 x 4
+// points (per-lane affine maps (q, J), a warp scan of their compositions,
+// the chunk's carry passed on), twice per direction: once from 0 to get the
+// period's partial sum, once from the periodic closure value.
+#pragma once
+
+#include <cmath>
+#include <vector>
+
+#include "sweep.cuh"
+
+namespace molt {
+
+// Device tables of one (axis, alpha, rule): structure of arrays, slot m of
+// the weights belongs to offset m - 3 (offsets -3..2; unused slots are 0).
+template <typename T>
+struct NuTables {
+  const T* cR;   // [6][n]: J_R(x_i) = sum_m cR[m][i] v_{i + m - 3}
+  const T* cL;   // [6][n]: J_L(x_i) = sum_m cL[m][i] v_{i - (m - 3)}
+  const T* q;    // [n]: q_i = e^{-alpha (x_i - x_{i-1})}
+};
+
+struct NuArgs {
+  LineGeom g;
+  int mode, P;
+  double inv1mmu;       // 1/(1 - mu), mu = e^{-alpha L}
+  const void* in;
+  void* out;
+  int* status;
+};
+
+// Roots and weights of the n-point Gauss-Legendre rule on [-1, 1] (Newton on
+// the three-term recurrence of the Legendre polynomials).
+inline void gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      const double dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) {
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        break;
+      }
+      x[i] = z;
+      w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+  }
+}
+
+// cR, cL: 6*n (slot-major), q: n.  x: the n nodes of one period [x_0, x_0 + L).
+inline void build_nonuniform_tables(const std::vector<double>& x, double L, double alpha, int npts,
+                                    std::vector<double>* cR, std::vector<double>* cL, std::vector<double>* q) {
+  const int n = int(x.size());
+  int lo = -3, hi = 2;                 // J_R stencil offsets (6 points)
+  if (npts == 5) hi = 1;
+  if (npts == 3) { lo = -1; hi = 1; }
+  const int k = hi - lo + 1;
+  cR->assign(6 * size_t(n), 0.0);
+  cL->assign(6 * size_t(n), 0.0);
+  q->assign(n, 0.0);
+  constexpr int kG = 16;
+  double gx[kG], gw[kG];
+  gauss_legendre(kG, gx, gw);
+  auto node = [&](long long j) {
+    long long r = j % n;
+    if (r < 0) r += n;
+    return x[size_t(r)] + double((j - r) / n) * L;
+  };
+  for (int i = 0; i < n; ++i) {
+    const double xi = x[size_t(i)];
+    for (int side = 0; side < 2; ++side) {
+      // J_R: cell [x_{i-1}, x_i], nodes x_{i+l}; J_L: cell [x_i, x_{i+1}], nodes x_{i-l}
+      const double a = side == 0 ? node(i - 1) : xi, b = side == 0 ? xi : node(i + 1);
+      double t[6];
+      for (int m = 0; m < k; ++m) t[m] = node(side == 0 ? i + lo + m : i - (lo + m)) - xi;
+      for (int m = 0; m < k; ++m) {
+        double sum = 0.0;
+        for (int gq = 0; gq < kG; ++gq) {
+          const double s = 0.5 * (b - a) * gx[gq] + 0.5 * (b + a);
+          double ell = 1.0;
+          for (int r = 0; r < k; ++r)
+            if (r != m) ell *= ((s - xi) - t[r]) / (t[m] - t[r]);
+          const double kern = side == 0 ? std::exp(-alpha * (xi - s)) : std::exp(-alpha * (s - xi));
+          sum += 0.5 * (b - a) * gw[gq] * alpha * kern * ell;
+        }
+        (side == 0 ? *cR : *cL)[size_t(lo + m + 3) * n + i] = sum;
+      }
+    }
+    (*q)[size_t(i)] = std::exp(-alpha * (xi - node(i - 1)));
+  }
+}
+
+// One direction of the recurrences over the staged line v (ghosts G = 3 each
+// side), in chunks of 32 x 4 points, starting from the value x0 before the
+// first point; writes I into w (R: ascending, L: descending).  Returns the
+// value after the last point.
+template <typename T, bool LEFT>
+__device__ __forceinline__ T nu_scan(const NuTables<T>& tb, const T* v, T* w, int n, T x0, int lane) {
+  constexpr int kPer = 4;
+  T carry = x0;
+  for (int c0 = 0; c0 < n; c0 += 32 * kPer) {
+    T qk[kPer], jk[kPer];
+    T A = T(1), B = T(0);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int step = c0 + lane * kPer + k;          // position along the scan
+      qk[k] = T(1);
+      jk[k] = T(0);
+      if (step < n) {
+        const int i = LEFT ? n - 1 - step : step;
+        T J = T(0);
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+          const int off = m - 3;
+          if (LEFT) J = fma(tb.cL[m * n + i], v[3 + i - off], J);
+          else J = fma(tb.cR[m * n + i], v[3 + i + off], J);
+        }
+        qk[k] = LEFT ? tb.q[i + 1 < n ? i + 1 : 0] : tb.q[i];
+        jk[k] = J;
+        B = fma(qk[k], B, J);
+        A *= qk[k];
+      }
+    }
+    // inclusive scan of the lane maps x -> A x + B (later lanes apply after)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T Ap = __shfl_up_sync(0xffffffffu, A, o), Bp = __shfl_up_sync(0xffffffffu, B, o);
+      if (lane >= o) {
+        B = fma(A, Bp, B);
+        A *= Ap;
+      }
+    }
+    T Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
+    if (lane == 0) {
+      Ae = T(1);
+      Be = T(0);
+    }
+    T y = fma(Ae, carry, Be);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int step = c0 + lane * kPer + k;
+      if (step < n) {
+        y = fma(qk[k], y, jk[k]);
+        w[LEFT ? n - 1 - step : step] = y;
+      }
+    }
+    const T At = __shfl_sync(0xffffffffu, A, 31), Bt = __shfl_sync(0xffffffffu, B, 31);
+    carry = fma(At, carry, Bt);
+  }
+  return carry;
+}
+
+// S_P along non-uniform periodic lines: one warp per line, `warps` lines per
+// CTA; shared memory per warp: v (n + 6) and w (n) of T, plus (MODE_0) I_L (n).
+template <typename T, typename TIO>
+__global__ void nonuniform_kernel(const NuArgs a, const NuTables<T> tb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = a.g.n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long line = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+  const size_t per = size_t(3 * n + 6);
+  T* v = reinterpret_cast<T*>(smem_raw) + per * warp;
+  T* w = v + n + 6;
+  T* wl = w + n;
+  if (line >= a.g.nlines) return;
+  const long long base = line_base(a.g, line);
+  const long long st = a.g.stride;
+  const TIO* in = static_cast<const TIO*>(a.in);
+  TIO* out = static_cast<TIO*>(a.out);
+  for (int i = lane; i < n; i += 32) v[3 + i] = T(in[base + i * st]);
+  __syncwarp();
+  const T k1 = T(a.inv1mmu);
+  for (int p = 0; p < a.P; ++p) {
+    if (lane < 3) {
+      const int j = lane + 1;
+      v[3 - j] = v[3 + ((n - j) % n + n) % n];
+      v[3 + n - 1 + j] = v[3 + (j - 1) % n];
+    }
+    __syncwarp();
+    if (a.mode != MODE_L) {
+      const T end = nu_scan<T, false>(tb, v, w, n, T(0), lane);
+      __syncwarp();
+      nu_scan<T, false>(tb, v, w, n, end * k1, lane);
+    }
+    if (a.mode != MODE_R) {
+      T* dl = a.mode == MODE_L ? w : wl;
+      const T end = nu_scan<T, true>(tb, v, dl, n, T(0), lane);
+      __syncwarp();
+      nu_scan<T, true>(tb, v, dl, n, end * k1, lane);
+    }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const T linv = a.mode == MODE_0 ? T(0.5) * (w[i] + wl[i]) : w[i];
+      const T d = v[3 + i] - linv;
+      TIO* o = out + base + i * st;
+      *o = p == 0 ? TIO(d) : TIO(T(*o) + d);
+      w[i] = d;
+    }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) v[3 + i] = w[i];
+    __syncwarp();
+  }
+}
+
+}  // namespace molt

@@ -24,7 +24,7 @@ INT_DEFAULT, INT_EULER, INT_RK3 = 0, 1, 2
 EXPORTS = ("molt_create", "molt_apply_D", "molt_step", "molt_set_option", "molt_profile_read", "molt_destroy",
            "molt_last_error", "molt_wave_step_noalloc", "molt_batch_tile_shape", "molt_set_mlp", "molt_mlp_stats",
            "molt_weno_linear_weights", "molt_mlp_pack", "molt_mlp_forward", "molt_mlp_loss_grad", "molt_mlp_adam",
-           "molt_mlp_harvest", "molt_quadrature_weights", "molt_set_source")
+           "molt_mlp_harvest", "molt_quadrature_weights", "molt_set_source", "molt_set_grid_axis")
 MLP_PARAMS = 1347
 MLP_BLOB_BYTES = 3728
 OPT_TMA, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_TEST_SKIP_ARRIVE = 0, 1, 2, 3
@@ -92,6 +92,7 @@ def load_library(path=LIB_PATH):
         vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
         lib.molt_set_mlp.argtypes = [vp, vp, ctypes.c_size_t]
         lib.molt_set_source.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
+        lib.molt_set_grid_axis.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl), i64]
         lib.molt_mlp_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.c_int]
         lib.molt_weno_linear_weights.argtypes = [dbl, ctypes.POINTER(dbl)]
         lib.molt_quadrature_weights.argtypes = [ctypes.c_int, dbl, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
@@ -102,7 +103,8 @@ def load_library(path=LIB_PATH):
         lib.molt_mlp_adam.argtypes = [vp, vp, vp, vp, i64, dbl, dbl, dbl, dbl, vp, vp]
         lib.molt_mlp_harvest.argtypes = [vp, i64, i64, vp, i64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl), vp,
                                          vp, i64, vp]
-        for f in ("molt_set_mlp", "molt_set_source", "molt_mlp_stats", "molt_weno_linear_weights", "molt_quadrature_weights",
+        for f in ("molt_set_mlp", "molt_set_source", "molt_set_grid_axis", "molt_mlp_stats",
+                  "molt_weno_linear_weights", "molt_quadrature_weights",
                   "molt_mlp_pack", "molt_mlp_forward",
                   "molt_mlp_loss_grad", "molt_mlp_adam", "molt_mlp_harvest"):
             getattr(lib, f).restype = ctypes.c_int
@@ -266,6 +268,17 @@ def molt_set_source(ctx, problem, coef, degree=None):
         raise ValueError("source coefficients must be contiguous")
     deg = coef.shape[0] - 1 if degree is None else degree
     _check(lib, ctx, lib.molt_set_source(ctx, problem, ctypes.c_void_p(coef.data_ptr()), deg))
+
+
+def molt_set_grid_axis(ctx, problem, axis, x):
+    """Non-uniform periodic axis from the node coordinates ``x`` of one period
+    (a sequence of floats), or None for a uniform axis again."""
+    lib = load_library()
+    if x is None:
+        _check(lib, ctx, lib.molt_set_grid_axis(ctx, problem, axis, None, 0))
+        return
+    arr = (ctypes.c_double * len(x))(*[float(v) for v in x])
+    _check(lib, ctx, lib.molt_set_grid_axis(ctx, problem, axis, arr, len(x)))
 
 
 def molt_mlp_stats(ctx, reset=False):

@@ -1,0 +1,112 @@
+"""GPU parity of sum_{p<=P} D^p along non-uniform periodic axes (point-local
+quadrature weights, the non-uniform case of Sec. 2.4) against the FP64
+oracle: 1-D lines of several lengths, every operator and rule, P = 1..3,
+FP64 / FP32 / mixed, contiguous and strided axes, in place; rejected setups."""
+import numpy as np
+import pytest
+
+from oracle import nonuniform
+from paper_2007_03041_gb300 import molt as M
+from paper_2007_03041_gb300 import workloads
+from tests.gpu_util import need_gpu, rel_l2, state_dtype, to_dev, tol_for
+
+pytestmark = pytest.mark.gpu
+OPS = {M.OP_L: "L", M.OP_R: "R", M.OP_0: "0"}
+
+
+def _nodes(n, lo, L, amp=0.3):
+    xi = L * np.arange(n) / n
+    return lo + xi + amp * (L / (2 * np.pi)) * np.sin(2 * np.pi * xi / L)
+
+
+@pytest.mark.parametrize("prec", [M.PREC_F64, M.PREC_F32, M.PREC_F32_F64UPDATE])
+@pytest.mark.parametrize("npts", [3, 5, 6])
+def test_lines_1d(prec, npts):
+    need_gpu()
+    import torch
+    lo, L = 0.5, 3.0
+    for n, op, P in ((7, M.OP_0, 1), (100, M.OP_R, 2), (513, M.OP_L, 3), (1000, M.OP_0, 2), (2048, M.OP_R, 1)):
+        x = _nodes(n, lo, L)
+        alpha = 0.6 * n / L                      # nu ~ 0.6 on the average cell
+        v = workloads.rng(n).standard_normal(n)
+        if prec == M.PREC_F32:
+            v = v.astype(np.float32).astype(np.float64)
+        d = M.make_desc((n,), lo=[lo], hi=[lo + L], quad_points=npts, prec=prec)
+        ctx = M.molt_create(d)
+        try:
+            M.molt_set_grid_axis(ctx, 0, 0, x)
+            vin = to_dev(v, state_dtype(prec))
+            out = torch.empty_like(vin)
+            M.molt_apply_D(ctx, 0, 0, op, P, alpha, vin, out)
+            got = out.double().cpu().numpy()
+        finally:
+            M.molt_destroy(ctx)
+        want = nonuniform.partial_sum(v, x, L, alpha, OPS[op], npts, P)
+        assert rel_l2(got, want) < tol_for(prec), (n, op, P)
+
+
+@pytest.mark.parametrize("prec", [M.PREC_F64, M.PREC_F32])
+def test_both_axes_of_a_2d_grid_and_in_place(prec):
+    need_gpu()
+    import torch
+    nx, ny, L = 96, 80, 2 * np.pi
+    xs, ys = _nodes(nx, 0.0, L), _nodes(ny, 0.0, L, amp=0.4)
+    u = workloads.rng(5).standard_normal((ny, nx))
+    if prec == M.PREC_F32:
+        u = u.astype(np.float32).astype(np.float64)
+    d = M.make_desc((nx, ny), lo=[0, 0], hi=[L, L], quad_points=6, prec=prec)
+    ctx = M.molt_create(d)
+    try:
+        M.molt_set_grid_axis(ctx, 0, 0, xs)
+        M.molt_set_grid_axis(ctx, 0, 1, ys)
+        uin = to_dev(u, state_dtype(prec))
+        gx = torch.empty_like(uin)
+        M.molt_apply_D(ctx, 0, 0, M.OP_0, 2, 9.0, uin, gx)
+        gy = uin.clone()
+        M.molt_apply_D(ctx, 0, 1, M.OP_R, 2, 7.0, gy, gy)         # in place
+        gotx, goty = gx.double().cpu().numpy(), gy.double().cpu().numpy()
+    finally:
+        M.molt_destroy(ctx)
+    wantx = np.stack([nonuniform.partial_sum(u[j], xs, L, 9.0, "0", 6, 2) for j in range(ny)])
+    wanty = np.stack([nonuniform.partial_sum(u[:, i], ys, L, 7.0, "R", 6, 2) for i in range(nx)], axis=1)
+    assert rel_l2(gotx, wantx) < tol_for(prec)
+    assert rel_l2(goty, wanty) < tol_for(prec)
+
+
+def test_rejected_setups():
+    need_gpu()
+    import torch
+    n, L = 64, 2.0
+    d = M.make_desc((n, n), lo=[0, 0], hi=[L, L], prec=M.PREC_F64, pde=M.PDE_HEAT, dt=0.01)
+    ctx = M.molt_create(d)
+    try:
+        with pytest.raises(M.MoltError):
+            M.molt_set_grid_axis(ctx, 0, 0, _nodes(n - 1, 0.0, L))            # wrong count
+        with pytest.raises(M.MoltError):
+            M.molt_set_grid_axis(ctx, 0, 0, _nodes(n, 0.0, L)[::-1])          # not increasing
+        with pytest.raises(M.MoltError):
+            M.molt_set_grid_axis(ctx, 0, 0, np.linspace(0, 1.5 * L, n))      # wider than the period
+        M.molt_set_grid_axis(ctx, 0, 1, _nodes(n, 0.0, L))
+        u = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+        with pytest.raises(M.MoltError):
+            M.molt_step(ctx, u, None, nsteps=1, t=[0.0])                      # molt_step: uniform grids
+        M.molt_set_grid_axis(ctx, 0, 1, None)
+        M.molt_step(ctx, u, None, nsteps=1, t=[0.0])
+    finally:
+        M.molt_destroy(ctx)
+    dd = M.make_desc((n,), bc=[M.BC_DIRICHLET], lo=[0], hi=[L], prec=M.PREC_F64)
+    ctx = M.molt_create(dd)
+    try:
+        with pytest.raises(M.MoltError):
+            M.molt_set_grid_axis(ctx, 0, 0, _nodes(n, 0.0, L))
+    finally:
+        M.molt_destroy(ctx)
+    dw = M.make_desc((n,), lo=[0], hi=[L], prec=M.PREC_F64, quad_points=5, weights=M.W_WENOZ)
+    ctx = M.molt_create(dw)
+    try:
+        M.molt_set_grid_axis(ctx, 0, 0, _nodes(n, 0.0, L))
+        v = torch.zeros(n, dtype=torch.float64, device="cuda")
+        with pytest.raises(M.MoltError):
+            M.molt_apply_D(ctx, 0, 0, M.OP_0, 1, 5.0, v, v)
+    finally:
+        M.molt_destroy(ctx)
