@@ -208,26 +208,33 @@ int device_sms() {
 
 // Points per lane for a line of n points: the largest of 16, 8, 4 whose
 // tile fits the line exactly (n = 32 * E * nwl, nwl <= 16 warps), else 16
-// with masked (ragged) tiles.  FP64 sweeps take the smallest that fits: their
-// recurrences wait on the FP64 pipe (2 operations per SM per cycle), so more
-// warps per line hide more of its latency (256^2 heat: 0.129 instead of
-// 0.165 ms per step with 4 instead of 8 points per lane).
+// with masked (ragged) tiles.  FP64 sweeps of grids with few lines take the
+// largest E that still gives 16 warps per SM, else the smallest that fits:
+// their recurrences wait on the FP64 pipe (2 operations per SM per cycle),
+// so more warps per line hide more of its latency (256^2 heat: 0.129
+// instead of 0.165 ms per step with 4 instead of 8 points per lane), while
+// grids with many lines keep the larger tiles.
 #ifndef MOLT_PREFER_E
 #define MOLT_PREFER_E 16
 #endif
 #ifndef MOLT_F64_SMALL_E
 #define MOLT_F64_SMALL_E 1
 #endif
-int choose_E(int n, bool f64) {
-  // plain arrays: a range-for over a conditional of two initializer lists
-  // would read a backing array whose lifetime has ended
-  static const int kSmallFirst[4] = {4, 8, 16, 16};
-  static const int kLargeFirst[4] = {MOLT_PREFER_E, 16, 8, 4};
-  const int* order = (f64 && MOLT_F64_SMALL_E) ? kSmallFirst : kLargeFirst;
-  for (int i = 0; i < 4; ++i) {
-    const int E = order[i];
-    if (n % (32 * E) == 0 && n / (32 * E) <= kMaxThreads / 32) return E;
+int choose_E(int n, bool f64, long long nlines) {
+  auto fits = [n](int E) { return n % (32 * E) == 0 && n / (32 * E) <= kMaxThreads / 32; };
+  if (f64 && MOLT_F64_SMALL_E) {
+    const long long want = 16LL * device_sms();
+    int smallest = 0;
+    for (int E : {16, 8, 4}) {
+      if (!fits(E)) continue;
+      if (nlines * (n / (32 * E)) >= want) return E;
+      smallest = E;
+    }
+    return smallest ? smallest : kE;
   }
+  static const int kOrder[4] = {MOLT_PREFER_E, 16, 8, 4};
+  for (int i = 0; i < 4; ++i)
+    if (fits(kOrder[i])) return kOrder[i];
   return kE;
 }
 
@@ -243,7 +250,7 @@ molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, do
   a.g = geom(p, ax);
   const int n = a.g.n;
   const bool auto_shape = E == 0;
-  if (auto_shape) E = choose_E(n, compute_bytes(p.d) == 8);
+  if (auto_shape) E = choose_E(n, compute_bytes(p.d) == 8, a.g.nlines);
   a.E = E;
   a.bc = p.d.bc[ax];
   a.mode = mode;
@@ -781,7 +788,7 @@ molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int 
   a.in = in;
   a.out = out;
   a.status = c->status_dev;
-  const size_t per = size_t(3 * n + 6) * tb;
+  const size_t per = size_t(2 * n + 6) * tb;
   int warps = int(std::min<size_t>(8, std::max<size_t>(1, (200 * 1024) / per)));
   if (per > 200 * 1024) return fail(c, MOLT_EUNSUPPORTED, "non-uniform line too long for shared memory");
   while (warps > 1 && (a.g.nlines + warps - 1) / warps < 2LL * device_sms()) warps /= 2;

@@ -110,9 +110,11 @@ inline void build_nonuniform_tables(const std::vector<double>& x, double L, doub
 
 // One direction of the recurrences over the staged line v (ghosts G = 3 each
 // side), in chunks of 32 x 4 points, starting from the value x0 before the
-// first point; writes I into w (R: ascending, L: descending).  Returns the
-// value after the last point.
-template <typename T, bool LEFT>
+// first point (R: ascending, L: descending).  Returns the value after the
+// last point.  OUT: 0 stores nothing (the pass that finds the periodic
+// closure), 1 stores I in w, 2 stores D = v - I in w, 3 stores
+// D = v - (w + I)/2 in w (w holding I_R: the L pass of L_0).
+template <typename T, bool LEFT, int OUT>
 __device__ __forceinline__ T nu_scan(const NuTables<T>& tb, const T* v, T* w, int n, T x0, int lane) {
   constexpr int kPer = 4;
   T carry = x0;
@@ -153,14 +155,22 @@ __device__ __forceinline__ T nu_scan(const NuTables<T>& tb, const T* v, T* w, in
       Ae = T(1);
       Be = T(0);
     }
-    T y = fma(Ae, carry, Be);
+    if constexpr (OUT != 0) {
+      T y = fma(Ae, carry, Be);
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const int step = c0 + lane * kPer + k;
-      if (step < n) {
-        y = fma(qk[k], y, jk[k]);
-        w[LEFT ? n - 1 - step : step] = y;
+      for (int k = 0; k < kPer; ++k) {
+        const int step = c0 + lane * kPer + k;
+        if (step < n) {
+          y = fma(qk[k], y, jk[k]);
+          const int i = LEFT ? n - 1 - step : step;
+          if constexpr (OUT == 1) w[i] = y;
+          if constexpr (OUT == 2) w[i] = v[3 + i] - y;
+          if constexpr (OUT == 3) w[i] = v[3 + i] - T(0.5) * (w[i] + y);
+        }
       }
+    } else {
+      (void)Ae;
+      (void)Be;
     }
     const T At = __shfl_sync(0xffffffffu, A, 31), Bt = __shfl_sync(0xffffffffu, B, 31);
     carry = fma(At, carry, Bt);
@@ -169,17 +179,16 @@ __device__ __forceinline__ T nu_scan(const NuTables<T>& tb, const T* v, T* w, in
 }
 
 // S_P along non-uniform periodic lines: one warp per line, `warps` lines per
-// CTA; shared memory per warp: v (n + 6) and w (n) of T, plus (MODE_0) I_L (n).
+// CTA; shared memory per warp: v (n + 6) and w (n) of T.
 template <typename T, typename TIO>
 __global__ void nonuniform_kernel(const NuArgs a, const NuTables<T> tb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = a.g.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long line = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-  const size_t per = size_t(3 * n + 6);
+  const size_t per = size_t(2 * n + 6);
   T* v = reinterpret_cast<T*>(smem_raw) + per * warp;
   T* w = v + n + 6;
-  T* wl = w + n;
   if (line >= a.g.nlines) return;
   const long long base = line_base(a.g, line);
   const long long st = a.g.stride;
@@ -195,24 +204,23 @@ __global__ void nonuniform_kernel(const NuArgs a, const NuTables<T> tb) {
       v[3 + n - 1 + j] = v[3 + (j - 1) % n];
     }
     __syncwarp();
+    // D into w: R alone, L alone, or I_R first and then the L pass of L_0
     if (a.mode != MODE_L) {
-      const T end = nu_scan<T, false>(tb, v, w, n, T(0), lane);
-      __syncwarp();
-      nu_scan<T, false>(tb, v, w, n, end * k1, lane);
+      const T end = nu_scan<T, false, 0>(tb, v, w, n, T(0), lane);
+      if (a.mode == MODE_R) nu_scan<T, false, 2>(tb, v, w, n, end * k1, lane);
+      else nu_scan<T, false, 1>(tb, v, w, n, end * k1, lane);
     }
+    __syncwarp();
     if (a.mode != MODE_R) {
-      T* dl = a.mode == MODE_L ? w : wl;
-      const T end = nu_scan<T, true>(tb, v, dl, n, T(0), lane);
-      __syncwarp();
-      nu_scan<T, true>(tb, v, dl, n, end * k1, lane);
+      const T end = nu_scan<T, true, 0>(tb, v, w, n, T(0), lane);
+      if (a.mode == MODE_L) nu_scan<T, true, 2>(tb, v, w, n, end * k1, lane);
+      else nu_scan<T, true, 3>(tb, v, w, n, end * k1, lane);
     }
     __syncwarp();
     for (int i = lane; i < n; i += 32) {
-      const T linv = a.mode == MODE_0 ? T(0.5) * (w[i] + wl[i]) : w[i];
-      const T d = v[3 + i] - linv;
+      const T d = w[i];
       TIO* o = out + base + i * st;
       *o = p == 0 ? TIO(d) : TIO(T(*o) + d);
-      w[i] = d;
     }
     __syncwarp();
     for (int i = lane; i < n; i += 32) v[3 + i] = w[i];
