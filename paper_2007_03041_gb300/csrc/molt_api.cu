@@ -788,12 +788,13 @@ molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int 
   a.in = in;
   a.out = out;
   a.status = c->status_dev;
-  const size_t per = size_t(2 * n + 6) * tb;
-  int warps = int(std::min<size_t>(8, std::max<size_t>(1, (200 * 1024) / per)));
-  if (per > 200 * 1024) return fail(c, MOLT_EUNSUPPORTED, "non-uniform line too long for shared memory");
-  while (warps > 1 && (a.g.nlines + warps - 1) / warps < 2LL * device_sms()) warps /= 2;
-  const long long blocks = (a.g.nlines + warps - 1) / warps;
-  const size_t smem = per * warps;
+  // one CTA per line, up to 8 warps splitting its scan positions (512 each)
+  const int nw = std::max(1, std::min(8, (n + 511) / 512));
+  const size_t smem = (size_t(2 * n + 6) + size_t(2 * nw)) * tb;
+  if (smem > 200 * 1024) return fail(c, MOLT_EUNSUPPORTED, "non-uniform line too long for shared memory");
+  if (a.g.nlines >= (1LL << 31)) return fail(c, MOLT_EUNSUPPORTED, "more than 2^31 lines along an axis");
+  const long long blocks = a.g.nlines;
+  const int warps = nw;
   molt_ctx::Rec rec;
   record_begin(c, &rec, MOLT_KERNEL_STORE);
   if (f64) {

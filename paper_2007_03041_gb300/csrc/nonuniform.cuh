@@ -7,11 +7,13 @@
 //
 // Host side: build_nonuniform_tables() integrates the Lagrange basis of each
 // point's stencil against the exponential by 16-point Gauss-Legendre
-// quadrature (FP64).  Device side: one warp per line, the line staged in
-// shared memory; each D application scans the line in chunks of 32 x 4
-// points (per-lane affine maps (q, J), a warp scan of their compositions,
-// the chunk's carry passed on), twice per direction: once from 0 to get the
-// period's partial sum, once from the periodic closure value.
+// quadrature (FP64).  Device side: one CTA per line, the line staged in
+// shared memory and its scan positions split between the CTA's warps; each
+// D application scans a warp's segment in chunks of 32 x 4 points (per-lane
+// affine maps (q, J), a warp scan of their compositions, the chunk's carry
+// passed on) twice per direction: once composing the segment's map only,
+// once from the start value that the segment maps and the periodic closure
+// give.
 #pragma once
 
 #include <cmath>
@@ -108,17 +110,19 @@ inline void build_nonuniform_tables(const std::vector<double>& x, double L, doub
   }
 }
 
-// One direction of the recurrences over the staged line v (ghosts G = 3 each
-// side), in chunks of 32 x 4 points, starting from the value x0 before the
-// first point (R: ascending, L: descending).  Returns the value after the
-// last point.  OUT: 0 stores nothing (the pass that finds the periodic
-// closure), 1 stores I in w, 2 stores D = v - I in w, 3 stores
-// D = v - (w + I)/2 in w (w holding I_R: the L pass of L_0).
-template <typename T, bool LEFT, int OUT>
-__device__ __forceinline__ T nu_scan(const NuTables<T>& tb, const T* v, T* w, int n, T x0, int lane) {
+// One chunked pass of one direction over the scan positions [s0, s1) of the
+// staged line v (ghosts G = 3 each side; R ascending, L descending), in
+// chunks of 32 x 4 points.  MAP: return the pass's composed affine map
+// (A, B) (x -> A x + B, from the value before s0 to the value after s1 - 1)
+// and store nothing.  Otherwise start from x0 and store by OUT: 1 I in w,
+// 2 D = v - I in w, 3 D = v - (w + I)/2 in w (w holding I_R: the L pass of
+// L_0).
+template <typename T, bool LEFT, bool MAP, int OUT>
+__device__ __forceinline__ void nu_pass(const NuTables<T>& tb, const T* v, T* w, int n, int s0, int s1, T x0,
+                                        int lane, T* mapA, T* mapB) {
   constexpr int kPer = 4;
-  T carry = x0;
-  for (int c0 = 0; c0 < n; c0 += 32 * kPer) {
+  T carry = x0, cA = T(1), cB = T(0);
+  for (int c0 = s0; c0 < s1; c0 += 32 * kPer) {
     T qk[kPer], jk[kPer];
     T A = T(1), B = T(0);
 #pragma unroll
@@ -126,7 +130,7 @@ __device__ __forceinline__ T nu_scan(const NuTables<T>& tb, const T* v, T* w, in
       const int step = c0 + lane * kPer + k;          // position along the scan
       qk[k] = T(1);
       jk[k] = T(0);
-      if (step < n) {
+      if (step < s1) {
         const int i = LEFT ? n - 1 - step : step;
         T J = T(0);
 #pragma unroll
@@ -150,17 +154,21 @@ __device__ __forceinline__ T nu_scan(const NuTables<T>& tb, const T* v, T* w, in
         A *= Ap;
       }
     }
-    T Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
-    if (lane == 0) {
-      Ae = T(1);
-      Be = T(0);
-    }
-    if constexpr (OUT != 0) {
+    const T At = __shfl_sync(0xffffffffu, A, 31), Bt = __shfl_sync(0xffffffffu, B, 31);
+    if constexpr (MAP) {
+      cB = fma(At, cB, Bt);
+      cA *= At;
+    } else {
+      T Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
+      if (lane == 0) {
+        Ae = T(1);
+        Be = T(0);
+      }
       T y = fma(Ae, carry, Be);
 #pragma unroll
       for (int k = 0; k < kPer; ++k) {
         const int step = c0 + lane * kPer + k;
-        if (step < n) {
+        if (step < s1) {
           y = fma(qk[k], y, jk[k]);
           const int i = LEFT ? n - 1 - step : step;
           if constexpr (OUT == 1) w[i] = y;
@@ -168,63 +176,86 @@ __device__ __forceinline__ T nu_scan(const NuTables<T>& tb, const T* v, T* w, in
           if constexpr (OUT == 3) w[i] = v[3 + i] - T(0.5) * (w[i] + y);
         }
       }
-    } else {
-      (void)Ae;
-      (void)Be;
+      carry = fma(At, carry, Bt);
     }
-    const T At = __shfl_sync(0xffffffffu, A, 31), Bt = __shfl_sync(0xffffffffu, B, 31);
-    carry = fma(At, carry, Bt);
   }
-  return carry;
+  if constexpr (MAP) {
+    *mapA = cA;
+    *mapB = cB;
+  }
 }
 
-// S_P along non-uniform periodic lines: one warp per line, `warps` lines per
-// CTA; shared memory per warp: v (n + 6) and w (n) of T.
+// One direction with the periodic closure, split over the `nw` warps of the
+// line (segment `seg` scan positions each): every warp composes its
+// segment's map, the maps go through shared memory (maps[2 * nw]), each warp
+// composes the earlier segments' maps into its start value for I = 0 before
+// the line, the line's last value closes the period (x = I_end / (1 - mu)),
+// and the segments are scanned again from their closed start values.
+template <typename T, bool LEFT, int OUT>
+__device__ __forceinline__ void nu_direction(const NuTables<T>& tb, const T* v, T* w, int n, int nw, int part,
+                                             int seg, T k1, T* maps, int lane) {
+  const int s0 = min(n, part * seg), s1 = min(n, s0 + seg);
+  T A, B;
+  nu_pass<T, LEFT, true, 0>(tb, v, w, n, s0, s1, T(0), lane, &A, &B);
+  if (lane == 0) {
+    maps[2 * part] = A;
+    maps[2 * part + 1] = B;
+  }
+  __syncthreads();
+  // value before this segment from I = 0 before the line, and the line's end value
+  T pre = T(0), all = T(0);
+  for (int j = 0; j < nw; ++j) {
+    if (j == part) pre = all;
+    all = fma(maps[2 * j], all, maps[2 * j + 1]);
+  }
+  // closed start: the closure value x carried through the earlier segments
+  const T x = all * k1;
+  T gA = T(1);
+  for (int j = 0; j < part; ++j) gA *= maps[2 * j];
+  const T start = fma(gA, x, pre);
+  nu_pass<T, LEFT, false, OUT>(tb, v, w, n, s0, s1, start, lane, nullptr, nullptr);
+  __syncthreads();
+}
+
+// S_P along non-uniform periodic lines: one CTA of `nw` warps per line (the
+// scan positions split into nw segments); shared memory: v (n + 6) and w (n)
+// of T plus the segment maps.
 template <typename T, typename TIO>
 __global__ void nonuniform_kernel(const NuArgs a, const NuTables<T> tb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = a.g.n;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long line = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-  const size_t per = size_t(2 * n + 6);
-  T* v = reinterpret_cast<T*>(smem_raw) + per * warp;
+  const int nw = blockDim.x >> 5, part = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long line = blockIdx.x;
+  T* v = reinterpret_cast<T*>(smem_raw);
   T* w = v + n + 6;
-  if (line >= a.g.nlines) return;
+  T* maps = w + n;
+  const int seg = ((n + nw - 1) / nw + 127) / 128 * 128;
   const long long base = line_base(a.g, line);
   const long long st = a.g.stride;
   const TIO* in = static_cast<const TIO*>(a.in);
   TIO* out = static_cast<TIO*>(a.out);
-  for (int i = lane; i < n; i += 32) v[3 + i] = T(in[base + i * st]);
-  __syncwarp();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[3 + i] = T(in[base + i * st]);
+  __syncthreads();
   const T k1 = T(a.inv1mmu);
   for (int p = 0; p < a.P; ++p) {
-    if (lane < 3) {
-      const int j = lane + 1;
+    if (threadIdx.x < 3) {
+      const int j = threadIdx.x + 1;
       v[3 - j] = v[3 + ((n - j) % n + n) % n];
       v[3 + n - 1 + j] = v[3 + (j - 1) % n];
     }
-    __syncwarp();
+    __syncthreads();
     // D into w: R alone, L alone, or I_R first and then the L pass of L_0
-    if (a.mode != MODE_L) {
-      const T end = nu_scan<T, false, 0>(tb, v, w, n, T(0), lane);
-      if (a.mode == MODE_R) nu_scan<T, false, 2>(tb, v, w, n, end * k1, lane);
-      else nu_scan<T, false, 1>(tb, v, w, n, end * k1, lane);
-    }
-    __syncwarp();
-    if (a.mode != MODE_R) {
-      const T end = nu_scan<T, true, 0>(tb, v, w, n, T(0), lane);
-      if (a.mode == MODE_L) nu_scan<T, true, 2>(tb, v, w, n, end * k1, lane);
-      else nu_scan<T, true, 3>(tb, v, w, n, end * k1, lane);
-    }
-    __syncwarp();
-    for (int i = lane; i < n; i += 32) {
+    if (a.mode == MODE_R) nu_direction<T, false, 2>(tb, v, w, n, nw, part, seg, k1, maps, lane);
+    if (a.mode == MODE_0) nu_direction<T, false, 1>(tb, v, w, n, nw, part, seg, k1, maps, lane);
+    if (a.mode == MODE_L) nu_direction<T, true, 2>(tb, v, w, n, nw, part, seg, k1, maps, lane);
+    if (a.mode == MODE_0) nu_direction<T, true, 3>(tb, v, w, n, nw, part, seg, k1, maps, lane);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const T d = w[i];
       TIO* o = out + base + i * st;
       *o = p == 0 ? TIO(d) : TIO(T(*o) + d);
+      v[3 + i] = d;
     }
-    __syncwarp();
-    for (int i = lane; i < n; i += 32) v[3 + i] = w[i];
-    __syncwarp();
+    __syncthreads();
   }
 }
 
