@@ -788,8 +788,10 @@ molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int 
   a.in = in;
   a.out = out;
   a.status = c->status_dev;
-  // one CTA per line, up to 8 warps splitting its scan positions (512 each)
-  const int nw = std::max(1, std::min(8, (n + 511) / 512));
+  // one CTA per line, its scan positions split between up to 16 warps (at
+  // most 512 each: the kernel keeps a segment's local integrals in registers)
+  const int nw = std::max(1, (n + 511) / 512);
+  if (nw > 16) return fail(c, MOLT_EUNSUPPORTED, "non-uniform line longer than 8192 points");
   const size_t smem = (size_t(2 * n + 6) + size_t(2 * nw)) * tb;
   if (smem > 200 * 1024) return fail(c, MOLT_EUNSUPPORTED, "non-uniform line too long for shared memory");
   if (a.g.nlines >= (1LL << 31)) return fail(c, MOLT_EUNSUPPORTED, "more than 2^31 lines along an axis");

@@ -8,12 +8,11 @@
 // Host side: build_nonuniform_tables() integrates the Lagrange basis of each
 // point's stencil against the exponential by 16-point Gauss-Legendre
 // quadrature (FP64).  Device side: one CTA per line, the line staged in
-// shared memory and its scan positions split between the CTA's warps; each
-// D application scans a warp's segment in chunks of 32 x 4 points (per-lane
-// affine maps (q, J), a warp scan of their compositions, the chunk's carry
-// passed on) twice per direction: once composing the segment's map only,
-// once from the start value that the segment maps and the periodic closure
-// give.
+// shared memory and its scan positions split between the CTA's warps; per D
+// application and direction each warp computes its segment's local integrals
+// once (chunks of 32 x 4 points: per-lane affine maps (q, J), a warp scan of
+// their compositions), the segment maps and the periodic closure give every
+// segment its start value, and the warp replays its chunks from there.
 #pragma once
 
 #include <cmath>
@@ -110,26 +109,32 @@ inline void build_nonuniform_tables(const std::vector<double>& x, double L, doub
   }
 }
 
-// One chunked pass of one direction over the scan positions [s0, s1) of the
-// staged line v (ghosts G = 3 each side; R ascending, L descending), in
-// chunks of 32 x 4 points.  MAP: return the pass's composed affine map
-// (A, B) (x -> A x + B, from the value before s0 to the value after s1 - 1)
-// and store nothing.  Otherwise start from x0 and store by OUT: 1 I in w,
-// 2 D = v - I in w, 3 D = v - (w + I)/2 in w (w holding I_R: the L pass of
-// L_0).
-template <typename T, bool LEFT, bool MAP, int OUT>
-__device__ __forceinline__ void nu_pass(const NuTables<T>& tb, const T* v, T* w, int n, int s0, int s1, T x0,
-                                        int lane, T* mapA, T* mapB) {
-  constexpr int kPer = 4;
-  T carry = x0, cA = T(1), cB = T(0);
-  for (int c0 = s0; c0 < s1; c0 += 32 * kPer) {
-    T qk[kPer], jk[kPer];
+// One direction with the periodic closure, split over the `nw` warps of the
+// line (segment `seg` <= 512 scan positions each, R ascending, L
+// descending).  Each warp computes the local integrals J and decays q of its
+// segment once (chunks of 32 x 4 points, kept in registers), the per-lane
+// affine maps x -> q x + J composed by a warp scan per chunk; the segments'
+// maps meet in shared memory (maps[2 * nw]); the line's last value from
+// I = 0 closes the period (x = I_end / (1 - mu)); each warp then replays its
+// chunks from its closed start value and stores by OUT: 1 I in w, 2 D = v - I
+// in w, 3 D = v - (w + I)/2 in w (w holding I_R: the L pass of L_0).
+template <typename T, bool LEFT, int OUT>
+__device__ __forceinline__ void nu_direction(const NuTables<T>& tb, const T* v, T* w, int n, int nw, int part,
+                                             int seg, T k1, T* maps, int lane) {
+  constexpr int kPer = 4, kChunks = 4;          // seg <= kChunks * 32 * kPer
+  const int s0 = min(n, part * seg), s1 = min(n, s0 + seg);
+  T jk[kChunks][kPer], qk[kChunks][kPer];
+  T Ae[kChunks], Be[kChunks], At[kChunks], Bt[kChunks];
+  T sA = T(1), sB = T(0);                        // the segment's map
+#pragma unroll
+  for (int c = 0; c < kChunks; ++c) {
+    const int c0 = s0 + c * 32 * kPer;
     T A = T(1), B = T(0);
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
-      const int step = c0 + lane * kPer + k;          // position along the scan
-      qk[k] = T(1);
-      jk[k] = T(0);
+      const int step = c0 + lane * kPer + k;
+      qk[c][k] = T(1);
+      jk[c][k] = T(0);
       if (step < s1) {
         const int i = LEFT ? n - 1 - step : step;
         T J = T(0);
@@ -139,13 +144,13 @@ __device__ __forceinline__ void nu_pass(const NuTables<T>& tb, const T* v, T* w,
           if (LEFT) J = fma(tb.cL[m * n + i], v[3 + i - off], J);
           else J = fma(tb.cR[m * n + i], v[3 + i + off], J);
         }
-        qk[k] = LEFT ? tb.q[i + 1 < n ? i + 1 : 0] : tb.q[i];
-        jk[k] = J;
-        B = fma(qk[k], B, J);
-        A *= qk[k];
+        qk[c][k] = LEFT ? tb.q[i + 1 < n ? i + 1 : 0] : tb.q[i];
+        jk[c][k] = J;
+        B = fma(qk[c][k], B, J);
+        A *= qk[c][k];
       }
     }
-    // inclusive scan of the lane maps x -> A x + B (later lanes apply after)
+    // inclusive scan of the lane maps (later lanes apply after)
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const T Ap = __shfl_up_sync(0xffffffffu, A, o), Bp = __shfl_up_sync(0xffffffffu, B, o);
@@ -154,74 +159,56 @@ __device__ __forceinline__ void nu_pass(const NuTables<T>& tb, const T* v, T* w,
         A *= Ap;
       }
     }
-    const T At = __shfl_sync(0xffffffffu, A, 31), Bt = __shfl_sync(0xffffffffu, B, 31);
-    if constexpr (MAP) {
-      cB = fma(At, cB, Bt);
-      cA *= At;
-    } else {
-      T Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
-      if (lane == 0) {
-        Ae = T(1);
-        Be = T(0);
-      }
-      T y = fma(Ae, carry, Be);
-#pragma unroll
-      for (int k = 0; k < kPer; ++k) {
-        const int step = c0 + lane * kPer + k;
-        if (step < s1) {
-          y = fma(qk[k], y, jk[k]);
-          const int i = LEFT ? n - 1 - step : step;
-          if constexpr (OUT == 1) w[i] = y;
-          if constexpr (OUT == 2) w[i] = v[3 + i] - y;
-          if constexpr (OUT == 3) w[i] = v[3 + i] - T(0.5) * (w[i] + y);
-        }
-      }
-      carry = fma(At, carry, Bt);
+    Ae[c] = __shfl_up_sync(0xffffffffu, A, 1);
+    Be[c] = __shfl_up_sync(0xffffffffu, B, 1);
+    if (lane == 0) {
+      Ae[c] = T(1);
+      Be[c] = T(0);
     }
+    At[c] = __shfl_sync(0xffffffffu, A, 31);
+    Bt[c] = __shfl_sync(0xffffffffu, B, 31);
+    sB = fma(At[c], sB, Bt[c]);
+    sA *= At[c];
   }
-  if constexpr (MAP) {
-    *mapA = cA;
-    *mapB = cB;
-  }
-}
-
-// One direction with the periodic closure, split over the `nw` warps of the
-// line (segment `seg` scan positions each): every warp composes its
-// segment's map, the maps go through shared memory (maps[2 * nw]), each warp
-// composes the earlier segments' maps into its start value for I = 0 before
-// the line, the line's last value closes the period (x = I_end / (1 - mu)),
-// and the segments are scanned again from their closed start values.
-template <typename T, bool LEFT, int OUT>
-__device__ __forceinline__ void nu_direction(const NuTables<T>& tb, const T* v, T* w, int n, int nw, int part,
-                                             int seg, T k1, T* maps, int lane) {
-  const int s0 = min(n, part * seg), s1 = min(n, s0 + seg);
-  T A, B;
-  nu_pass<T, LEFT, true, 0>(tb, v, w, n, s0, s1, T(0), lane, &A, &B);
   if (lane == 0) {
-    maps[2 * part] = A;
-    maps[2 * part + 1] = B;
+    maps[2 * part] = sA;
+    maps[2 * part + 1] = sB;
   }
   __syncthreads();
   // value before this segment from I = 0 before the line, and the line's end value
-  T pre = T(0), all = T(0);
+  T pre = T(0), all = T(0), gA = T(1);
   for (int j = 0; j < nw; ++j) {
     if (j == part) pre = all;
+    if (j < part) gA *= maps[2 * j];
     all = fma(maps[2 * j], all, maps[2 * j + 1]);
   }
-  // closed start: the closure value x carried through the earlier segments
-  const T x = all * k1;
-  T gA = T(1);
-  for (int j = 0; j < part; ++j) gA *= maps[2 * j];
-  const T start = fma(gA, x, pre);
-  nu_pass<T, LEFT, false, OUT>(tb, v, w, n, s0, s1, start, lane, nullptr, nullptr);
+  // closed start: the closure value carried through the earlier segments
+  T carry = fma(gA, all * k1, pre);
+#pragma unroll
+  for (int c = 0; c < kChunks; ++c) {
+    const int c0 = s0 + c * 32 * kPer;
+    T y = fma(Ae[c], carry, Be[c]);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int step = c0 + lane * kPer + k;
+      if (step < s1) {
+        y = fma(qk[c][k], y, jk[c][k]);
+        const int i = LEFT ? n - 1 - step : step;
+        if constexpr (OUT == 1) w[i] = y;
+        if constexpr (OUT == 2) w[i] = v[3 + i] - y;
+        if constexpr (OUT == 3) w[i] = v[3 + i] - T(0.5) * (w[i] + y);
+      }
+    }
+    carry = fma(At[c], carry, Bt[c]);
+  }
   __syncthreads();
 }
 
 // S_P along non-uniform periodic lines: one CTA of `nw` warps per line (the
-// scan positions split into nw segments); shared memory: v (n + 6) and w (n)
-// of T plus the segment maps.
+// scan positions split into nw segments of at most 512); shared memory: v
+// (n + 6) and w (n) of T plus the segment maps.
 template <typename T, typename TIO>
-__global__ void nonuniform_kernel(const NuArgs a, const NuTables<T> tb) {
+__global__ void __launch_bounds__(512, 1) nonuniform_kernel(const NuArgs a, const NuTables<T> tb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = a.g.n;
   const int nw = blockDim.x >> 5, part = threadIdx.x >> 5, lane = threadIdx.x & 31;

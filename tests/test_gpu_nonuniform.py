@@ -110,3 +110,24 @@ def test_rejected_setups():
             M.molt_apply_D(ctx, 0, 0, M.OP_0, 1, 5.0, v, v)
     finally:
         M.molt_destroy(ctx)
+
+
+def test_longest_line_uses_sixteen_warps():
+    """8192 points: 16 warps of 512 scan positions per line."""
+    need_gpu()
+    import torch
+    n, lo, L = 8192, 0.0, 2 * np.pi
+    x = _nodes(n, lo, L)
+    v = workloads.rng(3).standard_normal(n).astype(np.float32).astype(np.float64)
+    d = M.make_desc((n,), lo=[lo], hi=[lo + L], quad_points=6, prec=M.PREC_F32)
+    ctx = M.molt_create(d)
+    try:
+        M.molt_set_grid_axis(ctx, 0, 0, x)
+        vin = to_dev(v, torch.float32)
+        out = torch.empty_like(vin)
+        M.molt_apply_D(ctx, 0, 0, M.OP_0, 2, 0.6 * n / L, vin, out)
+        got = out.double().cpu().numpy()
+    finally:
+        M.molt_destroy(ctx)
+    want = nonuniform.partial_sum(v, x, L, 0.6 * n / L, "0", 6, 2)
+    assert rel_l2(got, want) < 1e-5
