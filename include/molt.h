@@ -181,6 +181,15 @@ molt_status molt_set_source(molt_ctx* ctx, int problem, const void* coef, int de
  * MOLT_EUNSUPPORTED: a Dirichlet axis.  Synchronous. */
 molt_status molt_set_grid_axis(molt_ctx* ctx, int problem, int axis, const double* x, int64_t n);
 
+/* The point tables of a non-uniform periodic line (host only, no device
+ * work): for nodes x[n] of one period of length `period`, alpha and the rule,
+ * cR[6 n] and cL[6 n] (slot m of point i at m * n + i belongs to offset
+ * m - 3: J_R(x_i) = sum_m cR v_{i+m-3}, J_L(x_i) = sum_m cL v_{i-(m-3)};
+ * unused slots 0) and q[n] (q_i = e^{-alpha (x_i - x_{i-1})}), as the
+ * non-uniform sweeps use them.  MOLT_EINVAL on bad arguments. */
+molt_status molt_nonuniform_weights(const double* x, int64_t n, double period, double alpha, int quad_points,
+                                    double* cR, double* cL, double* q);
+
 /* Context options.
  *   MOLT_OPT_TMA      1 (default): sweeps whose lines are an exact fit and
  *                     whose arrays meet the tensor-copy alignment rules run

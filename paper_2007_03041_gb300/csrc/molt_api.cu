@@ -1737,6 +1737,22 @@ molt_status molt_set_source(molt_ctx* c, int problem, const void* coef, int degr
   return MOLT_OK;
 }
 
+molt_status molt_nonuniform_weights(const double* x, int64_t n, double period, double alpha, int quad_points,
+                                    double* cR, double* cL, double* q) {
+  if (!x || !cR || !cL || !q || n < 1 || !(period > 0) || !(alpha > 0) || !std::isfinite(alpha))
+    return MOLT_EINVAL;
+  if (quad_points != 3 && quad_points != 5 && quad_points != 6) return MOLT_EINVAL;
+  for (int64_t i = 1; i < n; ++i)
+    if (!(x[i] > x[i - 1])) return MOLT_EINVAL;
+  if (!(x[n - 1] - x[0] < period)) return MOLT_EINVAL;
+  std::vector<double> nodes(x, x + n), r, l, qq;
+  build_nonuniform_tables(nodes, period, alpha, quad_points, &r, &l, &qq);
+  std::copy(r.begin(), r.end(), cR);
+  std::copy(l.begin(), l.end(), cL);
+  std::copy(qq.begin(), qq.end(), q);
+  return MOLT_OK;
+}
+
 molt_status molt_set_grid_axis(molt_ctx* c, int problem, int axis, const double* x, int64_t n) {
   if (!c) return fail(nullptr, MOLT_EINVAL, "null context");
   if (problem < 0 || problem >= int(c->probs.size())) return fail(c, MOLT_EINVAL, "problem index out of range");

@@ -24,7 +24,8 @@ INT_DEFAULT, INT_EULER, INT_RK3 = 0, 1, 2
 EXPORTS = ("molt_create", "molt_apply_D", "molt_step", "molt_set_option", "molt_profile_read", "molt_destroy",
            "molt_last_error", "molt_wave_step_noalloc", "molt_batch_tile_shape", "molt_set_mlp", "molt_mlp_stats",
            "molt_weno_linear_weights", "molt_mlp_pack", "molt_mlp_forward", "molt_mlp_loss_grad", "molt_mlp_adam",
-           "molt_mlp_harvest", "molt_quadrature_weights", "molt_set_source", "molt_set_grid_axis")
+           "molt_mlp_harvest", "molt_quadrature_weights", "molt_set_source", "molt_set_grid_axis",
+           "molt_nonuniform_weights")
 MLP_PARAMS = 1347
 MLP_BLOB_BYTES = 3728
 OPT_TMA, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_TEST_SKIP_ARRIVE = 0, 1, 2, 3
@@ -93,6 +94,8 @@ def load_library(path=LIB_PATH):
         lib.molt_set_mlp.argtypes = [vp, vp, ctypes.c_size_t]
         lib.molt_set_source.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
         lib.molt_set_grid_axis.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl), i64]
+        lib.molt_nonuniform_weights.argtypes = [ctypes.POINTER(dbl), i64, dbl, dbl, ctypes.c_int,
+                                                ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
         lib.molt_mlp_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.c_int]
         lib.molt_weno_linear_weights.argtypes = [dbl, ctypes.POINTER(dbl)]
         lib.molt_quadrature_weights.argtypes = [ctypes.c_int, dbl, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
@@ -103,7 +106,7 @@ def load_library(path=LIB_PATH):
         lib.molt_mlp_adam.argtypes = [vp, vp, vp, vp, i64, dbl, dbl, dbl, dbl, vp, vp]
         lib.molt_mlp_harvest.argtypes = [vp, i64, i64, vp, i64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl), vp,
                                          vp, i64, vp]
-        for f in ("molt_set_mlp", "molt_set_source", "molt_set_grid_axis", "molt_mlp_stats",
+        for f in ("molt_set_mlp", "molt_set_source", "molt_set_grid_axis", "molt_nonuniform_weights", "molt_mlp_stats",
                   "molt_weno_linear_weights", "molt_quadrature_weights",
                   "molt_mlp_pack", "molt_mlp_forward",
                   "molt_mlp_loss_grad", "molt_mlp_adam", "molt_mlp_harvest"):
@@ -279,6 +282,21 @@ def molt_set_grid_axis(ctx, problem, axis, x):
         return
     arr = (ctypes.c_double * len(x))(*[float(v) for v in x])
     _check(lib, ctx, lib.molt_set_grid_axis(ctx, problem, axis, arr, len(x)))
+
+
+def molt_nonuniform_weights(x, period, alpha, quad_points):
+    """(cR (6, n), cL (6, n), q (n,)) point tables of a non-uniform periodic
+    line, computed on the host by the library (no device work)."""
+    import numpy as np
+    lib = load_library()
+    n = len(x)
+    xs = (ctypes.c_double * n)(*[float(v) for v in x])
+    cR, cL, q = (ctypes.c_double * (6 * n))(), (ctypes.c_double * (6 * n))(), (ctypes.c_double * n)()
+    st = lib.molt_nonuniform_weights(xs, n, float(period), float(alpha), int(quad_points), cR, cL, q)
+    if st != MOLT_OK:
+        raise MoltError(st, "molt_nonuniform_weights")
+    return (np.frombuffer(cR, dtype=np.float64).reshape(6, n).copy(),
+            np.frombuffer(cL, dtype=np.float64).reshape(6, n).copy(), np.frombuffer(q, dtype=np.float64).copy())
 
 
 def molt_mlp_stats(ctx, reset=False):

@@ -47,3 +47,23 @@ def test_library_rejects_bad_rules(M):
         M.molt_quadrature_weights(6, 0.0)
     with pytest.raises(M.MoltError):
         M.molt_quadrature_weights(6, float("nan"))
+
+
+@pytest.mark.parametrize("npts", [3, 5, 6])
+@pytest.mark.parametrize("alpha", [0.5, 6.0, 80.0])
+def test_library_nonuniform_tables_match_oracle(M, npts, alpha):
+    """The library's point tables of a non-uniform periodic line (16-point
+    Gauss-Legendre in C++) against the oracle's (48-point, numpy)."""
+    from oracle import nonuniform
+    from oracle.quadrature import STENCIL
+    n, L = 37, 2 * np.pi
+    xi = L * np.arange(n) / n
+    x = 0.25 + xi + 0.35 * np.sin(xi)
+    cR, cL, q = M.molt_nonuniform_weights(x, L, alpha, npts)
+    wR, wL, wq = nonuniform.weights(x, L, alpha, npts)
+    for m, o in enumerate(STENCIL[npts]):
+        np.testing.assert_allclose(cR[o + 3], wR[:, m], rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(cL[o + 3], wL[:, m], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(q, wq, rtol=1e-14)
+    unused = [k for k in range(6) if k - 3 not in STENCIL[npts]]
+    assert np.all(cR[unused] == 0) and np.all(cL[unused] == 0)
