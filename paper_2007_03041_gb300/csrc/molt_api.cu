@@ -50,6 +50,7 @@ struct Problem {
     int npts = 0;
     void* dev = nullptr;         // cR[6n], cL[6n], q[n] of the compute type
   } nu[3];
+  void* nu_tmp[2] = {nullptr, nullptr};   // transposed copies for strided non-uniform 2-D sweeps
   int64_t hj_steps = 0;     // HJ steps taken (rotates the speed slots)
   bool hj_lag_ready = false;
 };
@@ -474,6 +475,8 @@ bool hj_transposed_y(molt_ctx* c, const Problem& p);
 namespace {
 molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int P, double alpha,
                                const void* in, void* out);
+molt_status transpose(molt_ctx* c, const Problem& p, const void* in, void* out, long long ny, long long nx);
+Problem transposed(const Problem& p);
 }  // namespace
 
 extern "C" {
@@ -780,13 +783,31 @@ molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int 
     cch.alpha = alpha;
     cch.npts = p.d.quad_points;
   }
+  // y lines of a 2-D grid run on the transposed array, where they are rows
+  // (the sweep reads and writes each strided line with one sector per point)
+  const bool trans = p.d.ndim == 2 && axis == 1;
+  const long long nx = p.n[0], ny = p.n[1];
+  const void* kin = in;
+  void* kout = out;
+  if (trans) {
+    for (void*& t : p.nu_tmp)
+      if (!t && cudaMalloc(&t, state_bytes(p.d) * size_t(p.total)) != cudaSuccess) {
+        cudaGetLastError();
+        t = nullptr;
+        return fail(c, MOLT_ENOMEM, "non-uniform transposed copies");
+      }
+    molt_status st = transpose(c, p, in, p.nu_tmp[0], ny, nx);
+    if (st != MOLT_OK) return st;
+    kin = p.nu_tmp[0];
+    kout = p.nu_tmp[1];
+  }
   NuArgs a{};
-  a.g = geom(p, axis);
+  a.g = trans ? geom(transposed(p), 0) : geom(p, axis);
   a.mode = mode;
   a.P = P;
   a.inv1mmu = 1.0 / (-std::expm1(-alpha * L));
-  a.in = in;
-  a.out = out;
+  a.in = kin;
+  a.out = kout;
   a.status = c->status_dev;
   // one CTA per line, its scan positions split between up to 16 warps (at
   // most 512 each: the kernel keeps a segment's local integrals in registers)
@@ -817,7 +838,8 @@ molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int 
   }
   record_end(c, &rec);
   e = cudaGetLastError();
-  return e == cudaSuccess ? MOLT_OK : cuda_fail(c, e, "non-uniform sweep");
+  if (e != cudaSuccess) return cuda_fail(c, e, "non-uniform sweep");
+  return trans ? transpose(c, p, p.nu_tmp[1], out, nx, ny) : MOLT_OK;
 }
 
 
@@ -1851,6 +1873,7 @@ molt_status molt_destroy(molt_ctx* c) {
     cudaFree(p.gp);
     cudaFree(p.gm);
     for (auto& cch : p.nu) cudaFree(cch.dev);
+    for (void* t : p.nu_tmp) cudaFree(t);
     for (void* v : p.hv) cudaFree(v);
     cudaFree(p.tu);
     cudaFree(p.thx);
