@@ -71,3 +71,17 @@ def test_paper_configs_build_the_sec51_problems():
     assert (d3[0].hamiltonian, d3[0].h0) == (M.H_AFFINE_SQ, 1.0)
     assert u1[0].shape == (5277, 5277) and float(abs(u3[0]).max()) == 0.0
     assert abs(float(u2[0][5277 // 4, 0]) - 1.0) < 1e-3      # sin(x) + sin(y) at y ~ pi/2, x = 0 ([y][x])
+
+
+def test_advdiff_bench_workload():
+    """The viscous Burgers workload: 4096^2 FP32, WENO-Z, forward Euler, and a
+    splitting bound c above max |u| of the initial state."""
+    import math
+    import bench
+    from paper_2007_03041_gb300 import molt as M
+    d, u = bench._problem("advdiff_burgers4096")
+    d = d[0]
+    assert (d.pde, d.flux, d.weights, d.quad_points, d.integrator, d.prec) == \
+        (M.PDE_ADVDIFF, M.FLUX_BURGERS, M.W_WENOZ, 5, M.INT_EULER, M.PREC_F32)
+    assert d.c > float(abs(u[0]).max())
+    assert abs(d.dt - 0.5 * (2 * math.pi / 4096) / d.c) < 1e-18
