@@ -23,11 +23,23 @@ computed for it.  This module writes that case out from the definitions:
 
 The integrals are evaluated by Gauss-Legendre quadrature of the Lagrange
 basis times the exponential (48 points per cell).
+
+WENO-Z on non-uniform lines (Sec. 2.4: the linear weights become local to
+each point): per point i and direction, the substencil rules c^{(r)} on the
+substencils S_r of the J_R stencil (mirrored for J_L), the linear weights d_r
+with sum_r d_r c^{(r)} = c (the large-stencil rule at that point), and the
+smoothness indicators of the commented WENO step,
+
+    beta_r = sum_l dx_i^{2l-1} int_cell (d^l p_r / ds^l)^2 ds,
+
+with dx_i the width of the integration cell (x_i - x_{i-1} for J_R,
+x_{i+1} - x_i for J_L) -- on a uniform grid this is the uniform indicator.
+The WENO-Z map (eps = 1e-6) then weights the J^{(r)} as on uniform grids.
 """
 import numpy as np
 from numpy.polynomial import polynomial as npoly
 
-from .quadrature import STENCIL, lagrange_basis
+from .quadrature import STENCIL, SUBSTENCILS, WENOZ_EPS, lagrange_basis, smoothness_orders
 
 _GL_X, _GL_W = np.polynomial.legendre.leggauss(48)
 
@@ -36,6 +48,25 @@ def _node(x, L, j):
     n = len(x)
     k, r = divmod(j, n)
     return x[r] + k * L
+
+
+def _cell(x, L, i, side):
+    """(a, b, sign): the integration cell of J_R (side R: [x_{i-1}, x_i],
+    nodes x_{i+l}) or J_L (side L: [x_i, x_{i+1}], nodes x_{i-l})."""
+    if side == "R":
+        return _node(x, L, i - 1), x[i], 1
+    return x[i], _node(x, L, i + 1), -1
+
+
+def _cell_rule(x, L, alpha, i, side, offs):
+    """alpha int_cell e^{-alpha |s - x_i|} ell_m(s) ds for the Lagrange basis
+    on the nodes of ``offs`` (Eqs. "JR", "JL" with p the interpolant)."""
+    a, b, sign = _cell(x, L, i, side)
+    xi = x[i]
+    s = 0.5 * (b - a) * _GL_X + 0.5 * (b + a)
+    w = 0.5 * (b - a) * _GL_W * alpha * np.exp(-alpha * np.abs(s - xi))
+    nodes = [_node(x, L, i + sign * l) - xi for l in offs]
+    return np.array([np.sum(w * npoly.polyval(s - xi, lagrange_basis(nodes, m))) for m in range(len(offs))])
 
 
 def weights(x, L, alpha, npts):
@@ -47,30 +78,103 @@ def weights(x, L, alpha, npts):
     cL = np.zeros((n, len(offs)))
     q = np.zeros(n)
     for i in range(n):
-        xi = x[i]
-        a, b = _node(x, L, i - 1), xi
-        q[i] = np.exp(-alpha * (b - a))
-        s = 0.5 * (b - a) * _GL_X + 0.5 * (b + a)
-        w = 0.5 * (b - a) * _GL_W * alpha * np.exp(-alpha * (xi - s))
-        nodes = [_node(x, L, i + l) - xi for l in offs]
-        for m in range(len(offs)):
-            cR[i, m] = np.sum(w * npoly.polyval(s - xi, lagrange_basis(nodes, m)))
-        a, b = xi, _node(x, L, i + 1)
-        s = 0.5 * (b - a) * _GL_X + 0.5 * (b + a)
-        w = 0.5 * (b - a) * _GL_W * alpha * np.exp(-alpha * (s - xi))
-        nodes = [_node(x, L, i - l) - xi for l in offs]
-        for m in range(len(offs)):
-            cL[i, m] = np.sum(w * npoly.polyval(s - xi, lagrange_basis(nodes, m)))
+        q[i] = np.exp(-alpha * (x[i] - _node(x, L, i - 1)))
+        cR[i] = _cell_rule(x, L, alpha, i, "R", offs)
+        cL[i] = _cell_rule(x, L, alpha, i, "L", offs)
     return cR, cL, q
 
 
-def inverse(v, x, L, alpha, op, npts, tables=None):
+def _smoothness_matrix(x, L, i, side, offs, orders):
+    """M with beta = v^T M v: sum_l dx^{2l-1} int_cell ell_a^{(l)} ell_b^{(l)} ds
+    over the cell of x_i on the given side, in physical coordinates."""
+    a, b, sign = _cell(x, L, i, side)
+    xi = x[i]
+    dx = b - a
+    s = 0.5 * (b - a) * _GL_X + 0.5 * (b + a) - xi
+    w = 0.5 * (b - a) * _GL_W
+    nodes = [_node(x, L, i + sign * l) - xi for l in offs]
+    m = len(offs)
+    M = np.zeros((m, m))
+    for l in orders:
+        ders = [npoly.polyval(s, npoly.polyder(lagrange_basis(nodes, j), l)) for j in range(m)]
+        for p in range(m):
+            for r in range(m):
+                M[p, r] += dx ** (2 * l - 1) * np.sum(w * ders[p] * ders[r])
+    return M
+
+
+def weno_tables(x, L, alpha, npts):
+    """Per side ('R', 'L') a dict of the point-local WENO constants:
+    sub (n, 3, m) substencil rules, d (n, 3) linear weights, M (n, 3, m, m)
+    smoothness matrices (npts 5: quadratic substencils; 6: cubic)."""
+    n = len(x)
+    subs = SUBSTENCILS[npts]
+    offs = STENCIL[npts]
+    m = len(subs[0])
+    orders = smoothness_orders(npts)
+    out = {}
+    for side in "RL":
+        sub = np.zeros((n, 3, m))
+        d = np.zeros((n, 3))
+        Ms = np.zeros((n, 3, m, m))
+        for i in range(n):
+            big = _cell_rule(x, L, alpha, i, side, offs)
+            A = np.zeros((len(offs), 3))
+            for r, so in enumerate(subs):
+                sub[i, r] = _cell_rule(x, L, alpha, i, side, so)
+                A[r:r + m, r] = sub[i, r]
+                Ms[i, r] = _smoothness_matrix(x, L, i, side, so, orders)
+            # sum_r d_r c^{(r)} = c on every node of the large stencil
+            # (consistent: the system is exact on data of the substencil degree)
+            d[i], *_ = np.linalg.lstsq(A, big, rcond=None)
+            resid = np.abs(A @ d[i] - big).max()
+            assert resid < 1e-12 * max(1.0, np.abs(big).max()), resid
+        out[side] = {"sub": sub, "d": d, "M": Ms}
+    return out
+
+
+def weno_weights_at(vals, d, Ms):
+    """WENO-Z nonlinear weights (commented WENO-Z step of Sec. 2.4) of one
+    point from its stencil values ``vals`` (large-stencil order)."""
+    m = Ms.shape[-1]
+    beta = np.array([vals[r:r + m] @ Ms[r] @ vals[r:r + m] for r in range(3)])
+    tau = abs(beta[0] - beta[2])
+    wt = d * (1.0 + tau / (WENOZ_EPS + beta))
+    return wt / wt.sum()
+
+
+def local_integrals(v, x, L, alpha, npts, weights_kind="linear", tables=None):
+    """(J_R, J_L) at every point: the large-stencil rule (linear) or the
+    WENO-Z combination of the substencil rules (wenoz)."""
+    n = len(x)
+    offs = STENCIL[npts]
+    if weights_kind == "linear":
+        cR, cL, _ = tables if tables is not None else weights(x, L, alpha, npts)
+        JR = np.array([sum(cR[i, m] * v[(i + l) % n] for m, l in enumerate(offs)) for i in range(n)])
+        JL = np.array([sum(cL[i, m] * v[(i - l) % n] for m, l in enumerate(offs)) for i in range(n)])
+        return JR, JL
+    if weights_kind != "wenoz":
+        raise ValueError(weights_kind)
+    wt = tables if tables is not None else weno_tables(x, L, alpha, npts)
+    m = wt["R"]["sub"].shape[-1]
+    J = {}
+    for side, sign in (("R", 1), ("L", -1)):
+        t = wt[side]
+        out = np.zeros(n)
+        for i in range(n):
+            vals = np.array([v[(i + sign * l) % n] for l in offs])
+            om = weno_weights_at(vals, t["d"][i], t["M"][i])
+            out[i] = sum(om[r] * (t["sub"][i, r] @ vals[r:r + m]) for r in range(3))
+        J[side] = out
+    return J["R"], J["L"]
+
+
+def inverse(v, x, L, alpha, op, npts, tables=None, weights_kind="linear", weno=None):
     """L_op^{-1}[v] on one periodic non-uniform line (op in R, L, 0)."""
     n = len(x)
     cR, cL, q = tables if tables is not None else weights(x, L, alpha, npts)
-    offs = STENCIL[npts]
-    JR = np.array([sum(cR[i, m] * v[(i + l) % n] for m, l in enumerate(offs)) for i in range(n)])
-    JL = np.array([sum(cL[i, m] * v[(i - l) % n] for m, l in enumerate(offs)) for i in range(n)])
+    JR, JL = local_integrals(v, x, L, alpha, npts, weights_kind,
+                             (cR, cL, q) if weights_kind == "linear" else weno)
     mu = np.prod(q)
     IR = np.zeros(n)
     acc = 0.0
@@ -99,12 +203,13 @@ def inverse(v, x, L, alpha, op, npts, tables=None):
     return 0.5 * (IL + IR)
 
 
-def partial_sum(v, x, L, alpha, op, npts, P):
+def partial_sum(v, x, L, alpha, op, npts, P, weights_kind="linear"):
     """S_P = sum_{p<=P} D^p[v] on one periodic non-uniform line."""
     tables = weights(x, L, alpha, npts)
+    weno = weno_tables(x, L, alpha, npts) if weights_kind == "wenoz" else None
     S = np.zeros(len(x))
     w = np.asarray(v, dtype=np.float64)
     for _ in range(P):
-        w = w - inverse(w, x, L, alpha, op, npts, tables)
+        w = w - inverse(w, x, L, alpha, op, npts, tables, weights_kind, weno)
         S = S + w
     return S

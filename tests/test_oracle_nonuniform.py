@@ -82,3 +82,154 @@ def test_converges_to_the_continuous_operator_on_stretched_grids():
         errs.append(np.abs(got - alpha ** 2 / (alpha ** 2 + k ** 2) * np.sin(k * x)).max())
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert all(r > 5.0 for r in rates), (errs, rates)
+
+
+# ---------------------------------------------------------------- WENO-Z
+# Point-local linear weights and smoothness indicators (Sec. 2.4: on a
+# non-uniform mesh the linear weights are local to each point).
+
+def _jagged(n, L=2 * np.pi, seed=5, spread=0.6):
+    """Nodes with independent random cell widths (no smooth mapping)."""
+    w = 1.0 + spread * np.random.default_rng(seed).uniform(-1, 1, n)
+    x = np.concatenate([[0.0], np.cumsum(w)[:-1]])
+    return x * (L / w.sum())
+
+
+@pytest.mark.parametrize("npts", [5, 6])
+def test_weno_tables_on_a_uniform_grid_are_the_uniform_constants(npts):
+    """d_r and the smoothness matrices of every point reduce to the uniform
+    ones (those are pinned to the closed forms of App. C)."""
+    from oracle import quadrature
+    n, L, alpha = 24, 3.0, 5.0
+    x = L * np.arange(n) / n
+    t = nonuniform.weno_tables(x, L, alpha, npts)
+    rule = quadrature.QuadratureRule(alpha * L / n, npts)
+    for side in "RL":
+        np.testing.assert_allclose(t[side]["d"], np.broadcast_to(rule.d, (n, 3)), rtol=0, atol=1e-12)
+        for r in range(3):
+            np.testing.assert_allclose(t[side]["sub"][:, r], np.broadcast_to(rule.sub_c[r], (n, len(rule.sub_c[r]))),
+                                       rtol=0, atol=1e-14)
+            np.testing.assert_allclose(t[side]["M"][:, r], np.broadcast_to(rule.beta_M[r], t[side]["M"][:, r].shape),
+                                       rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("op", ["R", "L", "0"])
+def test_weno_on_a_uniform_grid_reproduces_the_uniform_oracle(op):
+    n, L, alpha = 40, 2.0, 7.0
+    x = L * np.arange(n) / n
+    xs = x * 2 * np.pi / L
+    v = np.sign(np.sin(xs)) + 0.2 * np.cos(3 * xs)       # jumps: the nonlinear weights matter
+    got = nonuniform.partial_sum(v, x, L, alpha, op, 5, 2, weights_kind="wenoz")
+    want = sweep.partial_sum(v[None, :], 1, alpha, L / n, op, "periodic", 5, 2, weights="wenoz")[0]
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("npts", [5, 6])
+def test_weno_linear_weights_are_partitions_of_unity_and_substencils_sum_to_one_minus_q(npts):
+    n, L, alpha = 20, 2 * np.pi, 2.5
+    x = _jagged(n)
+    t = nonuniform.weno_tables(x, L, alpha, npts)
+    _, _, q = nonuniform.weights(x, L, alpha, npts)
+    for side, qs in (("R", q), ("L", np.roll(q, -1))):
+        np.testing.assert_allclose(t[side]["d"].sum(axis=1), 1.0, rtol=0, atol=1e-13)
+        for r in range(3):
+            np.testing.assert_allclose(t[side]["sub"][:, r].sum(axis=1), 1 - qs, rtol=1e-13)
+    for op in "RL0":
+        S = nonuniform.partial_sum(np.full(n, -1.3), x, L, alpha, op, npts, 2, weights_kind="wenoz")
+        assert np.abs(S).max() < 1e-13
+
+
+@pytest.mark.parametrize("npts", [5, 6])
+def test_weno_reproduces_the_exact_integral_of_substencil_degree_data(npts):
+    """On data of the substencils' degree every p_r is the data itself, so
+    beta_0 = beta_1 = beta_2, tau = 0, omega = d, and J is the exact kernel
+    integral of the polynomial (adaptive quadrature here)."""
+    from scipy.integrate import quad
+    n, L, alpha = 24, 2 * np.pi, 1.7
+    x = _jagged(n, seed=8)
+    deg = 2 if npts == 5 else 3
+    coef = [0.3, -1.1, 0.45, 0.2][:deg + 1]
+    poly = lambda s: npoly.polyval(s, coef)
+    v = poly(x)
+    t = nonuniform.weno_tables(x, L, alpha, npts)
+    JR, JL = nonuniform.local_integrals(v, x, L, alpha, npts, "wenoz", t)
+    offs = STENCIL[npts]
+    for i in range(-min(offs), n - max(offs)):           # stencils that do not wrap
+        vals = np.array([v[i + l] for l in offs])
+        om = nonuniform.weno_weights_at(vals, t["R"]["d"][i], t["R"]["M"][i])
+        np.testing.assert_allclose(om, t["R"]["d"][i], rtol=0, atol=1e-9)
+        want = quad(lambda s: alpha * math.exp(-alpha * (x[i] - s)) * poly(s), x[i - 1], x[i], epsabs=1e-15)[0]
+        assert abs(JR[i] - want) < 1e-13
+    for i in range(max(offs), n + min(offs)):            # J_L reads v_{i-l}
+        want = quad(lambda s: alpha * math.exp(-alpha * (s - x[i])) * poly(s), x[i], x[i + 1], epsabs=1e-15)[0]
+        assert abs(JL[i] - want) < 1e-13
+
+
+def test_weno_smoothness_indicator_of_a_quadratic_has_its_closed_form():
+    """p(s) = s^2 on the cell [a, b] of width dx: p' = 2s, p'' = 2, so
+    beta = dx int_a^b 4 s^2 ds + dx^3 int_a^b 4 ds = 4 dx (b^3 - a^3)/3 + 4 dx^4."""
+    n, L, alpha = 16, 2 * np.pi, 3.0
+    x = _jagged(n, seed=11)
+    t = nonuniform.weno_tables(x, L, alpha, 5)
+    v = x ** 2
+    for i in range(3, n - 3):
+        for side, sign, (a, b) in (("R", 1, (x[i - 1], x[i])), ("L", -1, (x[i], x[i + 1]))):
+            vals = np.array([v[i + sign * l] for l in STENCIL[5]])
+            dx = b - a
+            want = 4 * dx * (b ** 3 - a ** 3) / 3 + 4 * dx ** 4
+            for r in range(3):
+                got = vals[r:r + 3] @ t[side]["M"][i, r] @ vals[r:r + 3]
+                assert abs(got - want) < 1e-12 * max(1.0, want)
+
+
+def test_weno_is_invariant_under_scaling_and_mirroring():
+    """x -> lam x with alpha -> alpha/lam leaves every nu and beta unchanged;
+    mirroring the line (x -> L - x, order reversed) swaps J_R and J_L."""
+    n, L, alpha = 18, 2 * np.pi, 2.2
+    x = _jagged(n, seed=13)
+    v = np.where(x < 2.0, 1.0, -0.5) + 0.1 * np.sin(x)
+    JR, JL = nonuniform.local_integrals(v, x, L, alpha, 5, "wenoz")
+    lam = 3.7
+    JR2, JL2 = nonuniform.local_integrals(v, lam * x, lam * L, alpha / lam, 5, "wenoz")
+    np.testing.assert_allclose(JR2, JR, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(JL2, JL, rtol=0, atol=1e-12)
+    # mirrored nodes y_j = L - x_{n-1-j} (shifted to start at 0), data reversed
+    y = L - x[::-1]
+    y = y - y[0]
+    JRm, JLm = nonuniform.local_integrals(v[::-1].copy(), y, L, alpha, 5, "wenoz")
+    np.testing.assert_allclose(JRm[::-1], JL, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(JLm[::-1], JR, rtol=0, atol=1e-12)
+
+
+def test_weno_drops_the_substencil_across_a_jump():
+    """A jump between x_{i-3} and x_{i-2} lies only in S_0 of J_R(x_i): the
+    constant substencils have beta = 0, so omega_0 = O(eps) and J_R is the
+    constant's integral (1 - q_i) c to that accuracy."""
+    n, L, alpha = 30, 2 * np.pi, 2.0
+    x = _jagged(n, seed=17)
+    c = 0.8
+    i = 12
+    v = np.full(n, c)
+    v[:i - 2] = -1.0
+    v[i + 3:] = c                                        # the stencil of i sees one jump
+    t = nonuniform.weno_tables(x, L, alpha, 5)
+    vals = np.array([v[i + l] for l in STENCIL[5]])
+    om = nonuniform.weno_weights_at(vals, t["R"]["d"][i], t["R"]["M"][i])
+    assert om[0] < 1e-5, om
+    JR, _ = nonuniform.local_integrals(v, x, L, alpha, 5, "wenoz", t)
+    _, _, q = nonuniform.weights(x, L, alpha, 5)
+    assert abs(JR[i] - (1 - q[i]) * c) < 1e-5
+
+
+def test_weno_converges_on_stretched_grids():
+    """Smooth data: omega -> d, and L_0^{-1}[sin kx] reaches the continuous
+    alpha^2/(alpha^2 + k^2) sin kx at high order on a smoothly stretched grid."""
+    L, alpha, k = 2 * np.pi, 4.0, 3
+    errs = []
+    for n in (64, 128, 256):
+        x = _stretched(n)
+        got = nonuniform.inverse(np.sin(k * x), x, L, alpha, "0", 5, weights_kind="wenoz",
+                                 weno=nonuniform.weno_tables(x, L, alpha, 5))
+        errs.append(np.abs(got - alpha ** 2 / (alpha ** 2 + k ** 2) * np.sin(k * x)).max())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(r > 3.5 for r in rates), (errs, rates)
