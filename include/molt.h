@@ -174,8 +174,11 @@ molt_status molt_set_source(molt_ctx* ctx, int problem, const void* coef, int de
  * molt_apply_D along that axis then uses point-local quadrature weights
  * (each point's stencil nodes integrated against the exponential kernel,
  * the non-uniform case of Sec. 2.4) and cell decays e^{-alpha (x_i - x_{i-1})},
- * closed over the period with mu = e^{-alpha (hi - lo)} (Sec. 2.3); linear
- * weights only (MOLT_EUNSUPPORTED otherwise).  x == NULL makes the axis
+ * closed over the period with mu = e^{-alpha (hi - lo)} (Sec. 2.3).  With
+ * MOLT_W_WENOZ (5-point rule) the local integrals are the WENO-Z combination
+ * of the substencil rules, with point-local linear weights and smoothness
+ * indicators (see molt_nonuniform_weno_weights); MOLT_W_LEARNED is
+ * MOLT_EUNSUPPORTED on non-uniform axes.  x == NULL makes the axis
  * uniform again.  molt_step on a problem with a non-uniform axis returns
  * MOLT_EUNSUPPORTED.  MOLT_EINVAL: bad index, count or nodes;
  * MOLT_EUNSUPPORTED: a Dirichlet axis.  Synchronous. */
@@ -189,6 +192,26 @@ molt_status molt_set_grid_axis(molt_ctx* ctx, int problem, int axis, const doubl
  * non-uniform sweeps use them.  MOLT_EINVAL on bad arguments. */
 molt_status molt_nonuniform_weights(const double* x, int64_t n, double period, double alpha, int quad_points,
                                     double* cR, double* cL, double* q);
+
+/* The WENO-Z point tables of a non-uniform periodic line for the 5-point rule
+ * (host only, no device work; Sec. 2.4: on a non-uniform mesh the linear
+ * weights d_r are local to each point).  wR[30 n] (J_R) and wL[30 n] (J_L),
+ * slot s of point i at s * n + i, with substencil r = 0..2 on the offsets
+ * {r-3, r-2, r-1} (nodes x_{i+o} for J_R, x_{i-o} for J_L):
+ *   slots 3r+j     c^{(r)}_j, the rule of substencil r:
+ *                  J^{(r)} = sum_j c^{(r)}_j v(node j);
+ *   slots 9+r      d_r, with sum_r d_r c^{(r)} the 5-point rule of the point;
+ *   slots 12+3r+j  A_{rj}, slots 21+3r+j B_{rj}: with a = sum_j A_{rj} v,
+ *                  b = sum_j B_{rj} v the substencil interpolant has
+ *                  dp/dt = a + b t in the cell variable t in [-1, 0]
+ *                  (t = (s - x_i)/dx_i on [x_{i-1}, x_i] for J_R,
+ *                  t = (x_i - s)/dx_i on [x_i, x_{i+1}] for J_L), so its
+ *                  smoothness indicator, the sum over l = 1, 2 of
+ *                  dx_i^{2l-1} int_cell (d^l p/ds^l)^2 ds, is a^2 - a b + 4/3 b^2.
+ * WENO-Z: w~_r = d_r (1 + tau/(1e-6 + beta_r)), tau = |beta_0 - beta_2|,
+ * J = sum_r w~_r J^{(r)} / sum_r w~_r.  MOLT_EINVAL on bad arguments. */
+molt_status molt_nonuniform_weno_weights(const double* x, int64_t n, double period, double alpha, double* wR,
+                                         double* wL);
 
 /* Context options.
  *   MOLT_OPT_TMA      1 (default): sweeps whose lines are an exact fit and

@@ -203,10 +203,13 @@ def inverse(v, x, L, alpha, op, npts, tables=None, weights_kind="linear", weno=N
     return 0.5 * (IL + IR)
 
 
-def partial_sum(v, x, L, alpha, op, npts, P, weights_kind="linear"):
-    """S_P = sum_{p<=P} D^p[v] on one periodic non-uniform line."""
-    tables = weights(x, L, alpha, npts)
-    weno = weno_tables(x, L, alpha, npts) if weights_kind == "wenoz" else None
+def partial_sum(v, x, L, alpha, op, npts, P, weights_kind="linear", tables=None, weno=None):
+    """S_P = sum_{p<=P} D^p[v] on one periodic non-uniform line (``tables``,
+    ``weno``: the line's weights() / weno_tables(), built when not given)."""
+    if tables is None:
+        tables = weights(x, L, alpha, npts)
+    if weights_kind == "wenoz" and weno is None:
+        weno = weno_tables(x, L, alpha, npts)
     S = np.zeros(len(x))
     w = np.asarray(v, dtype=np.float64)
     for _ in range(P):

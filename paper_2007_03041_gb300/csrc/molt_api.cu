@@ -48,7 +48,9 @@ struct Problem {
   struct NuCache {
     double alpha = 0.0;
     int npts = 0;
-    void* dev = nullptr;         // cR[6n], cL[6n], q[n] of the compute type
+    int weights = -1;
+    void* dev = nullptr;         // cR[K n], cL[K n], q[n] of the compute type (K = 6, WENO-Z 30)
+    size_t count = 0;            // values allocated
   } nu[3];
   void* nu_tmp[2] = {nullptr, nullptr};   // transposed copies for strided non-uniform 2-D sweeps
   int64_t hj_steps = 0;     // HJ steps taken (rotates the speed slots)
@@ -753,26 +755,40 @@ void record_end(molt_ctx* c, molt_ctx::Rec* rec) {
 // sum_{p<=P} D^p along a non-uniform periodic axis (point-local weights).
 molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int P, double alpha, const void* in,
                                void* out) {
-  if (p.d.weights != MOLT_W_LINEAR) return fail(c, MOLT_EUNSUPPORTED, "non-uniform axes run linear weights");
+  if (p.d.weights == MOLT_W_LEARNED) return fail(c, MOLT_EUNSUPPORTED, "non-uniform axes run linear or WENO-Z weights");
   if (!(alpha > 0) || !std::isfinite(alpha)) return fail(c, MOLT_EINVAL, "alpha must be positive and finite");
   const std::vector<double>& x = p.nodes[axis];
   const int n = int(x.size());
   const double L = p.d.hi[axis] - p.d.lo[axis];
   const bool f64 = is_f64_sweep(p.d);
+  const bool weno = p.d.weights == MOLT_W_WENOZ;
+  const size_t slots = weno ? size_t(kNuWeno) : 6;
   const size_t tb = f64 ? 8 : 4;
   Problem::NuCache& cch = p.nu[axis];
   cudaError_t e;
-  if (!cch.dev || cch.alpha != alpha || cch.npts != p.d.quad_points) {
+  if (!cch.dev || cch.alpha != alpha || cch.npts != p.d.quad_points || cch.weights != int(p.d.weights)) {
     std::vector<double> cR, cL, q;
     build_nonuniform_tables(x, L, alpha, p.d.quad_points, &cR, &cL, &q);
+    if (weno) build_nonuniform_weno_tables(x, L, alpha, &cR, &cL);
     std::vector<double> all(cR);
     all.insert(all.end(), cL.begin(), cL.end());
     all.insert(all.end(), q.begin(), q.end());
-    if (!cch.dev && (e = cudaMalloc(&cch.dev, all.size() * tb)) != cudaSuccess) {
-      cch.dev = nullptr;
-      return fail(c, MOLT_ENOMEM, "non-uniform tables");
-    }
+    if (all.size() != (2 * slots + 1) * size_t(n)) return fail(c, MOLT_EINVAL, "non-uniform table size");
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "table sync");
+    if (cch.dev && cch.count < all.size()) {
+      cudaFree(cch.dev);
+      cch.dev = nullptr;
+    }
+    if (!cch.dev) {
+      if ((e = cudaMalloc(&cch.dev, all.size() * tb)) != cudaSuccess) {
+        cudaGetLastError();
+        cch.dev = nullptr;
+        cch.count = 0;
+        return fail(c, MOLT_ENOMEM, "non-uniform tables");
+      }
+      cch.count = all.size();
+    }
+    cch.weights = -1;            // invalid until the upload completes
     if (f64) {
       e = cudaMemcpy(cch.dev, all.data(), all.size() * 8, cudaMemcpyHostToDevice);
     } else {
@@ -782,6 +798,7 @@ molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int 
     if (e != cudaSuccess) return cuda_fail(c, e, "table upload");
     cch.alpha = alpha;
     cch.npts = p.d.quad_points;
+    cch.weights = int(p.d.weights);
   }
   // y lines of a 2-D grid run on the transposed array, where they are rows
   // (the sweep reads and writes each strided line with one sector per point)
@@ -820,20 +837,24 @@ molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int 
   const int warps = nw;
   molt_ctx::Rec rec;
   record_begin(c, &rec, MOLT_KERNEL_STORE);
+  auto launch = [&](auto kernel, auto tables) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    kernel<<<unsigned(blocks), 32 * warps, smem, c->stream>>>(a, tables);
+  };
   if (f64) {
-    NuTables<double> t{static_cast<const double*>(cch.dev), static_cast<const double*>(cch.dev) + 6 * size_t(n),
-                       static_cast<const double*>(cch.dev) + 12 * size_t(n)};
-    cudaFuncSetAttribute(nonuniform_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    nonuniform_kernel<double, double><<<unsigned(blocks), 32 * warps, smem, c->stream>>>(a, t);
+    const double* d = static_cast<const double*>(cch.dev);
+    NuTables<double> t{d, d + slots * n, d + 2 * slots * n};
+    if (weno) launch(nonuniform_kernel<double, double, true>, t);
+    else launch(nonuniform_kernel<double, double, false>, t);
   } else {
-    NuTables<float> t{static_cast<const float*>(cch.dev), static_cast<const float*>(cch.dev) + 6 * size_t(n),
-                      static_cast<const float*>(cch.dev) + 12 * size_t(n)};
+    const float* d = static_cast<const float*>(cch.dev);
+    NuTables<float> t{d, d + slots * n, d + 2 * slots * n};
     if (is_f32_state(p.d)) {
-      cudaFuncSetAttribute(nonuniform_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-      nonuniform_kernel<float, float><<<unsigned(blocks), 32 * warps, smem, c->stream>>>(a, t);
+      if (weno) launch(nonuniform_kernel<float, float, true>, t);
+      else launch(nonuniform_kernel<float, float, false>, t);
     } else {
-      cudaFuncSetAttribute(nonuniform_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-      nonuniform_kernel<float, double><<<unsigned(blocks), 32 * warps, smem, c->stream>>>(a, t);
+      if (weno) launch(nonuniform_kernel<float, double, true>, t);
+      else launch(nonuniform_kernel<float, double, false>, t);
     }
   }
   record_end(c, &rec);
@@ -1772,6 +1793,19 @@ molt_status molt_nonuniform_weights(const double* x, int64_t n, double period, d
   std::copy(r.begin(), r.end(), cR);
   std::copy(l.begin(), l.end(), cL);
   std::copy(qq.begin(), qq.end(), q);
+  return MOLT_OK;
+}
+
+molt_status molt_nonuniform_weno_weights(const double* x, int64_t n, double period, double alpha, double* wR,
+                                         double* wL) {
+  if (!x || !wR || !wL || n < 1 || !(period > 0) || !(alpha > 0) || !std::isfinite(alpha)) return MOLT_EINVAL;
+  for (int64_t i = 1; i < n; ++i)
+    if (!(x[i] > x[i - 1])) return MOLT_EINVAL;
+  if (!(x[n - 1] - x[0] < period)) return MOLT_EINVAL;
+  std::vector<double> nodes(x, x + n), r, l;
+  build_nonuniform_weno_tables(nodes, period, alpha, &r, &l);
+  std::copy(r.begin(), r.end(), wR);
+  std::copy(l.begin(), l.end(), wL);
   return MOLT_OK;
 }
 

@@ -22,12 +22,14 @@
 
 namespace molt {
 
-// Device tables of one (axis, alpha, rule): structure of arrays, slot m of
-// the weights belongs to offset m - 3 (offsets -3..2; unused slots are 0).
+// Device tables of one (axis, alpha, rule): structure of arrays.  Linear
+// weights: slot m belongs to offset m - 3 (offsets -3..2; unused slots are
+// 0).  WENO-Z: cR, cL hold the kNuWeno-slot tables of
+// build_nonuniform_weno_tables.
 template <typename T>
 struct NuTables {
-  const T* cR;   // [6][n]: J_R(x_i) = sum_m cR[m][i] v_{i + m - 3}
-  const T* cL;   // [6][n]: J_L(x_i) = sum_m cL[m][i] v_{i - (m - 3)}
+  const T* cR;   // [6][n]: J_R(x_i) = sum_m cR[m][i] v_{i + m - 3}   (WENO-Z: [30][n])
+  const T* cL;   // [6][n]: J_L(x_i) = sum_m cL[m][i] v_{i - (m - 3)} (WENO-Z: [30][n])
   const T* q;    // [n]: q_i = e^{-alpha (x_i - x_{i-1})}
 };
 
@@ -109,6 +111,115 @@ inline void build_nonuniform_tables(const std::vector<double>& x, double L, doub
   }
 }
 
+// WENO-Z tables of the 5-point rule (quadratic substencils S_r = offsets
+// {r-3, r-2, r-1}, Sec. 2.4), per point and direction, slot-major [kNuWeno][n]:
+//   slots 3r+j       c^{(r)}_j: J^{(r)} = sum_j c^{(r)}_j v(node j of S_r)
+//   slots 9+r        d_r, the linear weights with sum_r d_r c^{(r)} = c
+//   slots 12+3r+j    A_{rj} = l_j'(0), slots 21+3r+j  B_{rj} = l_j''
+// in the cell variable t in [-1, 0] (t = (s - x_i)/dx for J_R on
+// [x_{i-1}, x_i], t = (x_i - s)/dx for J_L on [x_i, x_{i+1}]), l_j the
+// Lagrange basis of S_r.  With a = sum A v and b = sum B v the interpolant has
+// p_t = a + b t, so its smoothness indicator int_{-1}^0 p_t^2 + p_tt^2 dt is
+// a^2 - a b + 4/3 b^2.  The node of slot j of S_r is x_{i + (r + j - 3)} for
+// J_R and x_{i - (r + j - 3)} for J_L.  Since every rule integrates the
+// constant exactly (weights summing to 1 - q), d_1 = 1 - d_0 - d_2 once the
+// two outer nodes, each in one substencil only, fix d_0 and d_2.
+constexpr int kNuWeno = 30;
+
+inline void build_nonuniform_weno_tables(const std::vector<double>& x, double L, double alpha,
+                                         std::vector<double>* wR, std::vector<double>* wL) {
+  const int n = int(x.size());
+  wR->assign(size_t(kNuWeno) * n, 0.0);
+  wL->assign(size_t(kNuWeno) * n, 0.0);
+  constexpr int kG = 16;
+  double gx[kG], gw[kG];
+  gauss_legendre(kG, gx, gw);
+  auto node = [&](long long j) {
+    long long r = j % n;
+    if (r < 0) r += n;
+    return x[size_t(r)] + double((j - r) / n) * L;
+  };
+  // nu int_{-1}^0 e^{nu t} l_m(t) dt for the Lagrange basis on nodes t[0..k)
+  auto rule = [&](const double* t, int k, int m, double nu) {
+    double sum = 0.0;
+    for (int g = 0; g < kG; ++g) {
+      const double tt = 0.5 * (gx[g] - 1.0);
+      double ell = 1.0;
+      for (int r = 0; r < k; ++r)
+        if (r != m) ell *= (tt - t[r]) / (t[m] - t[r]);
+      sum += 0.5 * gw[g] * nu * std::exp(nu * tt) * ell;
+    }
+    return sum;
+  };
+  for (int i = 0; i < n; ++i) {
+    const double xi = x[size_t(i)];
+    for (int side = 0; side < 2; ++side) {
+      const double dx = side == 0 ? xi - node(i - 1) : node(i + 1) - xi;
+      const double nu = alpha * dx;
+      double t5[5];
+      for (int k = 0; k < 5; ++k) {
+        const int off = k - 3;
+        t5[k] = side == 0 ? (node(i + off) - xi) / dx : (xi - node(i - off)) / dx;
+      }
+      std::vector<double>& w = side == 0 ? *wR : *wL;
+      auto at = [&](int slot) -> double& { return w[size_t(slot) * n + i]; };
+      for (int r = 0; r < 3; ++r) {
+        const double* t = t5 + r;
+        for (int j = 0; j < 3; ++j) {
+          const double ta = t[(j + 1) % 3], tb = t[(j + 2) % 3];
+          const double den = (t[j] - ta) * (t[j] - tb);
+          at(3 * r + j) = rule(t, 3, j, nu);
+          at(12 + 3 * r + j) = -(ta + tb) / den;
+          at(21 + 3 * r + j) = 2.0 / den;
+        }
+      }
+      const double d0 = rule(t5, 5, 0, nu) / at(0);
+      const double d2 = rule(t5, 5, 4, nu) / at(8);
+      at(9) = d0;
+      at(10) = 1.0 - d0 - d2;
+      at(11) = d2;
+    }
+  }
+}
+
+// WENO-Z local integral of point i from its point tables tw ([30][n], layout
+// of build_nonuniform_weno_tables): the five stencil values in the
+// orientation of the direction (J_L reads the mirrored nodes), per
+// substencil r its rule, a = p_t(0) and b = p_tt, beta_r = a^2 - a b +
+// 4/3 b^2, and the WENO-Z map w~_r = d_r (1 + tau/(eps + beta_r)),
+// tau = |beta_0 - beta_2|, eps = 1e-6 (Sec. 2.4).
+template <typename T, bool LEFT>
+__device__ __forceinline__ T nu_wenoz_integral(const T* tw, const T* v, int n, int i) {
+  T w[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) w[k] = LEFT ? v[3 + i - (k - 3)] : v[3 + i + (k - 3)];
+  T Jr[3], beta[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    T J = T(0), a = T(0), b = T(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const T val = w[r + j];
+      J = fma(tw[(3 * r + j) * n + i], val, J);
+      a = fma(tw[(12 + 3 * r + j) * n + i], val, a);
+      b = fma(tw[(21 + 3 * r + j) * n + i], val, b);
+    }
+    Jr[r] = J;
+    beta[r] = fma(a, a - b, T(4.0 / 3.0) * b * b);
+  }
+  const T tau = fabs(beta[0] - beta[2]);
+  const T eps = T(1e-6);
+  T num = T(0), sum = T(0);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const T d = tw[(9 + r) * n + i];
+    const T wt = fma(d * tau, weight_rcp(eps + beta[r]), d);
+    num = fma(wt, Jr[r], num);
+    sum += wt;
+  }
+  return num * weight_rcp(sum);
+}
+
 // One direction with the periodic closure, split over the `nw` warps of the
 // line (segment `seg` <= 512 scan positions each, R ascending, L
 // descending).  Each warp computes the local integrals J and decays q of its
@@ -118,7 +229,7 @@ inline void build_nonuniform_tables(const std::vector<double>& x, double L, doub
 // I = 0 closes the period (x = I_end / (1 - mu)); each warp then replays its
 // chunks from its closed start value and stores by OUT: 1 I in w, 2 D = v - I
 // in w, 3 D = v - (w + I)/2 in w (w holding I_R: the L pass of L_0).
-template <typename T, bool LEFT, int OUT>
+template <typename T, bool LEFT, int OUT, bool WENO>
 __device__ __forceinline__ void nu_direction(const NuTables<T>& tb, const T* v, T* w, int n, int nw, int part,
                                              int seg, T k1, T* maps, int lane) {
   constexpr int kPer = 4, kChunks = 4;          // seg <= kChunks * 32 * kPer
@@ -138,11 +249,15 @@ __device__ __forceinline__ void nu_direction(const NuTables<T>& tb, const T* v, 
       if (step < s1) {
         const int i = LEFT ? n - 1 - step : step;
         T J = T(0);
+        if constexpr (WENO) {
+          J = nu_wenoz_integral<T, LEFT>(LEFT ? tb.cL : tb.cR, v, n, i);
+        } else {
 #pragma unroll
-        for (int m = 0; m < 6; ++m) {
-          const int off = m - 3;
-          if (LEFT) J = fma(tb.cL[m * n + i], v[3 + i - off], J);
-          else J = fma(tb.cR[m * n + i], v[3 + i + off], J);
+          for (int m = 0; m < 6; ++m) {
+            const int off = m - 3;
+            if (LEFT) J = fma(tb.cL[m * n + i], v[3 + i - off], J);
+            else J = fma(tb.cR[m * n + i], v[3 + i + off], J);
+          }
         }
         qk[c][k] = LEFT ? tb.q[i + 1 < n ? i + 1 : 0] : tb.q[i];
         jk[c][k] = J;
@@ -206,8 +321,9 @@ __device__ __forceinline__ void nu_direction(const NuTables<T>& tb, const T* v, 
 
 // S_P along non-uniform periodic lines: one CTA of `nw` warps per line (the
 // scan positions split into nw segments of at most 512); shared memory: v
-// (n + 6) and w (n) of T plus the segment maps.
-template <typename T, typename TIO>
+// (n + 6) and w (n) of T plus the segment maps.  WENO: local integrals by
+// WENO-Z with the point-local tables, else the linear point weights.
+template <typename T, typename TIO, bool WENO>
 __global__ void __launch_bounds__(512, 1) nonuniform_kernel(const NuArgs a, const NuTables<T> tb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = a.g.n;
@@ -232,10 +348,10 @@ __global__ void __launch_bounds__(512, 1) nonuniform_kernel(const NuArgs a, cons
     }
     __syncthreads();
     // D into w: R alone, L alone, or I_R first and then the L pass of L_0
-    if (a.mode == MODE_R) nu_direction<T, false, 2>(tb, v, w, n, nw, part, seg, k1, maps, lane);
-    if (a.mode == MODE_0) nu_direction<T, false, 1>(tb, v, w, n, nw, part, seg, k1, maps, lane);
-    if (a.mode == MODE_L) nu_direction<T, true, 2>(tb, v, w, n, nw, part, seg, k1, maps, lane);
-    if (a.mode == MODE_0) nu_direction<T, true, 3>(tb, v, w, n, nw, part, seg, k1, maps, lane);
+    if (a.mode == MODE_R) nu_direction<T, false, 2, WENO>(tb, v, w, n, nw, part, seg, k1, maps, lane);
+    if (a.mode == MODE_0) nu_direction<T, false, 1, WENO>(tb, v, w, n, nw, part, seg, k1, maps, lane);
+    if (a.mode == MODE_L) nu_direction<T, true, 2, WENO>(tb, v, w, n, nw, part, seg, k1, maps, lane);
+    if (a.mode == MODE_0) nu_direction<T, true, 3, WENO>(tb, v, w, n, nw, part, seg, k1, maps, lane);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const T d = w[i];
       TIO* o = out + base + i * st;

@@ -25,7 +25,8 @@ EXPORTS = ("molt_create", "molt_apply_D", "molt_step", "molt_set_option", "molt_
            "molt_last_error", "molt_wave_step_noalloc", "molt_batch_tile_shape", "molt_set_mlp", "molt_mlp_stats",
            "molt_weno_linear_weights", "molt_mlp_pack", "molt_mlp_forward", "molt_mlp_loss_grad", "molt_mlp_adam",
            "molt_mlp_harvest", "molt_quadrature_weights", "molt_set_source", "molt_set_grid_axis",
-           "molt_nonuniform_weights")
+           "molt_nonuniform_weights", "molt_nonuniform_weno_weights")
+NU_WENO_SLOTS = 30
 MLP_PARAMS = 1347
 MLP_BLOB_BYTES = 3728
 OPT_TMA, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_TEST_SKIP_ARRIVE = 0, 1, 2, 3
@@ -96,6 +97,8 @@ def load_library(path=LIB_PATH):
         lib.molt_set_grid_axis.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl), i64]
         lib.molt_nonuniform_weights.argtypes = [ctypes.POINTER(dbl), i64, dbl, dbl, ctypes.c_int,
                                                 ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+        lib.molt_nonuniform_weno_weights.argtypes = [ctypes.POINTER(dbl), i64, dbl, dbl, ctypes.POINTER(dbl),
+                                                     ctypes.POINTER(dbl)]
         lib.molt_mlp_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.c_int]
         lib.molt_weno_linear_weights.argtypes = [dbl, ctypes.POINTER(dbl)]
         lib.molt_quadrature_weights.argtypes = [ctypes.c_int, dbl, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
@@ -107,7 +110,7 @@ def load_library(path=LIB_PATH):
         lib.molt_mlp_harvest.argtypes = [vp, i64, i64, vp, i64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl), vp,
                                          vp, i64, vp]
         for f in ("molt_set_mlp", "molt_set_source", "molt_set_grid_axis", "molt_nonuniform_weights", "molt_mlp_stats",
-                  "molt_weno_linear_weights", "molt_quadrature_weights",
+                  "molt_nonuniform_weno_weights", "molt_weno_linear_weights", "molt_quadrature_weights",
                   "molt_mlp_pack", "molt_mlp_forward",
                   "molt_mlp_loss_grad", "molt_mlp_adam", "molt_mlp_harvest"):
             getattr(lib, f).restype = ctypes.c_int
@@ -297,6 +300,21 @@ def molt_nonuniform_weights(x, period, alpha, quad_points):
         raise MoltError(st, "molt_nonuniform_weights")
     return (np.frombuffer(cR, dtype=np.float64).reshape(6, n).copy(),
             np.frombuffer(cL, dtype=np.float64).reshape(6, n).copy(), np.frombuffer(q, dtype=np.float64).copy())
+
+
+def molt_nonuniform_weno_weights(x, period, alpha):
+    """(wR (30, n), wL (30, n)) WENO-Z point tables (5-point rule) of a
+    non-uniform periodic line, computed on the host by the library."""
+    import numpy as np
+    lib = load_library()
+    n = len(x)
+    xs = (ctypes.c_double * n)(*[float(v) for v in x])
+    wR, wL = (ctypes.c_double * (NU_WENO_SLOTS * n))(), (ctypes.c_double * (NU_WENO_SLOTS * n))()
+    st = lib.molt_nonuniform_weno_weights(xs, n, float(period), float(alpha), wR, wL)
+    if st != MOLT_OK:
+        raise MoltError(st, "molt_nonuniform_weno_weights")
+    return (np.frombuffer(wR, dtype=np.float64).reshape(NU_WENO_SLOTS, n).copy(),
+            np.frombuffer(wL, dtype=np.float64).reshape(NU_WENO_SLOTS, n).copy())
 
 
 def molt_mlp_stats(ctx, reset=False):

@@ -1,7 +1,8 @@
 """GPU parity of sum_{p<=P} D^p along non-uniform periodic axes (point-local
 quadrature weights, the non-uniform case of Sec. 2.4) against the FP64
 oracle: 1-D lines of several lengths, every operator and rule, P = 1..3,
-FP64 / FP32 / mixed, contiguous and strided axes, in place; rejected setups."""
+FP64 / FP32 / mixed, contiguous and strided axes, in place; WENO-Z with
+point-local linear weights and smoothness indicators; rejected setups."""
 import numpy as np
 import pytest
 
@@ -101,13 +102,13 @@ def test_rejected_setups():
             M.molt_set_grid_axis(ctx, 0, 0, _nodes(n, 0.0, L))
     finally:
         M.molt_destroy(ctx)
-    dw = M.make_desc((n,), lo=[0], hi=[L], prec=M.PREC_F64, quad_points=5, weights=M.W_WENOZ)
+    dw = M.make_desc((n,), lo=[0], hi=[L], prec=M.PREC_F32, quad_points=5, weights=M.W_LEARNED)
     ctx = M.molt_create(dw)
     try:
         M.molt_set_grid_axis(ctx, 0, 0, _nodes(n, 0.0, L))
-        v = torch.zeros(n, dtype=torch.float64, device="cuda")
+        v = torch.zeros(n, dtype=torch.float32, device="cuda")
         with pytest.raises(M.MoltError):
-            M.molt_apply_D(ctx, 0, 0, M.OP_0, 1, 5.0, v, v)
+            M.molt_apply_D(ctx, 0, 0, M.OP_0, 1, 5.0, v, v)                # learned weights
     finally:
         M.molt_destroy(ctx)
 
@@ -131,3 +132,80 @@ def test_longest_line_uses_sixteen_warps():
         M.molt_destroy(ctx)
     want = nonuniform.partial_sum(v, x, L, 0.6 * n / L, "0", 6, 2)
     assert rel_l2(got, want) < 1e-5
+
+
+def _run_line(x, lo, L, v, op, P, alpha, prec, weights=M.W_LINEAR, npts=5):
+    import torch
+    n = len(x)
+    d = M.make_desc((n,), lo=[lo], hi=[lo + L], quad_points=npts, prec=prec, weights=weights)
+    ctx = M.molt_create(d)
+    try:
+        M.molt_set_grid_axis(ctx, 0, 0, x)
+        vin = to_dev(v, state_dtype(prec))
+        out = torch.empty_like(vin)
+        M.molt_apply_D(ctx, 0, 0, op, P, alpha, vin, out)
+        return out.double().cpu().numpy()
+    finally:
+        M.molt_destroy(ctx)
+
+
+def test_wenoz_lines_1d():
+    """WENO-Z with point-local d_r and smoothness indicators on rough data
+    (every nonlinear weight active), each line length, operator and P, in
+    FP64, FP32 and the mixed form."""
+    need_gpu()
+    lo, L = 0.5, 3.0
+    for n, op, P in ((7, M.OP_0, 1), (100, M.OP_R, 2), (513, M.OP_L, 1), (1000, M.OP_0, 2)):
+        x = _nodes(n, lo, L)
+        alpha = 0.6 * n / L
+        v = workloads.rng(40 + n).standard_normal(n).astype(np.float32).astype(np.float64)
+        want = nonuniform.partial_sum(v, x, L, alpha, OPS[op], 5, P, "wenoz")
+        for prec in (M.PREC_F64, M.PREC_F32, M.PREC_F32_F64UPDATE):
+            got = _run_line(x, lo, L, v, op, P, alpha, prec, M.W_WENOZ)
+            assert rel_l2(got, want) < tol_for(prec), (n, op, P, prec, rel_l2(got, want))
+
+
+def test_wenoz_keeps_a_jump_sharp_and_differs_from_the_linear_rule():
+    """A square wave on a jagged grid: the GPU WENO-Z result matches the
+    oracle's WENO-Z (FP64 bar) and not its linear rule, whose oscillations
+    near the jumps the nonlinear weights remove."""
+    need_gpu()
+    n, lo, L = 400, 0.0, 2 * np.pi
+    w = 1.0 + 0.6 * workloads.rng(9).uniform(-1, 1, n)
+    x = np.concatenate([[0.0], np.cumsum(w)[:-1]]) * (L / w.sum())
+    v = np.where((x > 1.0) & (x < 4.0), 1.0, 0.0)
+    alpha = 0.8 * n / L
+    want = nonuniform.partial_sum(v, x, L, alpha, "R", 5, 1, "wenoz")
+    lin = nonuniform.partial_sum(v, x, L, alpha, "R", 5, 1)
+    got = _run_line(x, lo, L, v, M.OP_R, 1, alpha, M.PREC_F64, M.W_WENOZ)
+    assert rel_l2(got, want) < 1e-12
+    assert rel_l2(got, lin) > 1e-3
+
+
+@pytest.mark.parametrize("prec", [M.PREC_F64, M.PREC_F32])
+def test_wenoz_both_axes_of_a_2d_grid(prec):
+    need_gpu()
+    import torch
+    nx, ny, L = 96, 80, 2 * np.pi
+    xs, ys = _nodes(nx, 0.0, L), _nodes(ny, 0.0, L, amp=0.4)
+    u = workloads.rng(6).standard_normal((ny, nx)).astype(np.float32).astype(np.float64)
+    d = M.make_desc((nx, ny), lo=[0, 0], hi=[L, L], quad_points=5, prec=prec, weights=M.W_WENOZ)
+    ctx = M.molt_create(d)
+    try:
+        M.molt_set_grid_axis(ctx, 0, 0, xs)
+        M.molt_set_grid_axis(ctx, 0, 1, ys)
+        uin = to_dev(u, state_dtype(prec))
+        gx = torch.empty_like(uin)
+        M.molt_apply_D(ctx, 0, 0, M.OP_L, 1, 9.0, uin, gx)
+        gy = uin.clone()
+        M.molt_apply_D(ctx, 0, 1, M.OP_0, 2, 7.0, gy, gy)         # in place, transposed lines
+        gotx, goty = gx.double().cpu().numpy(), gy.double().cpu().numpy()
+    finally:
+        M.molt_destroy(ctx)
+    tx, wx = nonuniform.weights(xs, L, 9.0, 5), nonuniform.weno_tables(xs, L, 9.0, 5)
+    ty, wy = nonuniform.weights(ys, L, 7.0, 5), nonuniform.weno_tables(ys, L, 7.0, 5)
+    wantx = np.stack([nonuniform.partial_sum(u[j], xs, L, 9.0, "L", 5, 1, "wenoz", tx, wx) for j in range(ny)])
+    wanty = np.stack([nonuniform.partial_sum(u[:, i], ys, L, 7.0, "0", 5, 2, "wenoz", ty, wy) for i in range(nx)],
+                     axis=1)
+    assert rel_l2(gotx, wantx) < tol_for(prec)
+    assert rel_l2(goty, wanty) < tol_for(prec)

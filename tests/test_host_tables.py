@@ -67,3 +67,31 @@ def test_library_nonuniform_tables_match_oracle(M, npts, alpha):
     np.testing.assert_allclose(q, wq, rtol=1e-14)
     unused = [k for k in range(6) if k - 3 not in STENCIL[npts]]
     assert np.all(cR[unused] == 0) and np.all(cL[unused] == 0)
+
+
+@pytest.mark.parametrize("alpha", [0.5, 6.0, 80.0])
+def test_library_nonuniform_weno_tables_match_oracle(M, alpha):
+    """The library's WENO-Z point tables (substencil rules, local d_r, and the
+    (a, b) form of the smoothness indicators) against the oracle's (rules,
+    least-squares d_r, indicator matrices in physical coordinates)."""
+    from oracle import nonuniform
+    n, L = 37, 2 * np.pi
+    w = 1.0 + 0.6 * np.random.default_rng(4).uniform(-1, 1, n)
+    x = 0.1 + np.concatenate([[0.0], np.cumsum(w)[:-1]]) * (L / w.sum())
+    wR, wL = M.molt_nonuniform_weno_weights(x, L, alpha)
+    t = nonuniform.weno_tables(x, L, alpha, 5)
+    V = np.random.default_rng(5).standard_normal((n, 5))
+    for side, tab in (("R", wR), ("L", wL)):
+        ref = t[side]
+        for r in range(3):
+            for j in range(3):
+                np.testing.assert_allclose(tab[3 * r + j], ref["sub"][:, r, j], rtol=1e-12, atol=1e-15)
+            np.testing.assert_allclose(tab[9 + r], ref["d"][:, r], rtol=1e-10, atol=1e-13)
+            vals = V[:, r:r + 3]
+            a = sum(tab[12 + 3 * r + j] * vals[:, j] for j in range(3))
+            b = sum(tab[21 + 3 * r + j] * vals[:, j] for j in range(3))
+            beta_lib = a * a - a * b + 4.0 / 3.0 * b * b
+            beta_ref = np.einsum("ia,iab,ib->i", vals, ref["M"][:, r], vals)
+            np.testing.assert_allclose(beta_lib, beta_ref, rtol=1e-10, atol=1e-14)
+    with pytest.raises(M.MoltError):
+        M.molt_nonuniform_weno_weights(x[::-1], L, alpha)
