@@ -35,6 +35,16 @@ smoothness indicators of the commented WENO step,
 with dx_i the width of the integration cell (x_i - x_{i-1} for J_R,
 x_{i+1} - x_i for J_L) -- on a uniform grid this is the uniform indicator.
 The WENO-Z map (eps = 1e-6) then weights the J^{(r)} as on uniform grids.
+
+Dirichlet lines (Sec. 2.3; pass L = None): the nodes x_0 = a < ... < x_N = b
+include both boundary nodes (N >= 3).  Stencils reach ghost nodes mirrored
+about the ends, x_{-j} = 2a - x_j and x_{N+j} = 2b - x_{N-j}, holding the odd
+reflection of the data about the boundary values, v_{-j} = 2 v_0 - v_j and
+v_{N+j} = 2 v_N - v_{N-j} (the readings of the uniform oracle with the
+actual node positions).  The recurrences start from I_R(x_0) = 0 and
+I_L(x_N) = 0, and the boundary constants are fixed by the boundary values:
+A = v(a) for L_R, B = v(b) for L_L, and for L_0 the 2x2 system
+[[1, mu], [mu, 1]] (A, B) = (v_0 - I_0(a), v_N - I_0(b)), mu = e^{-alpha (b - a)}.
 """
 import numpy as np
 from numpy.polynomial import polynomial as npoly
@@ -45,9 +55,32 @@ _GL_X, _GL_W = np.polynomial.legendre.leggauss(48)
 
 
 def _node(x, L, j):
+    """x_j for any j: periodic images (period L), or for a Dirichlet line
+    (L None) the ghost nodes mirrored about the ends."""
     n = len(x)
+    if L is None:
+        N = n - 1
+        if j < 0:
+            return 2.0 * x[0] - x[-j]
+        if j > N:
+            return 2.0 * x[N] - x[2 * N - j]
+        return x[j]
     k, r = divmod(j, n)
     return x[r] + k * L
+
+
+def _value(v, L, j):
+    """v_j for any j: periodic wrap, or (L None) odd reflection about the
+    boundary values."""
+    n = len(v)
+    if L is None:
+        N = n - 1
+        if j < 0:
+            return 2.0 * v[0] - v[-j]
+        if j > N:
+            return 2.0 * v[N] - v[2 * N - j]
+        return v[j]
+    return v[j % n]
 
 
 def _cell(x, L, i, side):
@@ -150,8 +183,8 @@ def local_integrals(v, x, L, alpha, npts, weights_kind="linear", tables=None):
     offs = STENCIL[npts]
     if weights_kind == "linear":
         cR, cL, _ = tables if tables is not None else weights(x, L, alpha, npts)
-        JR = np.array([sum(cR[i, m] * v[(i + l) % n] for m, l in enumerate(offs)) for i in range(n)])
-        JL = np.array([sum(cL[i, m] * v[(i - l) % n] for m, l in enumerate(offs)) for i in range(n)])
+        JR = np.array([sum(cR[i, m] * _value(v, L, i + l) for m, l in enumerate(offs)) for i in range(n)])
+        JL = np.array([sum(cL[i, m] * _value(v, L, i - l) for m, l in enumerate(offs)) for i in range(n)])
         return JR, JL
     if weights_kind != "wenoz":
         raise ValueError(weights_kind)
@@ -162,7 +195,7 @@ def local_integrals(v, x, L, alpha, npts, weights_kind="linear", tables=None):
         t = wt[side]
         out = np.zeros(n)
         for i in range(n):
-            vals = np.array([v[(i + sign * l) % n] for l in offs])
+            vals = np.array([_value(v, L, i + sign * l) for l in offs])
             om = weno_weights_at(vals, t["d"][i], t["M"][i])
             out[i] = sum(om[r] * (t["sub"][i, r] @ vals[r:r + m]) for r in range(3))
         J[side] = out
@@ -170,11 +203,17 @@ def local_integrals(v, x, L, alpha, npts, weights_kind="linear", tables=None):
 
 
 def inverse(v, x, L, alpha, op, npts, tables=None, weights_kind="linear", weno=None):
-    """L_op^{-1}[v] on one periodic non-uniform line (op in R, L, 0)."""
+    """L_op^{-1}[v] on one non-uniform line (op in R, L, 0): periodic with
+    period L, or Dirichlet (L None)."""
     n = len(x)
+    if L is None and n < 4:
+        raise ValueError("a Dirichlet line needs at least 4 nodes")
     cR, cL, q = tables if tables is not None else weights(x, L, alpha, npts)
     JR, JL = local_integrals(v, x, L, alpha, npts, weights_kind,
                              (cR, cL, q) if weights_kind == "linear" else weno)
+    if L is None:
+        return _inverse_dirichlet(np.asarray(v, dtype=np.float64), np.asarray(x, dtype=np.float64), alpha, op,
+                                  JR, JL, q)
     mu = np.prod(q)
     IR = np.zeros(n)
     acc = 0.0
@@ -203,9 +242,34 @@ def inverse(v, x, L, alpha, op, npts, tables=None, weights_kind="linear", weno=N
     return 0.5 * (IL + IR)
 
 
+def _inverse_dirichlet(v, x, alpha, op, JR, JL, q):
+    """Recurrences from I_R(x_0) = 0 and I_L(x_N) = 0, then the boundary
+    constants from the boundary values (Sec. 2.3, the 2x2 algebra of Sec. 3.3)."""
+    N = len(x) - 1
+    IR = np.zeros(N + 1)
+    for i in range(1, N + 1):
+        IR[i] = q[i] * IR[i - 1] + JR[i]
+    IL = np.zeros(N + 1)
+    for i in range(N - 1, -1, -1):
+        IL[i] = q[i + 1] * IL[i + 1] + JL[i]
+    ea = np.exp(-alpha * (x - x[0]))      # e^{-alpha (x_i - a)}
+    eb = np.exp(-alpha * (x[N] - x))      # e^{-alpha (b - x_i)}
+    mu = np.exp(-alpha * (x[N] - x[0]))
+    if op == "R":
+        return IR + v[0] * ea
+    if op == "L":
+        return IL + v[N] * eb
+    I0 = 0.5 * (IL + IR)
+    r0, r1 = v[0] - I0[0], v[N] - I0[N]
+    A = (r0 - mu * r1) / (1.0 - mu * mu)
+    B = (r1 - mu * r0) / (1.0 - mu * mu)
+    return I0 + A * ea + B * eb
+
+
 def partial_sum(v, x, L, alpha, op, npts, P, weights_kind="linear", tables=None, weno=None):
-    """S_P = sum_{p<=P} D^p[v] on one periodic non-uniform line (``tables``,
-    ``weno``: the line's weights() / weno_tables(), built when not given)."""
+    """S_P = sum_{p<=P} D^p[v] on one non-uniform line, periodic or (L None)
+    Dirichlet (``tables``, ``weno``: the line's weights() / weno_tables(),
+    built when not given)."""
     if tables is None:
         tables = weights(x, L, alpha, npts)
     if weights_kind == "wenoz" and weno is None:

@@ -233,3 +233,106 @@ def test_weno_converges_on_stretched_grids():
         errs.append(np.abs(got - alpha ** 2 / (alpha ** 2 + k ** 2) * np.sin(k * x)).max())
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert all(r > 3.5 for r in rates), (errs, rates)
+
+
+# ---------------------------------------------------------------- Dirichlet
+# Non-uniform Dirichlet lines (Sec. 2.3): nodes x_0 = a .. x_N = b, mirrored
+# ghost nodes with odd-reflected data, boundary constants from the boundary
+# values.
+
+def _dirichlet_nodes(N, a=0.0, b=np.pi, amp=0.25):
+    t = np.linspace(0.0, 1.0, N + 1)
+    return a + (b - a) * (t + amp * np.sin(2 * np.pi * t) / (2 * np.pi))
+
+
+@pytest.mark.parametrize("npts,kind", [(3, "linear"), (6, "linear"), (5, "linear"), (5, "wenoz")])
+@pytest.mark.parametrize("op", ["R", "L", "0"])
+def test_dirichlet_on_a_uniform_grid_reproduces_the_uniform_oracle(npts, kind, op):
+    N, a, b, alpha = 30, 0.5, 2.0, 9.0
+    x = np.linspace(a, b, N + 1)
+    v = np.random.default_rng(21).standard_normal(N + 1)
+    got = nonuniform.partial_sum(v, x, None, alpha, op, npts, 2, kind)
+    want = sweep.partial_sum(v[None, :], 1, alpha, (b - a) / N, op, "dirichlet", npts, 2, weights=kind)[0]
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("npts,kind", [(6, "linear"), (5, "wenoz")])
+def test_dirichlet_is_the_doubled_periodic_line_with_odd_data(npts, kind):
+    """Homogeneous data: the Dirichlet line equals the periodic line of
+    period 2(b - a) through the nodes mirrored about b, with the data odd
+    about a and b (images + uniqueness of the 2x2 solve), for L_0 and S_P."""
+    N, alpha = 17, 4.0
+    x = _dirichlet_nodes(N)
+    a, b = x[0], x[-1]
+    v = np.random.default_rng(22).standard_normal(N + 1)
+    v[0] = v[-1] = 0.0
+    xd = np.concatenate([x, 2 * b - x[-2:0:-1]])
+    vd = np.concatenate([v, -v[-2:0:-1]])
+    got = nonuniform.partial_sum(v, x, None, alpha, "0", npts, 3, kind)
+    want = nonuniform.partial_sum(vd, xd, 2 * (b - a), alpha, "0", npts, 3, kind)[:N + 1]
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("op", ["R", "L", "0"])
+def test_dirichlet_keeps_constants_in_the_kernel_of_D_and_meets_the_boundary_values(op):
+    N, alpha = 20, 3.0
+    x = _dirichlet_nodes(N, amp=0.4)
+    S = nonuniform.partial_sum(np.full(N + 1, 0.9), x, None, alpha, op, 6, 2)
+    assert np.abs(S).max() < 1e-13
+    v = np.random.default_rng(23).standard_normal(N + 1)
+    Li = nonuniform.inverse(v, x, None, alpha, op, 6)
+    if op in "R0":
+        assert abs(Li[0] - v[0]) < 1e-13                 # L^{-1}[v](a) = v(a)
+    if op in "L0":
+        assert abs(Li[-1] - v[-1]) < 1e-13               # L^{-1}[v](b) = v(b)
+
+
+def test_dirichlet_right_inverse_is_the_cell_by_cell_integral_plus_the_inflow_term():
+    """L_R^{-1}[v](x_i) = sum over the cells left of x_i of alpha int
+    e^{-alpha (x_i - s)} p_j(s) ds (p_j the interpolant of the cell's stencil,
+    with mirrored ghosts) + v(a) e^{-alpha (x_i - a)} -- no recurrence."""
+    N, alpha, npts = 9, 2.3, 6
+    x = _dirichlet_nodes(N, amp=0.5)
+    v = np.cos(x) + 0.4 * x
+    offs = STENCIL[npts]
+    gx, gw = np.polynomial.legendre.leggauss(40)
+
+    def node(j):
+        if j < 0:
+            return 2 * x[0] - x[-j]
+        if j > N:
+            return 2 * x[N] - x[2 * N - j]
+        return x[j]
+
+    def val(j):
+        if j < 0:
+            return 2 * v[0] - v[-j]
+        if j > N:
+            return 2 * v[N] - v[2 * N - j]
+        return v[j]
+
+    want = np.zeros(N + 1)
+    for i in range(N + 1):
+        tot = v[0] * math.exp(-alpha * (x[i] - x[0]))
+        for j in range(1, i + 1):
+            a, b = node(j - 1), node(j)
+            s = 0.5 * (b - a) * gx + 0.5 * (b + a)
+            nodes = [node(j + l) - node(j) for l in offs]
+            p = sum(val(j + l) * npoly.polyval(s - node(j), lagrange_basis(nodes, m)) for m, l in enumerate(offs))
+            tot += np.sum(0.5 * (b - a) * gw * alpha * np.exp(-alpha * (x[i] - s)) * p)
+        want[i] = tot
+    got = nonuniform.inverse(v, x, None, alpha, "R", npts)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
+def test_dirichlet_converges_to_the_continuous_operator_on_stretched_grids():
+    """sin kx on [0, pi] is odd about both ends, so the homogeneous Dirichlet
+    L_0^{-1}[sin kx] is alpha^2/(alpha^2 + k^2) sin kx."""
+    alpha, k = 4.0, 3
+    errs = []
+    for N in (64, 128, 256):
+        x = _dirichlet_nodes(N)
+        got = nonuniform.inverse(np.sin(k * x), x, None, alpha, "0", 6)
+        errs.append(np.abs(got - alpha ** 2 / (alpha ** 2 + k ** 2) * np.sin(k * x)).max())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(r > 5.0 for r in rates), (errs, rates)
