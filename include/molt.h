@@ -213,6 +213,31 @@ molt_status molt_nonuniform_weights(const double* x, int64_t n, double period, d
 molt_status molt_nonuniform_weno_weights(const double* x, int64_t n, double period, double alpha, double* wR,
                                          double* wL);
 
+/* Tile plan of a sweep (host only, no device work): the tile shape that
+ * molt_apply_D(op, P, alpha) along `axis` of a problem described by `d`
+ * launches with the plain sweep kernel -- points per lane E, warps per line
+ * (32 E warps_per_line >= n), lines per CTA (a power of two), threads per CTA
+ * (<= 512), CTAs (ceil(lines / lines_per_cta)), dynamic shared memory per
+ * CTA, and whether the line fills its lanes exactly (no masked points).
+ * Where the array geometry meets the tensor-copy alignment rules the
+ * persistent TMA kernel runs the same tiles with one CTA per SM.  The SM
+ * count that sizes grids with few lines is the current device's (152 when
+ * no device is present).  MOLT_EINVAL: an invalid descriptor or argument;
+ * MOLT_EUNSUPPORTED: a line or tile the sweeps do not take, learned weights.
+ * The reason is in molt_last_error(NULL). */
+typedef struct {
+  int32_t points_per_lane;
+  int32_t warps_per_line;
+  int32_t lines_per_cta;
+  int32_t threads_per_cta;
+  int64_t ctas;
+  int64_t smem_bytes;
+  int32_t exact_fit;
+  int32_t reserved;
+} molt_sweep_plan;
+
+molt_status molt_plan_sweep(const molt_desc* d, int axis, int op, int P, double alpha, molt_sweep_plan* out);
+
 /* Context options.
  *   MOLT_OPT_TMA      1 (default): sweeps whose lines are an exact fit and
  *                     whose arrays meet the tensor-copy alignment rules run

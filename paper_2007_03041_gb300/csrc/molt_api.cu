@@ -204,7 +204,7 @@ int device_sms() {
   if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
   }
   return sms;
 }
@@ -479,6 +479,25 @@ molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int 
                                const void* in, void* out);
 molt_status transpose(molt_ctx* c, const Problem& p, const void* in, void* out, long long ny, long long nx);
 Problem transposed(const Problem& p);
+
+// Sizes and spacings of a validated descriptor (periodic axes: n intervals,
+// Dirichlet axes: n - 1).
+Problem make_problem(const molt_desc& d) {
+  Problem p;
+  p.d = d;
+  p.total = 1;
+  for (int ax = 0; ax < 3; ++ax) {
+    p.n[ax] = ax < p.d.ndim ? p.d.n[ax] : 1;
+    p.total *= p.n[ax];
+    if (ax < p.d.ndim) {
+      const int64_t N = p.d.bc[ax] == MOLT_BC_PERIODIC ? p.n[ax] : p.n[ax] - 1;
+      p.h[ax] = (p.d.hi[ax] - p.d.lo[ax]) / double(N);
+    } else {
+      p.h[ax] = 1.0;
+    }
+  }
+  return p;
+}
 }  // namespace
 
 extern "C" {
@@ -494,19 +513,7 @@ molt_status molt_create(const molt_desc* descs, int count, void* cuda_stream, mo
       delete c;
       return fail(nullptr, MOLT_EINVAL, "problem " + std::to_string(i) + ": " + v);
     }
-    Problem p;
-    p.d = descs[i];
-    p.total = 1;
-    for (int ax = 0; ax < 3; ++ax) {
-      p.n[ax] = ax < p.d.ndim ? p.d.n[ax] : 1;
-      p.total *= p.n[ax];
-      if (ax < p.d.ndim) {
-        const int64_t N = p.d.bc[ax] == MOLT_BC_PERIODIC ? p.n[ax] : p.n[ax] - 1;
-        p.h[ax] = (p.d.hi[ax] - p.d.lo[ax]) / double(N);
-      } else {
-        p.h[ax] = 1.0;
-      }
-    }
+    Problem p = make_problem(descs[i]);
     if (p.d.pde == MOLT_PDE_HJ) {
       for (int ax = 0; ax < p.d.ndim; ++ax)
         if (p.d.bc[ax] != MOLT_BC_PERIODIC) {
@@ -629,6 +636,32 @@ molt_status molt_apply_D(molt_ctx* c, int problem, int axis, int op, int P, doub
   pl.a.in = in;
   pl.a.out = out;
   return run(c, p, EPI_STORE, pl, false);
+}
+
+molt_status molt_plan_sweep(const molt_desc* d, int axis, int op, int P, double alpha, molt_sweep_plan* out) {
+  if (!d || !out) return fail(nullptr, MOLT_EINVAL, "null descriptor or plan");
+  const std::string v = validate(*d);
+  if (!v.empty()) return fail(nullptr, MOLT_EINVAL, v);
+  if (axis < 0 || axis >= d->ndim) return fail(nullptr, MOLT_EINVAL, "axis out of range");
+  if (op != MOLT_OP_L && op != MOLT_OP_R && op != MOLT_OP_0) return fail(nullptr, MOLT_EINVAL, "unknown op");
+  if (P < 1 || P > 64) return fail(nullptr, MOLT_EINVAL, "P must be in 1..64");
+  if (d->weights == MOLT_W_LEARNED)
+    return fail(nullptr, MOLT_EUNSUPPORTED, "learned sweeps are planned with their network");
+  const Problem p = make_problem(*d);
+  molt_ctx host;                 // planning reads no device state
+  Plan pl;
+  const int mode = op == MOLT_OP_L ? MODE_L : (op == MOLT_OP_R ? MODE_R : MODE_0);
+  const molt_status st = plan_axis(&host, p, axis, mode, P, alpha, &pl);
+  if (st != MOLT_OK) return fail(nullptr, st, host.err);
+  out->points_per_lane = pl.a.E;
+  out->warps_per_line = pl.a.nwl;
+  out->lines_per_cta = pl.a.W;
+  out->threads_per_cta = pl.block;
+  out->ctas = pl.grid;
+  out->smem_bytes = int64_t(pl.smem);
+  out->exact_fit = exact_fit(pl.a) ? 1 : 0;
+  out->reserved = 0;
+  return MOLT_OK;
 }
 
 }  // extern "C"

@@ -25,7 +25,7 @@ EXPORTS = ("molt_create", "molt_apply_D", "molt_step", "molt_set_option", "molt_
            "molt_last_error", "molt_wave_step_noalloc", "molt_batch_tile_shape", "molt_set_mlp", "molt_mlp_stats",
            "molt_weno_linear_weights", "molt_mlp_pack", "molt_mlp_forward", "molt_mlp_loss_grad", "molt_mlp_adam",
            "molt_mlp_harvest", "molt_quadrature_weights", "molt_set_source", "molt_set_grid_axis",
-           "molt_nonuniform_weights", "molt_nonuniform_weno_weights")
+           "molt_nonuniform_weights", "molt_nonuniform_weno_weights", "molt_plan_sweep")
 NU_WENO_SLOTS = 30
 MLP_PARAMS = 1347
 MLP_BLOB_BYTES = 3728
@@ -56,6 +56,19 @@ class molt_desc(ctypes.Structure):
         ("h0", ctypes.c_double),
         ("integrator", ctypes.c_int),
         ("flux", ctypes.c_int),
+    ]
+
+
+class molt_sweep_plan(ctypes.Structure):
+    _fields_ = [
+        ("points_per_lane", ctypes.c_int32),
+        ("warps_per_line", ctypes.c_int32),
+        ("lines_per_cta", ctypes.c_int32),
+        ("threads_per_cta", ctypes.c_int32),
+        ("ctas", ctypes.c_int64),
+        ("smem_bytes", ctypes.c_int64),
+        ("exact_fit", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -99,6 +112,8 @@ def load_library(path=LIB_PATH):
                                                 ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
         lib.molt_nonuniform_weno_weights.argtypes = [ctypes.POINTER(dbl), i64, dbl, dbl, ctypes.POINTER(dbl),
                                                      ctypes.POINTER(dbl)]
+        lib.molt_plan_sweep.argtypes = [ctypes.POINTER(molt_desc), ctypes.c_int, ctypes.c_int, ctypes.c_int, dbl,
+                                        ctypes.POINTER(molt_sweep_plan)]
         lib.molt_mlp_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.c_int]
         lib.molt_weno_linear_weights.argtypes = [dbl, ctypes.POINTER(dbl)]
         lib.molt_quadrature_weights.argtypes = [ctypes.c_int, dbl, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
@@ -110,7 +125,7 @@ def load_library(path=LIB_PATH):
         lib.molt_mlp_harvest.argtypes = [vp, i64, i64, vp, i64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dbl), vp,
                                          vp, i64, vp]
         for f in ("molt_set_mlp", "molt_set_source", "molt_set_grid_axis", "molt_nonuniform_weights", "molt_mlp_stats",
-                  "molt_nonuniform_weno_weights", "molt_weno_linear_weights", "molt_quadrature_weights",
+                  "molt_nonuniform_weno_weights", "molt_plan_sweep", "molt_weno_linear_weights", "molt_quadrature_weights",
                   "molt_mlp_pack", "molt_mlp_forward",
                   "molt_mlp_loss_grad", "molt_mlp_adam", "molt_mlp_harvest"):
             getattr(lib, f).restype = ctypes.c_int
@@ -315,6 +330,19 @@ def molt_nonuniform_weno_weights(x, period, alpha):
         raise MoltError(st, "molt_nonuniform_weno_weights")
     return (np.frombuffer(wR, dtype=np.float64).reshape(NU_WENO_SLOTS, n).copy(),
             np.frombuffer(wL, dtype=np.float64).reshape(NU_WENO_SLOTS, n).copy())
+
+
+def molt_plan_sweep(desc, axis, op, P, alpha):
+    """Tile plan of molt_apply_D(op, P, alpha) along ``axis`` (host only):
+    dict of points_per_lane, warps_per_line, lines_per_cta, threads_per_cta,
+    ctas, smem_bytes, exact_fit."""
+    lib = load_library()
+    out = molt_sweep_plan()
+    st = lib.molt_plan_sweep(ctypes.byref(desc), int(axis), int(op), int(P), float(alpha), ctypes.byref(out))
+    if st != MOLT_OK:
+        msg = lib.molt_last_error(None)
+        raise MoltError(st, msg.decode() if msg else "molt_plan_sweep")
+    return {f: getattr(out, f) for f, _ in molt_sweep_plan._fields_ if f != "reserved"}
 
 
 def molt_mlp_stats(ctx, reset=False):
