@@ -280,3 +280,16 @@ def partial_sum(v, x, L, alpha, op, npts, P, weights_kind="linear", tables=None,
         w = w - inverse(w, x, L, alpha, op, npts, tables, weights_kind, weno)
         S = S + w
     return S
+
+
+def partial_sum_axis(u, ax, x, L, alpha, op, npts, P, weights_kind="linear"):
+    """S_P along axis ``ax`` of an n-D array whose lines along that axis have
+    the nodes x (period L, or L None for Dirichlet lines); every line is
+    independent (dimensional splitting, Sec. 2.2)."""
+    tables = weights(x, L, alpha, npts)
+    weno = weno_tables(x, L, alpha, npts) if weights_kind == "wenoz" else None
+    um = np.moveaxis(np.asarray(u, dtype=np.float64), ax, -1)
+    out = np.empty_like(um)
+    for idx in np.ndindex(um.shape[:-1]):
+        out[idx] = partial_sum(um[idx], x, L, alpha, op, npts, P, weights_kind, tables, weno)
+    return np.moveaxis(out, -1, ax)

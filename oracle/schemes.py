@@ -34,56 +34,74 @@ TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__``.
   [min(v_d^-, v_d^+), max(v_d^-, v_d^+)]; for these Hamiltonians |dH/dp_d| is
   the absolute value of an affine function, so the largest value sits at a
   corner of the box, and the oracle evaluates every corner.
+* Non-uniform axes (Sec. 2.4): ``grids[ax] = (x, L)`` gives the nodes of that
+  array axis (period L, or L None for a Dirichlet line) and its partial sums
+  use the point-local weights; alpha does not depend on the spacing for the
+  heat and wave equations, and for Hamilton-Jacobi ``dxs[ax]`` is the
+  smallest cell width of the axis (dt = CFL min_d dx_d / c_d and
+  alpha = beta/(CFL min dx) as on uniform grids).
 """
 import itertools
 
 import numpy as np
 
+from . import nonuniform
 from .sweep import partial_sum, BC_PERIODIC
 
 # 3-stage SSP RK in Shu-Osher form: u_s = a0 u^n + a1 (u_{s-1} + dt F(u_{s-1}))
 SSPRK3 = ((0.0, 1.0), (0.75, 0.25), (1.0 / 3.0, 2.0 / 3.0))
 
 
-def heat_rhs_dt(u, dxs, dt, kappa, beta, bc, npts, P):
+def axis_sum(u, ax, alpha, dx, op, bc, npts, P, weights="linear", weight_fn=None, grids=None):
+    """S_P along array axis ``ax``: uniform spacing dx, or the nodes of a
+    non-uniform axis (grids[ax] = (x, L))."""
+    g = grids[ax] if grids is not None else None
+    if g is None:
+        return partial_sum(u, ax, alpha, dx, op, bc, npts, P, weights, weight_fn)
+    if weight_fn is not None:
+        raise ValueError("learned weights run on uniform axes")
+    return nonuniform.partial_sum_axis(u, ax, g[0], g[1], alpha, op, npts, P, weights)
+
+
+def heat_rhs_dt(u, dxs, dt, kappa, beta, bc, npts, P, grids=None):
     """dt * F(u) = -kappa alpha^2 dt sum_d S_{P,d}[u] = -beta^2 sum_d S_{P,d}[u]."""
     alpha = beta / np.sqrt(kappa * dt)
     acc = np.zeros_like(u)
     for ax in range(u.ndim):
-        acc += partial_sum(u, ax, alpha, dxs[ax], "0", bc[ax], npts, P)
+        acc += axis_sum(u, ax, alpha, dxs[ax], "0", bc[ax], npts, P, grids=grids)
     return -kappa * alpha * alpha * dt * acc
 
 
-def heat_step(u, dxs, dt, kappa=1.0, beta=0.6, bc=None, npts=3, P=3):
+def heat_step(u, dxs, dt, kappa=1.0, beta=0.6, bc=None, npts=3, P=3, grids=None):
     """One SSP-RK3 step of the heat equation."""
     bc = bc or [BC_PERIODIC] * u.ndim
     un = np.asarray(u, dtype=np.float64)
     us = un
     for a0, a1 in SSPRK3:
-        us = a0 * un + a1 * (us + heat_rhs_dt(us, dxs, dt, kappa, beta, bc, npts, P))
+        us = a0 * un + a1 * (us + heat_rhs_dt(us, dxs, dt, kappa, beta, bc, npts, P, grids))
     return us
 
 
-def wave_step(u, u_prev, dxs, dt, c=1.0, beta=0.8, bc=None, npts=6, P=2, from_rest=False):
+def wave_step(u, u_prev, dxs, dt, c=1.0, beta=0.8, bc=None, npts=6, P=2, from_rest=False, grids=None):
     """One step of the wave equation; returns u^{n+1}."""
     bc = bc or [BC_PERIODIC] * u.ndim
     alpha = beta / (c * dt)
     S = np.zeros_like(u, dtype=np.float64)
     for ax in range(u.ndim):
-        S += partial_sum(u, ax, alpha, dxs[ax], "0", bc[ax], npts, P)
+        S += axis_sum(u, ax, alpha, dxs[ax], "0", bc[ax], npts, P, grids=grids)
     # c^2 dt^2 d_xx ~ -c^2 dt^2 alpha^2 S = -beta^2 S
     if from_rest:
         return u - 0.5 * beta * beta * S
     return 2.0 * u - u_prev - beta * beta * S
 
 
-def hj_derivatives(u, alpha, dxs, npts=5, weights="wenoz", weight_fn=None, P=1):
+def hj_derivatives(u, alpha, dxs, npts=5, weights="wenoz", weight_fn=None, P=1, grids=None):
     """(v_d^-, v_d^+) for every axis d: v^- = alpha sum_{p<=P} D_R^p[u],
     v^+ = -alpha sum_{p<=P} D_L^p[u] (Sec. 2.5; P = 1 for forward Euler)."""
     out = []
     for ax in range(u.ndim):
-        dm = alpha * partial_sum(u, ax, alpha, dxs[ax], "R", BC_PERIODIC, npts, P, weights, weight_fn)
-        dp = -alpha * partial_sum(u, ax, alpha, dxs[ax], "L", BC_PERIODIC, npts, P, weights, weight_fn)
+        dm = alpha * axis_sum(u, ax, alpha, dxs[ax], "R", BC_PERIODIC, npts, P, weights, weight_fn, grids)
+        dp = -alpha * axis_sum(u, ax, alpha, dxs[ax], "L", BC_PERIODIC, npts, P, weights, weight_fn, grids)
         out.append((dm, dp))
     return out
 
@@ -152,30 +170,32 @@ def hj_dt(speeds, dxs, cfl):
 
 
 def hj_initial_speeds(u, dxs, cfl=1.5, beta=1.0, npts=5, weights="wenoz", weight_fn=None,
-                      hamiltonian=H_HALF_SQ, a=None, h0=0.0):
+                      hamiltonian=H_HALF_SQ, a=None, h0=0.0, grids=None):
     alpha = beta / (cfl * min(dxs))
-    _, speeds = hj_hamiltonian(hj_derivatives(u, alpha, dxs, npts, weights, weight_fn), hamiltonian, a, h0)
+    _, speeds = hj_hamiltonian(hj_derivatives(u, alpha, dxs, npts, weights, weight_fn, 1, grids), hamiltonian, a,
+                               h0)
     return speeds
 
 
 def hj_step(u, dxs, lagged_speeds, cfl=1.5, beta=1.0, npts=5, weights="wenoz", weight_fn=None,
-            hamiltonian=H_HALF_SQ, a=None, h0=0.0, source=None, t=0.0):
+            hamiltonian=H_HALF_SQ, a=None, h0=0.0, source=None, t=0.0, grids=None):
     """One forward-Euler step u^{n+1} = u^n - dt^n (H^ - F(., t)); returns
     (u^{n+1}, dt^n, speeds of u^n) -- the speeds become the lagged speeds of
     the next step (Algorithm 1).  source: the coefficients F_k of F."""
     alpha = beta / (cfl * min(dxs))
     dt = hj_dt(lagged_speeds, dxs, cfl)
-    Hh, speeds = hj_hamiltonian(hj_derivatives(u, alpha, dxs, npts, weights, weight_fn), hamiltonian, a, h0)
+    Hh, speeds = hj_hamiltonian(hj_derivatives(u, alpha, dxs, npts, weights, weight_fn, 1, grids), hamiltonian, a,
+                                h0)
     if source is not None:
         Hh = Hh - source_at(source, t)
     return u - dt * Hh, dt, speeds
 
 
-def heat_euler_step(u, dxs, dt, kappa=1.0, beta=1.0, bc=None, npts=6, P=1):
+def heat_euler_step(u, dxs, dt, kappa=1.0, beta=1.0, bc=None, npts=6, P=1, grids=None):
     """One forward-Euler step of the heat equation (Sec. 5.1, Example 2)."""
     bc = bc or [BC_PERIODIC] * u.ndim
     un = np.asarray(u, dtype=np.float64)
-    return un + heat_rhs_dt(un, dxs, dt, kappa, beta, bc, npts, P)
+    return un + heat_rhs_dt(un, dxs, dt, kappa, beta, bc, npts, P, grids)
 
 
 # ---------------------------------------------------------------- advection-diffusion
