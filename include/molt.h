@@ -184,18 +184,25 @@ molt_status molt_set_source(molt_ctx* ctx, int problem, const void* coef, int de
  * MOLT_EUNSUPPORTED: a Dirichlet axis.  Synchronous. */
 molt_status molt_set_grid_axis(molt_ctx* ctx, int problem, int axis, const double* x, int64_t n);
 
-/* The point tables of a non-uniform periodic line (host only, no device
- * work): for nodes x[n] of one period of length `period`, alpha and the rule,
- * cR[6 n] and cL[6 n] (slot m of point i at m * n + i belongs to offset
- * m - 3: J_R(x_i) = sum_m cR v_{i+m-3}, J_L(x_i) = sum_m cL v_{i-(m-3)};
- * unused slots 0) and q[n] (q_i = e^{-alpha (x_i - x_{i-1})}), as the
- * non-uniform sweeps use them.  MOLT_EINVAL on bad arguments. */
+/* The point tables of a non-uniform line (host only, no device work): for
+ * nodes x[n] of one period of length `period` (> 0), or of a Dirichlet line
+ * (period == 0: x[0] = a .. x[n-1] = b are both boundary nodes, n >= 4, and
+ * the stencils reach ghost nodes mirrored about the ends, Sec. 2.3), alpha
+ * and the rule: cR[6 n] and cL[6 n] (slot m of point i at m * n + i belongs
+ * to offset m - 3: J_R(x_i) = sum_m cR v_{i+m-3}, J_L(x_i) = sum_m cL
+ * v_{i-(m-3)}; unused slots 0) and q[n] (q_i = e^{-alpha (x_i - x_{i-1})}),
+ * as the non-uniform sweeps use them.  On a Dirichlet line the recurrences
+ * start at the ends: J_R(x_0) = J_L(x_{n-1}) = 0 and q_0 = 0.  MOLT_EINVAL on
+ * bad arguments (nodes not strictly increasing or not finite, a periodic line
+ * wider than its period). */
 molt_status molt_nonuniform_weights(const double* x, int64_t n, double period, double alpha, int quad_points,
                                     double* cR, double* cL, double* q);
 
-/* The WENO-Z point tables of a non-uniform periodic line for the 5-point rule
- * (host only, no device work; Sec. 2.4: on a non-uniform mesh the linear
- * weights d_r are local to each point).  wR[30 n] (J_R) and wL[30 n] (J_L),
+/* The WENO-Z point tables of a non-uniform line for the 5-point rule (host
+ * only, no device work; Sec. 2.4: on a non-uniform mesh the linear weights
+ * d_r are local to each point); `period` as for molt_nonuniform_weights (a
+ * Dirichlet line's end points, where the recurrences start, get zero rules
+ * and d_r = 1/3).  wR[30 n] (J_R) and wL[30 n] (J_L),
  * slot s of point i at s * n + i, with substencil r = 0..2 on the offsets
  * {r-3, r-2, r-1} (nodes x_{i+o} for J_R, x_{i-o} for J_L):
  *   slots 3r+j     c^{(r)}_j, the rule of substencil r:

@@ -1813,14 +1813,24 @@ molt_status molt_set_source(molt_ctx* c, int problem, const void* coef, int degr
   return MOLT_OK;
 }
 
+// Nodes of a non-uniform line: strictly increasing and finite; a periodic
+// line (period > 0) fits in one period, a Dirichlet line (period == 0) has
+// at least 4 nodes.
+static bool nonuniform_nodes_ok(const double* x, int64_t n, double period) {
+  if (!x || n < 1 || !std::isfinite(period) || period < 0) return false;
+  if (period == 0 && n < 4) return false;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!std::isfinite(x[i])) return false;
+    if (i > 0 && !(x[i] > x[i - 1])) return false;
+  }
+  return period == 0 || x[n - 1] - x[0] < period;
+}
+
 molt_status molt_nonuniform_weights(const double* x, int64_t n, double period, double alpha, int quad_points,
                                     double* cR, double* cL, double* q) {
-  if (!x || !cR || !cL || !q || n < 1 || !(period > 0) || !(alpha > 0) || !std::isfinite(alpha))
+  if (!cR || !cL || !q || !nonuniform_nodes_ok(x, n, period) || !(alpha > 0) || !std::isfinite(alpha))
     return MOLT_EINVAL;
   if (quad_points != 3 && quad_points != 5 && quad_points != 6) return MOLT_EINVAL;
-  for (int64_t i = 1; i < n; ++i)
-    if (!(x[i] > x[i - 1])) return MOLT_EINVAL;
-  if (!(x[n - 1] - x[0] < period)) return MOLT_EINVAL;
   std::vector<double> nodes(x, x + n), r, l, qq;
   build_nonuniform_tables(nodes, period, alpha, quad_points, &r, &l, &qq);
   std::copy(r.begin(), r.end(), cR);
@@ -1831,10 +1841,7 @@ molt_status molt_nonuniform_weights(const double* x, int64_t n, double period, d
 
 molt_status molt_nonuniform_weno_weights(const double* x, int64_t n, double period, double alpha, double* wR,
                                          double* wL) {
-  if (!x || !wR || !wL || n < 1 || !(period > 0) || !(alpha > 0) || !std::isfinite(alpha)) return MOLT_EINVAL;
-  for (int64_t i = 1; i < n; ++i)
-    if (!(x[i] > x[i - 1])) return MOLT_EINVAL;
-  if (!(x[n - 1] - x[0] < period)) return MOLT_EINVAL;
+  if (!wR || !wL || !nonuniform_nodes_ok(x, n, period) || !(alpha > 0) || !std::isfinite(alpha)) return MOLT_EINVAL;
   std::vector<double> nodes(x, x + n), r, l;
   build_nonuniform_weno_tables(nodes, period, alpha, &r, &l);
   std::copy(r.begin(), r.end(), wR);

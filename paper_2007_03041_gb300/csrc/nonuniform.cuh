@@ -68,7 +68,27 @@ inline void gauss_legendre(int n, double* x, double* w) {
   }
 }
 
-// cR, cL: 6*n (slot-major), q: n.  x: the n nodes of one period [x_0, x_0 + L).
+// x_j for any j: periodic images (L > 0, x the nodes of one period), or for a
+// Dirichlet line (L == 0, nodes x_0 = a .. x_{n-1} = b, n >= 4) the ghost
+// nodes mirrored about the ends, x_{-j} = 2a - x_j, x_{N+j} = 2b - x_{N-j}
+// (Sec. 2.3: the stencils reach odd-reflected data there).
+inline double nu_node(const std::vector<double>& x, double L, long long j) {
+  const long long n = static_cast<long long>(x.size());
+  if (L > 0) {
+    long long r = j % n;
+    if (r < 0) r += n;
+    return x[size_t(r)] + double((j - r) / n) * L;
+  }
+  const long long N = n - 1;
+  if (j < 0) return 2.0 * x[0] - x[size_t(-j)];
+  if (j > N) return 2.0 * x[size_t(N)] - x[size_t(2 * N - j)];
+  return x[size_t(j)];
+}
+
+// cR, cL: 6*n (slot-major), q: n.  x: the n nodes of one period [x_0, x_0 + L),
+// or (L == 0) of a Dirichlet line.  Dirichlet lines start their recurrences
+// at the ends, I_R(x_0) = 0 and I_L(x_N) = 0: J_R(x_0) and J_L(x_N) are zero
+// and q_0 = 0, so a scan over the whole line gives exactly those values.
 inline void build_nonuniform_tables(const std::vector<double>& x, double L, double alpha, int npts,
                                     std::vector<double>* cR, std::vector<double>* cL, std::vector<double>* q) {
   const int n = int(x.size());
@@ -82,11 +102,7 @@ inline void build_nonuniform_tables(const std::vector<double>& x, double L, doub
   constexpr int kG = 16;
   double gx[kG], gw[kG];
   gauss_legendre(kG, gx, gw);
-  auto node = [&](long long j) {
-    long long r = j % n;
-    if (r < 0) r += n;
-    return x[size_t(r)] + double((j - r) / n) * L;
-  };
+  auto node = [&](long long j) { return nu_node(x, L, j); };
   for (int i = 0; i < n; ++i) {
     const double xi = x[size_t(i)];
     for (int side = 0; side < 2; ++side) {
@@ -109,10 +125,18 @@ inline void build_nonuniform_tables(const std::vector<double>& x, double L, doub
     }
     (*q)[size_t(i)] = std::exp(-alpha * (xi - node(i - 1)));
   }
+  if (!(L > 0)) {
+    for (int m = 0; m < 6; ++m) {
+      (*cR)[size_t(m) * n] = 0.0;
+      (*cL)[size_t(m) * n + n - 1] = 0.0;
+    }
+    (*q)[0] = 0.0;
+  }
 }
 
 // WENO-Z tables of the 5-point rule (quadratic substencils S_r = offsets
-// {r-3, r-2, r-1}, Sec. 2.4), per point and direction, slot-major [kNuWeno][n]:
+// {r-3, r-2, r-1}, Sec. 2.4), per point and direction, slot-major [kNuWeno][n]
+// (periodic lines, or Dirichlet lines with L == 0 as above):
 //   slots 3r+j       c^{(r)}_j: J^{(r)} = sum_j c^{(r)}_j v(node j of S_r)
 //   slots 9+r        d_r, the linear weights with sum_r d_r c^{(r)} = c
 //   slots 12+3r+j    A_{rj} = l_j'(0), slots 21+3r+j  B_{rj} = l_j''
@@ -134,11 +158,7 @@ inline void build_nonuniform_weno_tables(const std::vector<double>& x, double L,
   constexpr int kG = 16;
   double gx[kG], gw[kG];
   gauss_legendre(kG, gx, gw);
-  auto node = [&](long long j) {
-    long long r = j % n;
-    if (r < 0) r += n;
-    return x[size_t(r)] + double((j - r) / n) * L;
-  };
+  auto node = [&](long long j) { return nu_node(x, L, j); };
   // nu int_{-1}^0 e^{nu t} l_m(t) dt for the Lagrange basis on nodes t[0..k)
   auto rule = [&](const double* t, int k, int m, double nu) {
     double sum = 0.0;
@@ -178,6 +198,15 @@ inline void build_nonuniform_weno_tables(const std::vector<double>& x, double L,
       at(9) = d0;
       at(10) = 1.0 - d0 - d2;
       at(11) = d2;
+    }
+  }
+  if (!(L > 0)) {
+    // Dirichlet ends: J_R(x_0) = J_L(x_N) = 0 (zero rules, equal weights)
+    for (int side = 0; side < 2; ++side) {
+      std::vector<double>& w = side == 0 ? *wR : *wL;
+      const size_t i = side == 0 ? 0 : size_t(n - 1);
+      for (int slot = 0; slot < kNuWeno; ++slot) w[size_t(slot) * n + i] = 0.0;
+      for (int r = 0; r < 3; ++r) w[size_t(9 + r) * n + i] = 1.0 / 3.0;
     }
   }
 }

@@ -95,3 +95,43 @@ def test_library_nonuniform_weno_tables_match_oracle(M, alpha):
             np.testing.assert_allclose(beta_lib, beta_ref, rtol=1e-10, atol=1e-14)
     with pytest.raises(M.MoltError):
         M.molt_nonuniform_weno_weights(x[::-1], L, alpha)
+
+
+@pytest.mark.parametrize("npts", [3, 5, 6])
+def test_library_dirichlet_nonuniform_tables_match_oracle(M, npts):
+    """period == 0: a Dirichlet line with both boundary nodes; the stencils
+    reach mirrored ghost nodes.  The rows the recurrences use match the
+    oracle; J_R(x_0), J_L(x_N) and q_0 are zero (the recurrences start there)."""
+    from oracle import nonuniform
+    from oracle.quadrature import STENCIL
+    N, a, b, alpha = 30, 0.2, 2.9, 11.0
+    t = np.linspace(0.0, 1.0, N + 1)
+    x = a + (b - a) * (t + 0.3 * np.sin(2 * np.pi * t) / (2 * np.pi))
+    cR, cL, q = M.molt_nonuniform_weights(x, 0.0, alpha, npts)
+    wR, wL, wq = nonuniform.weights(x, None, alpha, npts)
+    for m, o in enumerate(STENCIL[npts]):
+        np.testing.assert_allclose(cR[o + 3][1:], wR[1:, m], rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(cL[o + 3][:-1], wL[:-1, m], rtol=1e-12, atol=1e-15)
+    assert np.all(cR[:, 0] == 0) and np.all(cL[:, -1] == 0) and q[0] == 0
+    np.testing.assert_allclose(q[1:], wq[1:], rtol=1e-14)
+
+
+def test_library_dirichlet_nonuniform_weno_tables_match_oracle(M):
+    from oracle import nonuniform
+    N, alpha = 25, 6.0
+    t = np.linspace(0.0, 1.0, N + 1)
+    x = np.pi * (t + 0.25 * np.sin(2 * np.pi * t) / (2 * np.pi))
+    wR, wL = M.molt_nonuniform_weno_weights(x, 0.0, alpha)
+    ref = nonuniform.weno_tables(x, None, alpha, 5)
+    for side, tab, rows in (("R", wR, slice(1, None)), ("L", wL, slice(None, -1))):
+        for r in range(3):
+            for j in range(3):
+                np.testing.assert_allclose(tab[3 * r + j][rows], ref[side]["sub"][rows, r, j], rtol=1e-12,
+                                           atol=1e-15)
+            np.testing.assert_allclose(tab[9 + r][rows], ref[side]["d"][rows, r], rtol=1e-10, atol=1e-13)
+    assert np.all(wR[:9, 0] == 0) and np.all(wL[:9, -1] == 0)
+    np.testing.assert_allclose(wR[9:12, 0], 1.0 / 3.0)
+    with pytest.raises(M.MoltError):
+        M.molt_nonuniform_weights(x[:3], 0.0, alpha, 6)                       # fewer than 4 nodes
+    with pytest.raises(M.MoltError):
+        M.molt_nonuniform_weights(x, -1.0, alpha, 6)                          # negative period
