@@ -302,7 +302,7 @@ molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, do
     a.mlp = static_cast<const MlpBlob*>(c->mlp_blob);
     a.mlp_stats = c->mlp_stats;
   }
-  if (out->smem > 200 * 1024) return fail(c, MOLT_EUNSUPPORTED, "tile does not fit in shared memory");
+  if (out->smem > kSmemTileBudget) return fail(c, MOLT_EUNSUPPORTED, "tile does not fit in shared memory");
   out->block = 32 * nwl * W;
   out->grid = int((a.g.nlines + W - 1) / W);
   a.status = c->status_dev;
@@ -365,7 +365,7 @@ void plan_tma(const Problem& p, int ax, const void* in, size_t in_bytes, Plan* p
   const size_t bar_off = (pl->smem + 15) & ~size_t(15);
   const size_t stage_off = (bar_off + 16 + 127) & ~size_t(127);
   const size_t total = stage_off + size_t(tg.tx_bytes);
-  if (total > 210 * 1024) return;
+  if (total > kSmemOptIn) return;
   pl->tma.tg = tg;
   pl->tma.map = map;
   pl->tma.smem = total;
@@ -864,14 +864,14 @@ molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int 
   const int nw = std::max(1, (n + 511) / 512);
   if (nw > 16) return fail(c, MOLT_EUNSUPPORTED, "non-uniform line longer than 8192 points");
   const size_t smem = (size_t(2 * n + 6) + size_t(2 * nw)) * tb;
-  if (smem > 200 * 1024) return fail(c, MOLT_EUNSUPPORTED, "non-uniform line too long for shared memory");
+  if (smem > kSmemTileBudget) return fail(c, MOLT_EUNSUPPORTED, "non-uniform line too long for shared memory");
   if (a.g.nlines >= (1LL << 31)) return fail(c, MOLT_EUNSUPPORTED, "more than 2^31 lines along an axis");
   const long long blocks = a.g.nlines;
   const int warps = nw;
   molt_ctx::Rec rec;
   record_begin(c, &rec, MOLT_KERNEL_STORE);
   auto launch = [&](auto kernel, auto tables) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemOptIn));
     kernel<<<unsigned(blocks), 32 * warps, smem, c->stream>>>(a, tables);
   };
   if (f64) {

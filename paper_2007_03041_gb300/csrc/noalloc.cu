@@ -84,7 +84,7 @@ bool plan(const molt_desc& d, int ax, double alpha, int* status, SweepArgs* a, i
   a->LS = LS;
   const size_t off = (size_t(4 * W) * 8 + size_t(W * nwl * 4) * 4 + 15) & ~size_t(15);
   *smem = off + size_t(W) * LS * 4;
-  if (*smem > 200 * 1024) return false;
+  if (*smem > kSmemTileBudget) return false;
   *block = 32 * nwl * W;
   *grid = int((g.nlines + W - 1) / W);
   a->status = status;

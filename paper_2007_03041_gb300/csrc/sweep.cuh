@@ -49,6 +49,11 @@ constexpr int kMaxThreads = MOLT_MAX_THREADS;
 #define MOLT_MIN_BLOCKS 1
 #endif
 constexpr int kMinBlocks = MOLT_MIN_BLOCKS;   // resident CTAs per SM the register budget targets
+// Shared memory per CTA (the GPU allows 227 KB): a sweep tile's budget, and the
+// dynamic size the sweep kernels opt into (a TMA tile plus its staging buffer
+// must fit it).
+constexpr size_t kSmemTileBudget = 200 * 1024;
+constexpr size_t kSmemOptIn = 210 * 1024;
 
 enum Epi {
   EPI_STORE = 0,       // out = S

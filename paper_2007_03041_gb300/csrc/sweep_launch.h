@@ -40,7 +40,7 @@ inline bool exact_fit(const SweepArgs& a) { return a.g.n == a.nwl * 32 * plan_E(
       static bool configured = false;                                                            \
       if (!configured) {                                                                         \
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                                             210 * 1024);                                        \
+                                             int(kSmemOptIn));                                   \
         if (e != cudaSuccess) return e;                                                          \
         configured = true;                                                                       \
       }                                                                                          \
@@ -66,7 +66,7 @@ inline bool exact_fit(const SweepArgs& a) { return a.g.n == a.nwl * 32 * plan_E(
     static bool configured[3][2] = {};                                                           \
     if (!configured[ei][fit]) {                                                                  \
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
-                                           200 * 1024);                                          \
+                                           int(kSmemTileBudget));                                \
       if (e != cudaSuccess) return e;                                                            \
       configured[ei][fit] = true;                                                                \
     }                                                                                            \
