@@ -240,3 +240,22 @@ def test_partial_sum_along_axes_of_nd_array():
         for x in range(8):
             line = sweep.partial_sum_lines(u[z, :, x][None, :], 3.0, 0.1, "0", "periodic", 6, 2)[0]
             np.testing.assert_allclose(S[z, :, x], line, atol=1e-15)
+
+
+@pytest.mark.parametrize("npts", [3, 5, 6])
+@pytest.mark.parametrize("op", ["L", "R", "0"])
+def test_tiny_periodic_lines_follow_the_symbol(npts, op):
+    """Lines shorter than the stencil (n = 1..5, the stencil wraps onto the
+    same points): every discrete mode still gets the symbol's factor, since
+    the recurrences with the periodic closure sum all images exactly."""
+    for n in range(1, 6):
+        dx = 2 * np.pi / n
+        alpha = 0.8 / dx
+        j = np.arange(n)
+        for k in range(n):
+            th = 2 * np.pi * k / n
+            lam = stability.symbol(th, alpha * dx, op, npts)
+            v = np.cos(th * j + 0.4)
+            got = sweep.inverse_operator(v[None, :], alpha, dx, op, "periodic", npts)[0]
+            want = (lam * np.exp(1j * (th * j + 0.4))).real
+            np.testing.assert_allclose(got, want, atol=1e-14, err_msg=f"n={n} k={k}")
