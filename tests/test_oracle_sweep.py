@@ -259,3 +259,24 @@ def test_tiny_periodic_lines_follow_the_symbol(npts, op):
             got = sweep.inverse_operator(v[None, :], alpha, dx, op, "periodic", npts)[0]
             want = (lam * np.exp(1j * (th * j + 0.4))).real
             np.testing.assert_allclose(got, want, atol=1e-14, err_msg=f"n={n} k={k}")
+
+
+@pytest.mark.parametrize("npts", [3, 5, 6])
+def test_short_dirichlet_lines_meet_the_boundary_values(npts):
+    """Dirichlet lines of 2-6 nodes (ghosts reflected about the ends, clamped
+    where the line is shorter than the stencil): L_0^{-1}[v] takes the
+    boundary values at both ends, L_R^{-1}[v](a) = v(a), L_L^{-1}[v](b) = v(b),
+    and constants lie in the kernel of D."""
+    rng = np.random.default_rng(44)
+    for n in range(2, 7):
+        dx = 1.0 / (n - 1)
+        alpha = 0.9 / dx
+        v = rng.standard_normal((1, n))
+        L0 = sweep.inverse_operator(v, alpha, dx, "0", "dirichlet", npts)[0]
+        LR = sweep.inverse_operator(v, alpha, dx, "R", "dirichlet", npts)[0]
+        LL = sweep.inverse_operator(v, alpha, dx, "L", "dirichlet", npts)[0]
+        assert abs(L0[0] - v[0, 0]) < 1e-14 and abs(L0[-1] - v[0, -1]) < 1e-14, n
+        assert abs(LR[0] - v[0, 0]) < 1e-14 and abs(LL[-1] - v[0, -1]) < 1e-14, n
+        for op in "LR0":
+            S = sweep.partial_sum_lines(np.full((1, n), 0.6), alpha, dx, op, "dirichlet", npts, 2)
+            assert np.abs(S).max() < 1e-14, (n, op)
