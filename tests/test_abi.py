@@ -2,6 +2,7 @@
 (no GPU needed: nothing here calls into CUDA)."""
 import ctypes
 import os
+import pathlib
 import re
 
 from tests.conftest import ROOT
@@ -12,7 +13,7 @@ def declared_functions():
     inc = os.path.join(ROOT, "include")
     for f in sorted(os.listdir(inc)):
         if f.endswith(".h"):
-            src = open(os.path.join(inc, f)).read()
+            src = pathlib.Path(inc, f).read_text()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
             names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(molt_\w+)\s*\(", src, flags=re.M)
     return names

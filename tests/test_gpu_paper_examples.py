@@ -7,6 +7,7 @@ grid against the closed-form discrete solutions, the exact solutions and the
 L-infinity errors the paper prints."""
 import math
 import os
+import pathlib
 
 import numpy as np
 import pytest
@@ -24,7 +25,7 @@ ORACLE_H = {M.H_HALF_SQ: schemes.H_HALF_SQ, M.H_LINEAR: schemes.H_LINEAR, M.H_AF
 
 def _paper_numbers():
     out = {}
-    for line in open(GOLDEN):
+    for line in pathlib.Path(GOLDEN).read_text().splitlines():
         line = line.split("#")[0].split()
         if len(line) == 2:
             out[line[0]] = float(line[1])

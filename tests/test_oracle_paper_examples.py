@@ -6,6 +6,7 @@ from the recurrences), the manufactured Hamilton-Jacobi problem's first-order
 convergence, and the L-infinity errors the paper prints for 5277^2 grids."""
 import math
 import os
+import pathlib
 
 import numpy as np
 import pytest
@@ -18,7 +19,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.txt")
 
 def _paper_numbers():
     out = {}
-    for line in open(GOLDEN):
+    for line in pathlib.Path(GOLDEN).read_text().splitlines():
         line = line.split("#")[0].split()
         if len(line) == 2:
             out[line[0]] = float(line[1])

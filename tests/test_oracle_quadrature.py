@@ -2,6 +2,7 @@
 the paper prints and against identities fixed by the mathematics."""
 import math
 import os
+import pathlib
 
 import numpy as np
 import pytest
@@ -17,7 +18,7 @@ def _poly(c, x):
 
 def _closed_forms():
     out = {}
-    for line in open(os.path.join(GOLDEN, "app_c_closed_forms.txt")):
+    for line in pathlib.Path(os.path.join(GOLDEN, "app_c_closed_forms.txt")).read_text().splitlines():
         line = line.strip()
         if not line or line.startswith("#"):
             continue
@@ -60,7 +61,7 @@ def test_printed_c_m1_0_is_garbled():
 
 def _linear_weight_forms():
     out = {}
-    for line in open(os.path.join(GOLDEN, "app_c_linear_weights.txt")):
+    for line in pathlib.Path(os.path.join(GOLDEN, "app_c_linear_weights.txt")).read_text().splitlines():
         line = line.strip()
         if not line or line.startswith("#"):
             continue
@@ -131,7 +132,7 @@ def test_moment_identities(npts, nu):
 
 def _printed_betas():
     rows = []
-    for line in open(os.path.join(GOLDEN, "app_c_smoothness.txt")):
+    for line in pathlib.Path(os.path.join(GOLDEN, "app_c_smoothness.txt")).read_text().splitlines():
         line = line.strip()
         if not line or line.startswith("#"):
             continue
