@@ -33,6 +33,9 @@
  *   - Every entry point returns a molt_status; nothing throws across the ABI.
  *     On failure, molt_last_error(ctx) describes the cause.  Unsupported
  *     combinations return MOLT_EUNSUPPORTED; there is no CPU fallback.
+ *   - Entry points whose comment cites no section have no counterpart in the
+ *     paper: lifecycle, options, profiling, tile planning, the allocation-free
+ *     wave step and the learned local-integral weights.
  */
 #ifndef MOLT_H
 #define MOLT_H
