@@ -21,6 +21,12 @@ what the paper states:
   operators and the stability bound on beta it implies.
 * ``mlp``         -- FP64 forward/backward of the WENO-weight network used by
   the learned weight path (no counterpart in the paper).
+* ``dense``       -- the partial sums of one axis as a dense matrix (the image
+  of the identity under ``sweep``), applied along the grid's axes by matrix
+  products: the linear schemes' steps at full grid sizes.
+* ``parallel``    -- ``sweep``'s partial sums on blocks of lines in a process
+  pool (lines are independent), and the Hamilton-Jacobi step composed from
+  them as ``schemes`` composes it.
 
 Every function cites the passage it follows.  Readings of garbled or silent
 passages are stated in the docstring of the function that takes them.
