@@ -262,9 +262,15 @@ typedef enum {
   MOLT_OPT_WAIT_LIMIT = 2,        /* cycles a device-side wait may take before the
                                      kernel records MOLT_ETIMEOUT and returns
                                      (default 2e9, >= 1000)                      */
-  MOLT_OPT_TEST_SKIP_ARRIVE = 3   /* test hook: 1 makes one CTA of the batched step
+  MOLT_OPT_TEST_SKIP_ARRIVE = 3,  /* test hook: 1 makes one CTA of the batched step
                                      skip its first grid barrier, so the others'
                                      bounded waits run out (MOLT_ETIMEOUT)       */
+  MOLT_OPT_LANES = 4              /* line-per-lane FP32 sweeps (one lane per line,
+                                     one warp per 16-point segment, difference
+                                     form of the recurrences): 1 (default) when
+                                     the line shape allows and nu*16 >= ~3.5;
+                                     2 whenever the shape allows; 0 never.
+                                     Both kernels compute the same values      */
 } molt_option;
 molt_status molt_set_option(molt_ctx* ctx, int option, int64_t value);
 
@@ -281,12 +287,16 @@ typedef enum {
   MOLT_KERNEL_BATCH = 8,       /* one persistent batched heat step            */
   MOLT_KERNEL_TRANSPOSE = 9,   /* state transposes of the 2-D Hamilton-Jacobi
                                   y pass on long lines                        */
-  MOLT_KERNEL_FLUX = 10        /* advection-diffusion: split fluxes g^+, g^-  */
+  MOLT_KERNEL_FLUX = 10,       /* advection-diffusion: split fluxes g^+, g^-  */
+  MOLT_KERNEL_LANES_STORE = 11,   /* line-per-lane sweeps (MOLT_OPT_LANES):      */
+  MOLT_KERNEL_LANES_ACC_SET = 12, /*   STORE, ACC_SET, and ACC_ADD / the        */
+  MOLT_KERNEL_LANES_ACC_ADD = 13  /*   advection-diffusion accumulations        */
 } molt_kernel_kind;
 
 /* With MOLT_OPT_PROFILE on: synchronises the stream, returns the summed
  * device time (ms) and count of the recorded launches of `kind`, and clears
- * every recorded launch.  Either output pointer may be NULL. */
+ * those records (setting MOLT_OPT_PROFILE, to either value, clears all
+ * records).  Either output pointer may be NULL. */
 molt_status molt_profile_read(molt_ctx* ctx, int kind, double* total_ms, int64_t* launches);
 
 /* One wave time step that allocates no device memory.  The paper has no
@@ -302,14 +312,19 @@ molt_status molt_profile_read(molt_ctx* ctx, int kind, double* total_ms, int64_t
  *   u, u_prev u^n and u^{n-1}: device arrays of doubles (u_prev unused and
  *             may be NULL when from_rest != 0).
  *   u_next    receives u^{n+1} = 2u^n - u^{n-1} - beta^2 sum_d S_{P,d}[u^n]
- *             (from_rest: u^n - beta^2/2 sum_d S_{P,d}[u^n]); must not alias
- *             u or u_prev.  All three 16-byte aligned.
+ *             (from_rest: u^n - beta^2/2 sum_d S_{P,d}[u^n]).  It may be
+ *             u_prev (the usual leapfrog rotation: each point of u^{n-1} is
+ *             read by the thread that then writes that point), never u
+ *             (MOLT_EINVAL).  All three 16-byte aligned.
  *   cuda_stream  cudaStream_t the work is enqueued on.
  * Scratch (the FP32 copy of u^n, the FP32 axis accumulator and a status
  * word, 8 MiB + 256 bytes) is a file-scope device array that every GPU
  * loading the library holds until the process exits.  The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress) with
- * the device current; make that first call before any stream capture.
+ * the device current, and looks it up again whenever the current CUDA
+ * context differs from the one it was looked up in (after cudaDeviceReset
+ * the module loads again and the array may move); make the first call on a
+ * device, and the first after a context reset, before any stream capture.
  * Every call on a device shares the array and clears the status word, so
  * calls that overlap on the GPU (other streams, other host threads) race.
  * Synchronous: returns after the step finished (MOLT_ENONFINITE if a

@@ -16,6 +16,7 @@
 #include "nonuniform.cuh"
 #include "molt.h"
 #include "sweep_launch.h"
+#include "sweep_lanes_launch.h"
 #include "batch.cuh"
 
 using namespace molt;
@@ -84,6 +85,7 @@ struct molt_ctx {
   double* t_dev = nullptr;         // per problem time (HJ)
   double* tnow_dev = nullptr;      // per problem time at the start of the step (HJ source)
   bool no_tma = false;             // force the plain kernels (molt_set_option)
+  int lanes = 1;                   // line-per-lane FP32 sweeps: 0 off, 1 auto, 2 whenever the shape allows
   void* mlp_blob = nullptr;        // learned weights: the BF16 network (MlpBlob)
   unsigned long long* mlp_stats = nullptr;  // [stencils evaluated, fallbacks]
   bool mlp_ready = false;          // molt_set_mlp has been called
@@ -436,9 +438,141 @@ cudaError_t launch(const Problem& p, int epi, const Plan& pl, cudaStream_t s, bo
   return dispatch_lin<float, float, double>(epi, pl, s);
 }
 
+// Line-per-lane FP32 sweeps (csrc/sweep_lanes.cuh): FP32 input, linear rule,
+// D_0 / D_R / D_L with P <= 2, lines of 16..512 points (multiples of 16) in
+// tiles of 32 lines, epilogues STORE (FP32 state), ACC_SET, ACC_ADD,
+// ACC_AXPY.  In auto mode they run when a segment's look-back reaches at most
+// kLanesAutoDepth segments (nu >= ~0.22 for 16-point segments): below that
+// the look-back grows with 1/nu while the scan kernel's cost does not.
+constexpr int kLanesAutoDepth = 8;
+constexpr double kLanesTailWeight = 9.094947017729282e-13;   // 2^-40
+
+bool plan_lanes(const molt_ctx* c, const Problem& p, int epi, const Plan& pl, bool f32_input, LanesArgs* la,
+                CUtensorMap* map) {
+  if (c->lanes == 0) return false;
+  const SweepArgs& a = pl.a;
+  if (compute_bytes(p.d) != 4 || !f32_input || p.d.weights != MOLT_W_LINEAR) return false;
+  if (!p.nodes[pl.ax].empty()) return false;
+  if (a.mode != MODE_0 && a.mode != MODE_R && a.mode != MODE_L) return false;
+  if (a.P < 1 || a.P > 2) return false;
+  if (epi != EPI_ACC_SET && epi != EPI_ACC_ADD && epi != EPI_ACC_AXPY && !(epi == EPI_STORE && is_f32_state(p.d)))
+    return false;
+  const int n = a.g.n;
+  if (n % kLE != 0 || n < kLE || n > kLE * kLMaxSeg) return false;
+  const void* outp = epi == EPI_STORE ? a.out : a.acc;
+  if (!a.in || !outp || ((reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(outp)) & 15)) return false;
+  LanesArgs L;
+  std::memset(&L, 0, sizeof(L));
+  L.n = n;
+  L.S = n / kLE;
+  L.bc = a.bc;
+  L.mode = a.mode;
+  L.P = a.P;
+  L.in = static_cast<const float*>(a.in);
+  L.out = static_cast<float*>(a.out);
+  L.acc = static_cast<float*>(a.acc);
+  L.coef = float(a.coefS);
+  L.status = a.status;
+  const int64_t nx = axis_n(p, 0), ny = axis_n(p, 1), nz = axis_n(p, 2);
+  std::memset(map, 0, sizeof(*map));
+  if (pl.ax == 0) {
+    if (a.g.nlines % kLW != 0) return false;
+    L.contiguous = 1;
+    L.LS = n + 4;
+    L.ntiles = a.g.nlines / kLW;
+  } else {
+    if (nx % kLW != 0) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    L.contiguous = 0;
+    L.kind = pl.ax;
+    L.tiles_per_row = nx / kLW;
+    L.ntiles = L.tiles_per_row * (pl.ax == 1 ? nz : ny);
+    L.s_hi = pl.ax == 1 ? nx * ny : nx;
+    L.stride = pl.ax == 1 ? nx : nx * ny;
+    L.nbox = n <= 256 ? 1 : 2;
+    L.box_p = n / L.nbox;
+    cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(ny), cuuint64_t(nz)};
+    cuuint64_t strides[2] = {cuuint64_t(nx * 4), cuuint64_t(nx * ny * 4)};
+    cuuint32_t box[3] = {cuuint32_t(kLW), pl.ax == 1 ? cuuint32_t(L.box_p) : 1u, pl.ax == 2 ? cuuint32_t(L.box_p) : 1u};
+    cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(a.in), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  if (L.ntiles < 1 || L.ntiles >= (1LL << 31)) return false;
+  // quadrature weights (FP64) and the FP32 decay the kernel runs
+  const double nu = a.alpha * p.h[pl.ax];
+  QuadTable qt;
+  if (!build_quadrature(p.d.quad_points, nu, &qt)) return false;
+  const float q32 = float(qt.q);
+  const double lq = std::log(double(q32));
+  L.q = q32;
+  L.qE = float(std::exp(lq * kLE));
+  // first-difference taps b_m, m = -2..2 (c[0..5] are the J_R weights on offsets -3..2)
+  const double* cw = qt.c;
+  const double b[5] = {cw[0], cw[0] + cw[1], cw[0] + cw[1] + cw[2] + qt.q, -(cw[4] + cw[5]), -cw[5]};
+  const double sR = a.mode == MODE_0 ? 0.5 : (a.mode == MODE_R ? 1.0 : 0.0);
+  const double sL = a.mode == MODE_0 ? -0.5 : (a.mode == MODE_L ? -1.0 : 0.0);
+  for (int i = 0; i < 5; ++i) {
+    L.bR[i] = float(sR * b[i]);
+    L.bL[i] = float(sL * b[i]);
+  }
+  // line constants C = kA T_same + kB T_other
+  if (a.bc == MOLT_BC_PERIODIC) {
+    L.kA = 1.0 / (-std::expm1(lq * n));
+    L.kB = 0.0;
+  } else if (a.mode == MODE_0) {
+    const double N = double(n - 1), mu = std::exp(lq * N);
+    const double k = 1.0 / (-std::expm1(2.0 * lq * N)) * std::exp(-lq);
+    L.kA = mu < kLanesTailWeight ? 0.0 : mu * k;
+    L.kB = -k;
+  } else {
+    L.kA = 0.0;
+    L.kB = 0.0;
+  }
+  L.needA = L.kA != 0.0;
+  L.needB = L.kB != 0.0;
+  // look-back depth: segment weights (q^16)^j >= 2^-40
+  double w = 1.0;
+  int lb = 0;
+  const double qE = std::exp(lq * kLE);
+  while (lb < L.S && w >= kLanesTailWeight) {
+    w *= qE;
+    ++lb;
+  }
+  L.lb = lb;
+  if (c->lanes == 1 && lb > kLanesAutoDepth) return false;
+  *la = L;
+  return true;
+}
+
 molt_status run(molt_ctx* c, const Problem& p, int epi, Plan& pl, bool from_state_copy = true) {
   // element size of the sweep input: FP64 except FP32 state or the FP32 copy
   const size_t in_bytes = is_f32_state(p.d) || (is_mixed(p.d) && from_state_copy) ? 4 : 8;
+  {
+    LanesArgs la;
+    CUtensorMap lmap;
+    if (plan_lanes(c, p, epi, pl, in_bytes == 4, &la, &lmap)) {
+      molt_ctx::Rec rec{epi == EPI_STORE ? int(MOLT_KERNEL_LANES_STORE)
+                                         : (epi == EPI_ACC_SET ? int(MOLT_KERNEL_LANES_ACC_SET)
+                                                               : int(MOLT_KERNEL_LANES_ACC_ADD)),
+                        nullptr, nullptr};
+      if (c->profile) {
+        cudaEventCreate(&rec.start);
+        cudaEventCreate(&rec.stop);
+        cudaEventRecord(rec.start, c->stream);
+      }
+      const cudaError_t e = launch_lanes(epi, la, lmap, c->stream);
+      if (c->profile) {
+        cudaEventRecord(rec.stop, c->stream);
+        c->recs.push_back(rec);
+      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "line-per-lane sweep launch");
+      return MOLT_OK;
+    }
+  }
   if (!c->no_tma && p.d.weights != MOLT_W_LEARNED) plan_tma(p, pl.ax, pl.a.in, in_bytes, &pl);
   // profiling kind: the general Hamilton-Jacobi passes count as HJ_X / HJ_Y
   // (the advection-diffusion accumulations count as ACC_ADD)
@@ -1874,15 +2008,23 @@ molt_status molt_set_grid_axis(molt_ctx* c, int problem, int axis, const double*
   return MOLT_OK;
 }
 
+static void clear_records(molt_ctx* c);
+
 molt_status molt_set_option(molt_ctx* c, int option, int64_t value) {
   if (!c) return fail(nullptr, MOLT_EINVAL, "null context");
   if (option == MOLT_OPT_WAIT_LIMIT) {
     if (value < 1000) return fail(c, MOLT_EINVAL, "wait limit below 1000 cycles");
     c->wait_limit = value;
+  } else if (option == MOLT_OPT_LANES) {
+    if (value < 0 || value > 2) return fail(c, MOLT_EINVAL, "MOLT_OPT_LANES takes 0, 1 or 2");
+    c->lanes = int(value);
   } else {
     if (value != 0 && value != 1) return fail(c, MOLT_EINVAL, "option value must be 0 or 1");
     if (option == MOLT_OPT_TMA) c->no_tma = value == 0;
-    else if (option == MOLT_OPT_PROFILE) c->profile = value == 1;
+    else if (option == MOLT_OPT_PROFILE) {
+      c->profile = value == 1;
+      clear_records(c);
+    }
     else if (option == MOLT_OPT_TEST_SKIP_ARRIVE) c->test_skip_arrive = value == 1;
     else return fail(c, MOLT_EINVAL, "unknown option");
   }
@@ -1919,15 +2061,21 @@ molt_status molt_profile_read(molt_ctx* c, int kind, double* total_ms, int64_t* 
   if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
   double tot = 0.0;
   int64_t cnt = 0;
+  std::vector<molt_ctx::Rec> keep;
   for (auto& r : c->recs) {
-    if (r.kind != kind) continue;
+    if (r.kind != kind) {
+      keep.push_back(r);
+      continue;
+    }
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.start, r.stop) == cudaSuccess) {
       tot += ms;
       ++cnt;
     }
+    if (r.start) cudaEventDestroy(r.start);
+    if (r.stop) cudaEventDestroy(r.stop);
   }
-  clear_records(c);
+  c->recs.swap(keep);
   if (total_ms) *total_ms = tot;
   if (launches) *launches = cnt;
   return MOLT_OK;

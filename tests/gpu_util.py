@@ -38,3 +38,44 @@ def tol_for(prec):
 def state_dtype(prec):
     from paper_2007_03041_gb300 import molt as M
     return torch.float32 if prec == M.PREC_F32 else torch.float64
+
+
+# Element-wise bound next to the relative L2 norm: the largest pointwise error
+# over the largest value.  An error confined to a few points of a long line
+# (the ghost-affected ends) is diluted in the L2 norm but not here.
+MAX_F64 = 1e-11
+MAX_F32 = 2e-5
+
+
+def max_for(prec):
+    from paper_2007_03041_gb300 import molt as M
+    return MAX_F64 if prec == M.PREC_F64 else MAX_F32
+
+
+def max_rel(got, want):
+    want = np.asarray(want)
+    den = np.abs(want).max() if want.size else 0.0
+    return np.abs(np.asarray(got) - want).max() / (den if den > 0 else 1.0) if want.size else 0.0
+
+
+def assert_parity(got, want, tol_l2, tol_max, line_axis=None, what=""):
+    """rel-L2 <= tol_l2, max-abs <= tol_max * max|want|, and the first and
+    last 4 points of every line along ``line_axis`` (numpy axis) held to the
+    same max-abs bound on their own."""
+    got = np.asarray(got)
+    want = np.asarray(want)
+    e2 = rel_l2(got, want)
+    em = max_rel(got, want)
+    assert e2 <= tol_l2, "%s rel-L2 %.3e > %.1e" % (what, e2, tol_l2)
+    assert em <= tol_max, "%s max-abs %.3e > %.1e (x max|want|)" % (what, em, tol_max)
+    if line_axis is not None and got.shape[line_axis] > 0:
+        den = np.abs(want).max()
+        den = den if den > 0 else 1.0
+        g = np.moveaxis(got, line_axis, -1)
+        w = np.moveaxis(want, line_axis, -1)
+        k = min(4, g.shape[-1])
+        for sl, name in ((np.s_[..., :k], "first"), (np.s_[..., -k:], "last")):
+            ee = np.abs(g[sl] - w[sl]).max() / den
+            assert ee <= tol_max, "%s %s %d points of the lines: %.3e > %.1e" % (what, name, k, ee, tol_max)
+    return e2, em
+
