@@ -10,10 +10,12 @@
 // every GPU that loads the library holds until the process exits.  The caller
 // passes u^n, u^{n-1} and the output u^{n+1}.  The sweep kernels are the ones
 // molt_step runs (plain one-tile-per-CTA variant).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "coeffs.h"
 #include "line_constants.h"
@@ -32,9 +34,67 @@ constexpr int kMaxDevices = 64;
 // Shared by every call on a device: status word, FP32 accumulator, FP32 copy.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Host-side device address of g_noalloc_scratch per device (the symbol's name
-// in host code is only a stand-in, never a device address).
-void* g_scratch_addr[kMaxDevices] = {nullptr};
+// Host-side device address of g_noalloc_scratch, looked up once per device
+// and CUDA context (the symbol's name in host code is only a stand-in, never
+// a device address).  The context is part of the key: after cudaDeviceReset,
+// or whenever the primary context is destroyed and created again, the module
+// loads again and the array may sit at another address, so a new context
+// means a new lookup.  The mutex orders first calls from several host threads.
+struct ScratchAddr {
+  CUcontext ctx = nullptr;
+  void* ptr = nullptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
+std::mutex g_scratch_mutex;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+
+// cuCtxGetCurrent through the runtime's driver entry point (the library does
+// not link the driver library itself).
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Device address of the scratch array for the current device and context;
+// nullptr on failure.
+void* scratch_address(int dev) {
+  CtxGetCurrentFn get = ctx_get_current();
+  CUcontext cur = nullptr;
+  if (!get || get(&cur) != CUDA_SUCCESS) return nullptr;
+  if (!cur) {
+    // no context current on this thread yet: the runtime's first call (the
+    // lookup itself) makes the device's primary context current
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    if (get(&cur) != CUDA_SUCCESS || !cur) return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  ScratchAddr& e = g_scratch_addr[dev];
+  if (e.ctx != cur || !e.ptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    e.ctx = cur;
+    e.ptr = p;
+  }
+  return e.ptr;
+}
 
 __global__ void noalloc_copy_kernel(const double* __restrict__ in, float* __restrict__ out, long long n) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -101,6 +161,7 @@ extern "C" molt_status molt_wave_step_noalloc(const molt_desc* d, const double* 
   if (d->ndim < 1 || d->ndim > 3 || d->P < 1 || d->P > 64 || !(d->dt > 0) || !(d->c > 0) || !(d->beta > 0))
     return MOLT_EINVAL;
   if (d->quad_points != 3 && d->quad_points != 5 && d->quad_points != 6) return MOLT_EINVAL;
+  if (u_next == u) return MOLT_EINVAL;   // u_next may be u_prev, never u^n itself
   long long total = 1;
   for (int ax = 0; ax < d->ndim; ++ax) {
     if (d->n[ax] < 2 || d->n[ax] > 8192) return MOLT_EINVAL;
@@ -113,18 +174,11 @@ extern "C" molt_status molt_wave_step_noalloc(const molt_desc* d, const double* 
       15)
     return MOLT_EINVAL;
 
-  // Set-up, once per device: the device address of the scratch array.
+  // Set-up, once per device and context: the device address of the scratch array.
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MOLT_ECUDA;
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return MOLT_ECUDA;
-    }
-    g_scratch_addr[dev] = p;
-  }
-  unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  unsigned char* base = static_cast<unsigned char*>(scratch_address(dev));
+  if (!base) return MOLT_ECUDA;
   int* status = reinterpret_cast<int*>(base);
   float* acc = reinterpret_cast<float*>(base + kStatusBytes);
   float* copy = acc + kNoAllocMaxPoints;
