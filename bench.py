@@ -7,13 +7,22 @@ quadrature, dt = 2h, beta = 0.8, sweeps in FP32 with the boundary solve and
 the leapfrog update in FP64; u0 = 16 seeded Gaussian bumps (synthetic).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--config C] [--headline-only]
 
-Prints one JSON line.  ``value`` is device-timed (inputs resident in HBM),
-``e2e`` goes through the same C-ABI call with pinned host buffers copied in
-and the new state copied out every step.  ``--impl reference`` times the FP64
-CPU oracle (numpy) on a bounded sample of the same workload.  Under torchrun
-(N > 1) every rank advances its own replica (the path does not shard across
-GPUs: replicas only); rank 0 prints.
+Prints one JSON line.  ``value`` is device-timed (inputs resident in HBM,
+no instrumentation in the timed region), ``e2e`` goes through the same C-ABI
+call with pinned host buffers copied in and the new state copied out every
+step.  ``error_vs_oracle`` states the error of the result against the FP64
+oracle: the first 10 steps on the full 512^3 grid and all 50 steps of the
+run on a 256^3 grid, both compared in full (the oracle's axis sums as dense
+matrices, oracle/dense.py).  Unless --headline-only, ``other_configs`` carries
+the lines of the other workloads (2-D heat 256^2 FP64, 64 batched heat
+problems, Hamilton-Jacobi 4096^2 WENO-Z, and 8192^2 with WENO-Z and with the
+learned weights), each with its own clock record, roofline, oracle error and
+speedup over the plain FP64 GPU form.  ``--impl reference`` times the FP64
+CPU oracle on the host's cores on a bounded sample of the wave workload.
+Under torchrun (N > 1) every rank advances its own replica (the path does not
+shard across GPUs: replicas only); rank 0 prints.
 """
 import argparse
 import json
@@ -33,6 +42,8 @@ QUAD = 6
 BETA = 0.8
 METRIC = "DOF updates/sec (3-D wave, 512^3, P=2) on GB300"
 UNIT = "DOF/s"
+TOL_F32 = 1e-5   # stated tolerance of the FP32-sweep forms (relative L2 vs the FP64 oracle)
+TOL_F64 = 1e-12  # FP64 forms
 WORKLOAD = {
     "workload": "wave3d_dirichlet_512^3_P2_quad6_beta0.8_dt2h",
     "grid": [N, N, N],
@@ -48,9 +59,10 @@ WORKLOAD = {
 BYTES_PER_DOF = {"x": 8, "yz": 12, "update": 32}
 LAUNCHES_PER_STEP = {"x": 1, "yz": 2, "update": 1}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per DOF per launch
-# from one ncu capture of these kernels on the 512 x 256 x 512 grid, scaled to
-# a full launch by the points processed (traffic grows with the points)
-TRAFFIC_PER_DOF = {"x": 7.31, "yz": 11.38, "update": 31.37}
+# from one ncu capture of each kernel on the 512 x 256 x 512 grid, scaled to a
+# full launch by the points processed (traffic grows with the points); a
+# kernel changed since its capture has no entry
+TRAFFIC_PER_DOF = {"wave_update_kernel (FP64 leapfrog update)": 31.37}
 
 
 def dist_env():
@@ -81,6 +93,7 @@ class ClockSampler:
                  "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+        time.sleep(0.3)
 
     def stop(self):
         if self.proc is None:
@@ -118,57 +131,156 @@ def measured_peaks():
         return None
 
 
-def cpu_oracle_sample(seconds_target=15.0, k=None):
-    """Times the FP64 oracle on a bounded sample: S_2 along x and y on k
-    complete z-planes of the 512^3 grid, S_2 along z on the same number of
-    complete z-lines, and the FP64 leapfrog update of those points.  Returns
-    (DOF/s, description, cores)."""
+def cpu_info():
+    """(cores, CPU model) of the host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return os.cpu_count() or 1, model
+
+
+def error_stats(got, want):
+    """Relative L2, largest pointwise error over the largest value, largest
+    pointwise error (numpy arrays)."""
+    import numpy as np
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    den = float(np.linalg.norm(want))
+    err = np.abs(got - want)
+    amax = float(np.abs(want).max()) if want.size else 0.0
+    return {"rel_l2": float(np.linalg.norm(got - want)) / (den if den > 0 else 1.0),
+            "linf_rel": float(err.max()) / (amax if amax > 0 else 1.0), "linf": float(err.max())}
+
+
+# ------------------------------------------------------------ oracle legs
+def _oracle_sample(k, pool=None):
+    """The FP64 oracle on a bounded sample of the wave workload: S_2 along x
+    and y on k complete z-planes of the 512^3 grid, S_2 along z on k x 512
+    complete z-lines, and the FP64 leapfrog update of those k x 512^2 points.
+    pool: an oracle.parallel.LinePool (lines split among its processes) or
+    None (one core).  Returns the elapsed seconds."""
     import numpy as np
     from oracle import sweep
     from paper_2007_03041_gb300 import workloads
     h = 1.0 / (N - 1)
     alpha = BETA / (2 * h)
     g = workloads.rng(7)
-    if k is None:
-        k = 2
     slab = g.standard_normal((k, N, N))
     zl = g.standard_normal((N, k, N))
+    ps = pool.partial_sum if pool is not None else sweep.partial_sum
     t0 = time.perf_counter()
-    sx = sweep.partial_sum(slab, 2, alpha, h, "0", "dirichlet", QUAD, P)
-    sy = sweep.partial_sum(slab, 1, alpha, h, "0", "dirichlet", QUAD, P)
-    sz = sweep.partial_sum(zl, 0, alpha, h, "0", "dirichlet", QUAD, P)
+    sx = ps(slab, 2, alpha, h, "0", "dirichlet", QUAD, P)
+    sy = ps(slab, 1, alpha, h, "0", "dirichlet", QUAD, P)
+    sz = ps(zl, 0, alpha, h, "0", "dirichlet", QUAD, P)
     new = 2.0 * slab - slab - BETA * BETA * (sx + sy + np.moveaxis(sz, 0, 1).reshape(slab.shape))
     el = time.perf_counter() - t0
     del new
-    pts = k * N * N
-    return pts / el, "S_2 along x, y on %d complete 512^2 z-planes, along z on %d complete z-lines, and the update " \
-                     "(%d DOF of the 512^3 grid)" % (k, k * N, pts), 1, el
+    return el
+
+
+def _sample_desc(k):
+    return ("S_2 along x and y on %d complete 512^2 z-planes, along z on %d complete z-lines, and the leapfrog "
+            "update (%d DOF of the 512^3 grid)" % (k, k * N, k * N * N))
+
+
+def cpu_baseline(budget_s=8.0):
+    """The oracle, as it stands, on the host: on every core (its lines split
+    among one process per core) and on one core."""
+    from oracle.parallel import LinePool
+    cores, model = cpu_info()
+    k_all = max(cores, 2)
+    with LinePool(cores) as pool:
+        _oracle_sample(1, pool)                  # worker start-up
+        pts, el, reps = 0, 0.0, 0
+        while el < budget_s or reps < 2:
+            el += _oracle_sample(k_all, pool)
+            pts += k_all * N * N
+            reps += 1
+    v_all = pts / el
+    pts1, el1, reps1 = 0, 0.0, 0
+    while el1 < budget_s / 2 or reps1 < 2:
+        el1 += _oracle_sample(1)
+        pts1 += N * N
+        reps1 += 1
+    return {"value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": model,
+            "sample": "%d repetitions of: %s; lines split among %d processes (one per core)"
+                      % (reps, _sample_desc(k_all), cores),
+            "one_core": {"value": pts1 / el1, "unit": UNIT, "cores": 1,
+                         "sample": "%d repetitions of: %s" % (reps1, _sample_desc(1))}}
 
 
 def run_reference(args):
+    """The FP64 oracle as it stands on the host's cores: each step is the
+    bounded sample above with as many z-planes as cores."""
+    from oracle.parallel import LinePool
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        cpu_oracle_sample(k=1)
-    tot_pts, tot_t = 0, 0.0
-    desc = None
-    for _ in range(args.steps):
-        v, desc, cores, el = cpu_oracle_sample(k=1)
-        tot_pts += N * N
-        tot_t += el
-    value = tot_pts / tot_t
+    cores, model = cpu_info()
+    k = max(cores, 2)
+    with LinePool(cores) as pool:
+        for _ in range(max(args.warmup, 1)):
+            _oracle_sample(k, pool)
+        tot = 0.0
+        for _ in range(args.steps):
+            tot += _oracle_sample(k, pool)
+    value = args.steps * k * N * N / tot
+    desc = _sample_desc(k) + "; lines split among %d processes (one per core)" % cores
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(WORKLOAD, sample=desc),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": model,
+                         "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
 
 
+def wave_error_vs_oracle(n, nsteps, stream):
+    """Runs the wave workload on an n^3 grid (the seeded bumps, from rest) for
+    nsteps steps and compares the final state in full with the FP64 oracle
+    (oracle/dense.py: the oracle's S_2 as per-axis matrices)."""
+    import numpy as np
+    import torch
+    from oracle import dense
+    from paper_2007_03041_gb300 import molt as M
+    from paper_2007_03041_gb300 import workloads
+    h = 1.0 / (n - 1)
+    dt = 2 * h
+    u0 = workloads.wave_bumps(n)
+    d = M.make_desc((n, n, n), bc=[M.BC_DIRICHLET] * 3, P=P, quad_points=QUAD, beta=BETA, pde=M.PDE_WAVE,
+                    c=1.0, dt=dt, prec=M.PREC_F32_F64UPDATE)
+    ctx = M.molt_create(d, stream)
+    try:
+        u = torch.tensor(u0, device="cuda")
+        up = torch.empty_like(u)
+        t = M.molt_step(ctx, u, up, nsteps=1, t=[0.0])
+        if nsteps > 1:
+            M.molt_step(ctx, u, up, nsteps=nsteps - 1, t=t)
+        got = u.cpu().numpy()
+        del u, up
+    finally:
+        M.molt_destroy(ctx)
+    t0 = time.perf_counter()
+    mats = dense.wave_matrices(u0.shape, [h] * 3, dt, 1.0, BETA, ["dirichlet"] * 3, QUAD, P)
+    prev, cur = None, u0
+    for k in range(nsteps):
+        prev, cur = cur, dense.wave_step(cur, prev, mats, BETA, from_rest=(k == 0))
+    out = error_stats(got, cur)
+    out.update(grid=[n, n, n], steps=nsteps, compared="every grid point", oracle_s=time.perf_counter() - t0,
+               tolerance_rel_l2=TOL_F32)
+    return out
+
+
+# ------------------------------------------------------------ headline
 def run_ours(args):
     import torch
     from paper_2007_03041_gb300 import molt as M
@@ -188,7 +300,8 @@ def run_ours(args):
                     c=1.0, dt=dt, prec=M.PREC_F32_F64UPDATE)
     stream = torch.cuda.current_stream(dev)
     ctx = M.molt_create(d, stream)
-    # synthetic initial state (16 seeded bumps; generated on the device)
+    # synthetic initial state (the seeded bumps of workloads.wave_bumps,
+    # evaluated on the device)
     cen, wid = workloads.wave_bump_params()
     xs = [torch.arange(m, device=dev, dtype=torch.float64) / (m - 1) for m in (nx, ny, nz)]
     u = torch.zeros((nz, ny, nx), device=dev, dtype=torch.float64)
@@ -232,8 +345,6 @@ def run_ours(args):
 
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(0.3)
-    M.molt_set_option(ctx, M.OPT_PROFILE, 1)
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -242,25 +353,29 @@ def run_ours(args):
     ev1.record(stream)
     barrier()
     ms = ev0.elapsed_time(ev1)
-    # launch events of the timed region (sweeps along y and z, the largest
-    # share of the step; molt_profile_read clears all records)
-    yz_ms, yz_cnt = M.molt_profile_read(ctx, M.KERNEL_ACC_ADD)
-    M.molt_set_option(ctx, M.OPT_PROFILE, 0)
     clk = clocks.stop()
     if dist:
         tt = torch.tensor([ms], device=dev)
         tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
         ms = float(tt.item())
 
-    # per-kernel averages: y/z from the timed region, the others from runs of
-    # the same length
-    per_kernel = {"yz": yz_ms / max(yz_cnt, 1)}
-    for name, kind in (("x", M.KERNEL_ACC_SET), ("update", M.KERNEL_UPDATE)):
-        M.molt_set_option(ctx, M.OPT_PROFILE, 1)
-        t = M.molt_step(ctx, u, up, nsteps=args.steps, t=t)
-        tot, cnt = M.molt_profile_read(ctx, kind)
-        M.molt_set_option(ctx, M.OPT_PROFILE, 0)
-        per_kernel[name] = tot / max(cnt, 1)
+    # per-kernel averages from a second run of the same length with an event
+    # pair around every launch (the headline region above runs without them)
+    M.molt_set_option(ctx, M.OPT_PROFILE, 1)
+    t = M.molt_step(ctx, u, up, nsteps=args.steps, t=t)
+    per_kernel, kernel_names = {}, {}
+    for name, kinds in (("x", ((M.KERNEL_LANES_ACC_SET, "lanes_sweep_kernel ACC_SET (x lines)"),
+                               (M.KERNEL_ACC_SET, "sweep_tma_kernel ACC_SET (x lines)"))),
+                        ("yz", ((M.KERNEL_LANES_ACC_ADD, "lanes_sweep_kernel ACC_ADD (y and z lines)"),
+                                (M.KERNEL_ACC_ADD, "sweep_tma_kernel ACC_ADD (y and z lines)"))),
+                        ("update", ((M.KERNEL_UPDATE, "wave_update_kernel (FP64 leapfrog update)"),))):
+        for kind, kname in kinds:
+            tot, cnt = M.molt_profile_read(ctx, kind)
+            if cnt:
+                per_kernel[name] = tot / cnt
+                kernel_names[name] = kname
+                break
+    M.molt_set_option(ctx, M.OPT_PROFILE, 0)
 
     # end to end: every step copies its inputs (u^n, u^{n-1}) in from pinned
     # host memory and its result u^{n+1} back out.  Two device buffer sets
@@ -268,50 +383,53 @@ def run_ours(args):
     # of step k's result run on their own streams, overlapping step k's (or
     # k+1's) sweeps; each step is an independent problem read from the host.
     e2e_steps = 0 if args.no_e2e else max(4, min(args.steps, 8))
-    hu = torch.empty_like(u, device="cpu").pin_memory()
-    hup = torch.empty_like(u, device="cpu").pin_memory()
-    hout = [torch.empty_like(u, device="cpu").pin_memory() for _ in range(2)]
-    hu.copy_(u)
-    hup.copy_(up)
-    bufs = [(u, up), (torch.empty_like(u), torch.empty_like(u))]
-    s_in = torch.cuda.Stream(dev)
-    s_out = torch.cuda.Stream(dev)
-    ev_in = [torch.cuda.Event() for _ in range(2)]
-    ev_done = [torch.cuda.Event() for _ in range(2)]
-    ev_free = [torch.cuda.Event() for _ in range(2)]
+    e2e_s = 1e-9
+    if e2e_steps:
+        hu = torch.empty_like(u, device="cpu").pin_memory()
+        hup = torch.empty_like(u, device="cpu").pin_memory()
+        hout = [torch.empty_like(u, device="cpu").pin_memory() for _ in range(2)]
+        hu.copy_(u)
+        hup.copy_(up)
+        bufs = [(u, up), (torch.empty_like(u), torch.empty_like(u))]
+        s_in = torch.cuda.Stream(dev)
+        s_out = torch.cuda.Stream(dev)
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_done = [torch.cuda.Event() for _ in range(2)]
+        ev_free = [torch.cuda.Event() for _ in range(2)]
 
-    def copy_in(b):
-        with torch.cuda.stream(s_in):
-            s_in.wait_event(ev_free[b])
-            bufs[b][0].copy_(hu, non_blocking=True)
-            bufs[b][1].copy_(hup, non_blocking=True)
-            ev_in[b].record(s_in)
+        def copy_in(b):
+            with torch.cuda.stream(s_in):
+                s_in.wait_event(ev_free[b])
+                bufs[b][0].copy_(hu, non_blocking=True)
+                bufs[b][1].copy_(hup, non_blocking=True)
+                ev_in[b].record(s_in)
 
-    def pipelined(nsteps, t):
-        for b in range(2):
-            ev_free[b].record(s_out)
-        if nsteps:
-            copy_in(0)
-        for k in range(nsteps):
-            b = k % 2
-            if k + 1 < nsteps:
-                copy_in(1 - b)
-            stream.wait_event(ev_in[b])
-            t = M.molt_step(ctx, bufs[b][0], bufs[b][1], nsteps=1, t=t)
-            ev_done[b].record(stream)
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(ev_done[b])
-                hout[b].copy_(bufs[b][0], non_blocking=True)
+        def pipelined(nsteps, t):
+            for b in range(2):
                 ev_free[b].record(s_out)
-        torch.cuda.synchronize()
-        return t
+            if nsteps:
+                copy_in(0)
+            for k in range(nsteps):
+                b = k % 2
+                if k + 1 < nsteps:
+                    copy_in(1 - b)
+                stream.wait_event(ev_in[b])
+                t = M.molt_step(ctx, bufs[b][0], bufs[b][1], nsteps=1, t=t)
+                ev_done[b].record(stream)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(ev_done[b])
+                    hout[b].copy_(bufs[b][0], non_blocking=True)
+                    ev_free[b].record(s_out)
+            torch.cuda.synchronize()
+            return t
 
-    t = pipelined(2 if e2e_steps else 0, t)    # warm-up of the copy path
-    barrier()
-    e0 = time.perf_counter()
-    t = pipelined(e2e_steps, t)
-    barrier()
-    e2e_s = max(time.perf_counter() - e0, 1e-9)
+        t = pipelined(2, t)    # warm-up of the copy path
+        barrier()
+        e0 = time.perf_counter()
+        t = pipelined(e2e_steps, t)
+        barrier()
+        e2e_s = max(time.perf_counter() - e0, 1e-9)
+        del hu, hup, hout, bufs
     M.molt_destroy(ctx)
 
     dof = nx * ny * nz
@@ -326,27 +444,19 @@ def run_ours(args):
     share = {k: per_kernel[k] * LAUNCHES_PER_STEP[k] for k in per_kernel}
     dom = max(share, key=share.get)
     achieved = BYTES_PER_DOF[dom] * dof / (per_kernel[dom] / 1e3) / 1e9
-    names = {"x": "sweep_tma_kernel ACC_SET (x lines)", "yz": "sweep_tma_kernel ACC_ADD (y and z lines)",
-             "update": "wave_update_kernel (FP64 leapfrog update)"}
+    traffic = TRAFFIC_PER_DOF.get(kernel_names[dom])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_PER_DOF.get(dom) and TRAFFIC_PER_DOF[dom] * dof,
-                "kernel": names[dom], "peak_source": "measured" if peaks else "fallback",
-                "per_kernel_ms": per_kernel,
+                "traffic": traffic and traffic * dof,
+                "kernel": kernel_names[dom], "peak_source": "measured" if peaks else "fallback",
+                "per_kernel_ms": per_kernel, "per_kernel_name": kernel_names,
                 "per_kernel_gbs": {k: BYTES_PER_DOF[k] * dof / (per_kernel[k] / 1e3) / 1e9 for k in per_kernel},
-                "algorithmic_bytes_per_dof": BYTES_PER_DOF}
+                "per_kernel_frac": {k: BYTES_PER_DOF[k] * dof / (per_kernel[k] / 1e3) / 1e9 / peak
+                                    for k in per_kernel},
+                "algorithmic_bytes_per_dof": BYTES_PER_DOF,
+                "step_bytes_per_dof": sum(BYTES_PER_DOF[k] * LAUNCHES_PER_STEP[k] for k in BYTES_PER_DOF),
+                "per_kernel_source": "CUDA events around each launch, a second run of the same length"}
     if rank != 0:
-        return
-    cpu = None
-    if ws == 1 and not args.no_cpu:
-        # repeat the one-plane sample for about 10 s of CPU work
-        pts, el_tot, reps = 0, 0.0, 0
-        while el_tot < 10.0 or reps < 3:
-            v, desc, cores, el = cpu_oracle_sample(k=1)
-            pts += N * N
-            el_tot += el
-            reps += 1
-        cpu = {"value": pts / el_tot, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "%d repetitions of: %s" % (reps, desc)}
+        return None
     compare = None
     if args.compare:
         nst = max(2, min(args.steps, 10))
@@ -355,6 +465,14 @@ def run_ours(args):
         compare = {"fp64_value": dof / (ms64 / 1e3), "fp64_ms_per_step": ms64, "mixed_ms_per_step": ms32,
                    "speedup": ms64 / ms32, "steps_compared": nst + 1,
                    "rel_l2_vs_fp64": float(torch.linalg.norm(a32 - a64) / torch.linalg.norm(a64))}
+        del a32, a64
+    del u, up, u0
+    torch.cuda.empty_cache()
+    err = None
+    if not args.no_oracle and ws == 1 and [nx, ny, nz] == [N, N, N]:
+        err = {"full_grid_first_steps": wave_error_vs_oracle(N, 10, stream),
+               "half_grid_whole_run": wave_error_vs_oracle(N // 2, 50, stream)}
+    cpu = cpu_baseline() if (ws == 1 and not args.no_cpu) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -362,24 +480,27 @@ def run_ours(args):
         "config": dict(WORKLOAD, grid=[nx, ny, nz], parallelism="replicas" if ws > 1 else "1gpu"),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": 4 * args.steps + 1, "clocks": clk,
+        "error_vs_oracle": err,
     }
     if compare:
         line["vs_plain_fp64_gpu"] = compare
-    print(json.dumps(line))
+    return line
 
 
 # --------------------------------------------------------------- other configs
 # The default line is the 3-D wave workload above.  ``--config`` times the other
 # workloads of the method on the same contract (device-timed DOF/s, step-level
-# algorithmic bytes), and ``--compare`` adds the plain FP64 GPU form of the
-# same problem: its DOF/s, the speedup of the measured form over it, and the
-# relative L2 difference of the two final states.
+# algorithmic bytes, a clock record), with the error against the FP64 oracle
+# and the plain FP64 GPU form of the same problem (its DOF/s, the speedup of
+# the measured form over it, the relative L2 difference of the final states).
 CONFIGS = {
     "heat256": dict(metric="DOF updates/sec (2-D heat, 256^2, P=3, FP64, SSP-RK3) on GB300",
                     bytes_per_dof=168, bound="latency", dtype="f64"),
     "batch64": dict(metric="DOF updates/sec (64 batched 2-D heat problems, sides 128..2048, P=3) on GB300",
                     bytes_per_dof=156, bound="hbm", dtype="f32"),
     "hj4096": dict(metric="DOF updates/sec (2-D Hamilton-Jacobi, 4096^2, WENO-Z, FP32) on GB300",
+                   bytes_per_dof=20, bound="hbm", dtype="f32"),
+    "hj8192": dict(metric="DOF updates/sec (2-D Hamilton-Jacobi, 8192^2, WENO-Z, FP32) on GB300",
                    bytes_per_dof=20, bound="hbm", dtype="f32"),
     "hj8192_learned": dict(metric="DOF updates/sec (2-D Hamilton-Jacobi, 8192^2, learned WENO weights, FP32) on GB300",
                            bytes_per_dof=20, bound="tensor+alu", dtype="f32"),
@@ -452,7 +573,7 @@ def _problem(config, prec=None):
                              prec=M.PREC_F32_F64UPDATE if prec is None else prec) for n in sides]
         return descs, workloads.batched_heat(sides=sides)
     n = 4096 if config == "hj4096" else 8192
-    weights = M.W_WENOZ if config == "hj4096" else M.W_LEARNED
+    weights = M.W_LEARNED if config == "hj8192_learned" else M.W_WENOZ
     if prec == M.PREC_F64:
         weights = M.W_WENOZ
     seed = workloads.SEED_HJ if config == "hj4096" else workloads.SEED_HJ_LARGE
@@ -461,14 +582,16 @@ def _problem(config, prec=None):
     return [d], [workloads.hj_initial(n, seed=seed)]
 
 
-def _timed_steps(config, steps, warmup, prec=None, blob=None, profile_kinds=()):
+def _timed_steps(config, steps, warmup, prec=None, blob=None, profile_kinds=(), clocks=False):
     """Runs a config on the device: returns (ms per step, final states (device
-    tensors), per-kind device ms per step, learned-weight stats)."""
+    tensors), per-kind device ms per step, learned-weight stats, clock record
+    of the timed region)."""
     import torch
     from paper_2007_03041_gb300 import molt as M
     descs, u0 = _problem(config, prec)
     f32 = descs[0].prec == M.PREC_F32
     stream = torch.cuda.Stream()
+    clk = None
     with torch.cuda.stream(stream):
         ctx = M.molt_create(descs, stream)
         try:
@@ -483,28 +606,152 @@ def _timed_steps(config, steps, warmup, prec=None, blob=None, profile_kinds=()):
             if blob is not None and descs[0].weights == M.W_LEARNED:
                 M.molt_mlp_stats(ctx, reset=True)
             stream.synchronize()
+            sampler = ClockSampler(0) if clocks else None
+            if sampler:
+                sampler.start()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             t = M.molt_step(ctx, us, None, nsteps=steps, t=t)
             e1.record(stream)
             stream.synchronize()
+            if sampler:
+                clk = sampler.stop()
             ms = e0.elapsed_time(e1) / steps
             stats = M.molt_mlp_stats(ctx) if (blob is not None and descs[0].weights == M.W_LEARNED) else None
             # per-kind device times from a separate profiled run of the same
             # length (event pairs around each launch; no graph replay)
             kinds = {}
-            for name, kind in profile_kinds:
+            if profile_kinds:
                 M.molt_set_option(ctx, M.OPT_PROFILE, 1)
                 pu = [x.clone() for x in us]
                 M.molt_step(ctx, pu, None, nsteps=steps, t=list(t))
-                tot, cnt = M.molt_profile_read(ctx, kind)
+                for name, kind in profile_kinds:
+                    tot, cnt = M.molt_profile_read(ctx, kind)
+                    if cnt:
+                        kinds[name] = tot / steps
                 M.molt_set_option(ctx, M.OPT_PROFILE, 0)
-                kinds[name] = tot / steps
                 del pu
         finally:
             M.molt_destroy(ctx)
-    return ms, us, kinds, stats
+    return ms, us, kinds, stats, clk
+
+
+def _rk3(z):
+    return 1.0 + z + z * z / 2.0 + z ** 3 / 6.0
+
+
+def _modal_heat(n, seed, nsteps, iy, ix, beta=0.6, npts=3, P=3):
+    """Closed-form discrete solution of the periodic heat step (dt = h/2) at
+    the points (iy, ix): every Fourier mode of u0 is multiplied by the RK3
+    polynomial of its exact discrete symbol (oracle/stability.py) per step.
+    The oracle's line-by-line step matches it to 1e-14 (tests/test_oracle_schemes.py)."""
+    import math
+    import numpy as np
+    from oracle import stability
+    from paper_2007_03041_gb300 import workloads
+    k, a = workloads.heat_mode_params(seed)
+    h = 1.0 / n
+    nu = beta / math.sqrt(h / 2) * h
+    out = np.zeros(len(ix))
+    for (kx, ky), am in zip(k, a):
+        tx, ty = 2 * np.pi * kx / n, 2 * np.pi * ky / n
+        z = -beta ** 2 * (stability.partial_sum_symbol(tx, nu, "0", npts, P).real
+                          + stability.partial_sum_symbol(ty, nu, "0", npts, P).real)
+        out += am * _rk3(z) ** nsteps * np.cos(tx * ix + ty * iy)
+    return out
+
+
+def _hj_first_step_error(n, seed, weights, blob=None, theta=None, samples=256):
+    """Error of u^1 of the 2-D Hamilton-Jacobi run at sampled points against
+    the oracle, which needs only the x and y lines of u^0 through each point
+    (weights "wenoz" or "learned" with the same BF16 network)."""
+    import math
+    import numpy as np
+    import torch
+    from oracle import mlp, schemes, sweep
+    from oracle.quadrature import QuadratureRule
+    from paper_2007_03041_gb300 import molt as M
+    from paper_2007_03041_gb300 import workloads
+    h = 2 * math.pi / n
+    u0 = workloads.hj_initial(n, seed=seed).astype(np.float32)
+    d = M.make_desc((n, n), lo=[0, 0], hi=[2 * math.pi] * 2, P=1, quad_points=5,
+                    weights=M.W_LEARNED if weights == "learned" else M.W_WENOZ, beta=1.0, pde=M.PDE_HJ, cfl=1.5,
+                    dt=0.0, prec=M.PREC_F32)
+    ctx = M.molt_create(d)
+    try:
+        if blob is not None:
+            M.molt_set_mlp(ctx, blob)
+        u = torch.tensor(u0, device="cuda")
+        t = M.molt_step(ctx, u, None, nsteps=1, t=[0.0])
+        u1 = u.cpu().numpy()
+    finally:
+        M.molt_destroy(ctx)
+    g = workloads.rng(5)
+    iy, ix = g.integers(0, n, samples), g.integers(0, n, samples)
+    alpha = 1.0 / (1.5 * h)
+    fn = None
+    if weights == "learned":
+        fn = mlp.learned_weight_fn(np.asarray(theta, dtype=np.float64), QuadratureRule(1.0 / 1.5, 5),
+                                   emulate_bf16=True)
+    u064 = u0.astype(np.float64)
+    ders = []
+    for lines, pos in ((u064[iy, :], ix), (u064[:, ix].T, iy)):
+        dm = alpha * sweep.partial_sum(lines, 1, alpha, h, "R", "periodic", 5, 1, weights, fn)
+        dp = -alpha * sweep.partial_sum(lines, 1, alpha, h, "L", "periodic", 5, 1, weights, fn)
+        r = np.arange(len(pos))
+        ders.append((dm[r, pos], dp[r, pos]))
+    Hh, _ = schemes.hj_hamiltonian(ders)
+    want = u064[iy, ix] - t[0] * Hh
+    out = error_stats(u1[iy, ix], want)
+    inc = error_stats(u1[iy, ix].astype(np.float64) - u064[iy, ix], -t[0] * Hh)
+    out.update(steps=1, grid=[n, n], compared="%d sampled points (the x and y lines of u^0 through each)" % samples,
+               increment_rel_l2=inc["rel_l2"], tolerance_rel_l2=TOL_F32,
+               note="dt is the device's lagged step (the oracle step uses the same dt)")
+    return out
+
+
+def _hj_first_steps_error(n, seed, nsteps):
+    """Error after the first nsteps steps of the 2-D Hamilton-Jacobi run
+    (WENO-Z, FP32) against the oracle on the whole grid (the oracle's line
+    sums split among one process per core)."""
+    import math
+    import numpy as np
+    import torch
+    from oracle.parallel import LinePool
+    from paper_2007_03041_gb300 import molt as M
+    from paper_2007_03041_gb300 import workloads
+    h = 2 * math.pi / n
+    u0 = workloads.hj_initial(n, seed=seed).astype(np.float32)
+    d = M.make_desc((n, n), lo=[0, 0], hi=[2 * math.pi] * 2, P=1, quad_points=5, weights=M.W_WENOZ, beta=1.0,
+                    pde=M.PDE_HJ, cfl=1.5, dt=0.0, prec=M.PREC_F32)
+    ctx = M.molt_create(d)
+    try:
+        u = torch.tensor(u0, device="cuda")
+        t = M.molt_step(ctx, u, None, nsteps=nsteps, t=[0.0])
+        got = u.cpu().numpy()
+    finally:
+        M.molt_destroy(ctx)
+    t0 = time.perf_counter()
+    uu = u0.astype(np.float64)
+    tt = 0.0
+    with LinePool() as pool:
+        sp = pool.hj_initial_speeds(uu, [h, h])
+        for _ in range(nsteps):
+            uu, dt, sp = pool.hj_step(uu, [h, h], sp)
+            tt += dt
+    out = error_stats(got, uu)
+    out.update(steps=nsteps, grid=[n, n], compared="every grid point", t_gpu=t[0], t_oracle=tt,
+               oracle_s=time.perf_counter() - t0, tolerance_rel_l2=TOL_F32)
+    return out
+
+
+# FP32-issue bound of the Hamilton-Jacobi WENO-Z steps: thread instructions
+# per DOF and step of the sweeps (x pass 204, y pass on the transposed state
+# 232, from one ncu capture at 4096^2) against 128 thread instructions per SM
+# per cycle (4 schedulers x 32 lanes) x 152 SMs x 2070 MHz
+HJ_INST_PER_DOF = 436.0
+ISSUE_PEAK_GINST = 128 * 152 * 2.070
 
 
 # Sec. 5.1 figure caption: L-infinity errors on the 5277^2 grid
@@ -609,101 +856,166 @@ def run_nonuniform(args):
                      "peak_source": "measured" if peaks else "fallback"},
         "gpu_launches": 4 * args.steps, "clocks": clk,
     }
-    print(json.dumps(line))
+    return line
 
 
-def run_config(args):
+def config_line(name, steps, warmup, compare=True, error=True, size=None):
     import torch
     from paper_2007_03041_gb300 import molt as M
+    from paper_2007_03041_gb300 import workloads
     global PAPER_N
-    if args.size:
-        PAPER_N = args.size
-    cfg = dict(CONFIGS[args.config])
-    if args.config.startswith("paper_ex"):
+    if size:
+        PAPER_N = size
+    cfg = dict(CONFIGS[name])
+    if name.startswith("paper_ex"):
         cfg["metric"] = cfg["metric"].replace("5277^2", "%d^2" % PAPER_N)
-    descs, _ = _problem(args.config)
+    descs, u0s = _problem(name)
     dof = sum(int(d.n[0] * d.n[1] * d.n[2]) for d in descs)
     extra = {}
-    blob = None
-    if args.config == "hj8192_learned":
+    blob = theta = None
+    if name == "hj8192_learned":
         from paper_2007_03041_gb300 import learned
         t0 = time.perf_counter()
         x, y, dlin = learned.harvest(n=4096, steps=500, snapshots=5, count=10_000_000)
         t1 = time.perf_counter()
         xe, ye = x[-500_000:], y[-500_000:]
-        _, blob, hist = learned.train(x[:-500_000], y[:-500_000], epochs=3, batch=16384, lr=3e-3, lr_final=3e-4)
+        theta, blob, hist = learned.train(x[:-500_000], y[:-500_000], epochs=3, batch=16384, lr=3e-3, lr_final=3e-4)
         t2 = time.perf_counter()
         loss, fb = learned.evaluate(blob, xe, ye, dlin)
         extra["training"] = {"stencils": int(x.shape[0]), "harvest_s": t1 - t0, "train_s": t2 - t1,
                              "epochs": 3, "batch": 16384, "heldout_loss": loss, "heldout_fallback": fb,
                              "source": "4096^2 WENO-Z Hamilton-Jacobi run, 500 steps, 5 snapshots"}
-        del x, y
+        del x, y, xe, ye
     kinds = {"heat256": (("sweep_final", M.KERNEL_HEAT_FINAL), ("sweep_acc", M.KERNEL_ACC_SET)),
              "batch64": (("batch_step", M.KERNEL_BATCH),),
-             "hj4096": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y)),
-             "hj8192_learned": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y)),
+             "hj4096": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y), ("transpose", M.KERNEL_TRANSPOSE)),
+             "hj8192": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y), ("transpose", M.KERNEL_TRANSPOSE)),
+             "hj8192_learned": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y), ("transpose", M.KERNEL_TRANSPOSE)),
              "paper_ex1_advection": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y),
                                      ("transpose", M.KERNEL_TRANSPOSE)),
              "paper_ex2_diffusion": (("sweep_final", M.KERNEL_HEAT_FINAL), ("sweep_acc", M.KERNEL_ACC_SET)),
              "advdiff_burgers4096": (("flux", M.KERNEL_FLUX), ("sweeps", M.KERNEL_ACC_ADD),
-                                     ("update", M.KERNEL_UPDATE)),
-             "paper_ex3_hj": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y))}[args.config]
-    ms, us, per_kind, stats = _timed_steps(args.config, args.steps, args.warmup, blob=blob, profile_kinds=kinds)
+                                     ("sweeps_lanes", M.KERNEL_LANES_ACC_ADD), ("update", M.KERNEL_UPDATE)),
+             "paper_ex3_hj": (("hj_x", M.KERNEL_HJ_X), ("hj_y", M.KERNEL_HJ_Y))}[name]
+    ms, us, per_kind, stats, clk = _timed_steps(name, steps, warmup, blob=blob, profile_kinds=kinds, clocks=True)
     value = dof / (ms / 1e3)
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = cfg["bytes_per_dof"] * dof / (ms / 1e3) / 1e9
-    if cfg["bound"] == "fp64":
-        ach = cfg["fp64_inst_per_dof"] * dof / (ms / 1e3) / 1e9
-        roof = {"bound": "fp64", "achieved": ach, "peak": FP64_PEAK_GINST,
-                "unit": "G FP64 thread-instructions/s", "frac": ach / FP64_PEAK_GINST,
-                "traffic": cfg["dram_per_dof"] * dof, "scope": "whole step",
-                "fp64_inst_per_dof_step": cfg["fp64_inst_per_dof"],
-                "hbm_gbs_algorithmic": achieved, "per_kind_ms_per_step": None,
-                "peak_source": "nominal (ncu sustained FP64 rate x maximum SM clock)"}
     line = {
-        "metric": cfg["metric"], "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "metric": cfg["metric"], "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": cfg["dtype"], "data": "synthetic",
-        "config": {"workload": args.config, "dof": dof},
+        "config": {"workload": name, "dof": dof},
         "roofline": {"bound": cfg["bound"], "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "scope": "whole step, algorithmic bytes",
                      "algorithmic_bytes_per_dof_step": cfg["bytes_per_dof"],
                      "per_kind_ms_per_step": per_kind,
                      "peak_source": "measured" if peaks else "fallback"},
+        "clocks": clk,
     }
     if cfg["bound"] == "fp64":
-        roof["per_kind_ms_per_step"] = per_kind
-        line["roofline"] = roof
-    if args.config.startswith("paper_ex") and PAPER_N == 5277:
-        err, tf, nst = _paper_final_error(args.config)
+        ach = cfg["fp64_inst_per_dof"] * dof / (ms / 1e3) / 1e9
+        line["roofline"] = {"bound": "fp64", "achieved": ach, "peak": FP64_PEAK_GINST,
+                            "unit": "G FP64 thread-instructions/s", "frac": ach / FP64_PEAK_GINST,
+                            "traffic": cfg["dram_per_dof"] * dof, "scope": "whole step",
+                            "fp64_inst_per_dof_step": cfg["fp64_inst_per_dof"],
+                            "hbm_gbs_algorithmic": achieved, "per_kind_ms_per_step": per_kind,
+                            "peak_source": "nominal (ncu sustained FP64 rate x maximum SM clock)"}
+    if name in ("hj4096", "hj8192"):
+        ach = HJ_INST_PER_DOF * dof / (ms / 1e3) / 1e9
+        line["roofline"]["issue_bound"] = {"achieved": ach, "peak": ISSUE_PEAK_GINST,
+                                          "unit": "G thread-instructions/s", "frac": ach / ISSUE_PEAK_GINST,
+                                          "inst_per_dof_step": HJ_INST_PER_DOF,
+                                          "note": "instruction issue binds before HBM for WENO-Z"}
+    # error of the result against the FP64 oracle
+    if error:
+        import numpy as np
+        if name == "heat256":
+            # relative error after 10 steps (the slowest mode keeps 2% of its
+            # amplitude), and after the whole run (every mode has decayed to
+            # the rounding level) against the initial amplitude
+            from oracle import dense
+            n = int(descs[0].n[0])
+            mats = dense.heat_matrices((n, n), [1.0 / n] * 2, 0.5 / n, 1.0, 0.6, None, 3, 3)
+            ms10, us10 = _timed_steps(name, 10, 0)[:2]
+            w = u0s[0]
+            w10 = None
+            for k in range(warmup + steps):
+                w = dense.heat_step(w, mats, 0.6)
+                if k == 9:
+                    w10 = w
+            e = error_stats(us10[0].cpu().numpy(), w10)
+            ef = error_stats(us[0].cpu().numpy(), w)
+            e.update(steps=10, grid=[n, n], compared="every grid point", tolerance_rel_l2=TOL_F64,
+                     whole_run={"steps": warmup + steps,
+                                "linf_vs_initial_amplitude": ef["linf"] / float(np.abs(u0s[0]).max())})
+            line["error_vs_oracle"] = e
+        elif name == "batch64":
+            g = workloads.rng(77)
+            gots, wants, worst = [], [], 0.0
+            for i, (n, a0, x) in enumerate(zip([int(d.n[0]) for d in descs], u0s, us)):
+                iy, ix = g.integers(0, n, 256), g.integers(0, n, 256)
+                want = _modal_heat(n, 3000 + i, warmup + steps, iy, ix)
+                got = x.cpu().numpy()[iy, ix]
+                gots.append(got)
+                wants.append(want)
+                worst = max(worst, float(np.abs(got - want).max()) / float(np.abs(a0).max()))
+            e = error_stats(np.concatenate(gots), np.concatenate(wants))
+            e.update(steps=warmup + steps, problems=len(descs), tolerance_rel_l2=TOL_F32,
+                     worst_problem_linf_vs_initial_amplitude=worst,
+                     compared="256 sampled points of every problem together, against the closed-form discrete "
+                              "solution (every mode times the RK3 polynomial of its exact discrete symbol)")
+            line["error_vs_oracle"] = e
+        elif name == "hj4096":
+            line["error_vs_oracle"] = _hj_first_steps_error(4096, workloads.SEED_HJ, 2)
+        elif name == "hj8192":
+            line["error_vs_oracle"] = _hj_first_step_error(8192, workloads.SEED_HJ_LARGE, "wenoz")
+        elif name == "hj8192_learned":
+            line["error_vs_oracle"] = _hj_first_step_error(8192, workloads.SEED_HJ_LARGE, "learned", blob,
+                                                           theta.cpu().numpy())
+    if name.startswith("paper_ex") and PAPER_N == 5277:
+        err, tf, nst = _paper_final_error(name)
         extra["final_error"] = {"linf_vs_exact": err, "t_final": tf, "steps": nst,
-                                "paper_linf_5277": PAPER_LINF[args.config]}
+                                "paper_linf_5277": PAPER_LINF[name]}
         line["vs_baseline"] = value / PAPER_NODE_DOF_PER_S
         extra["vs_baseline_note"] = ("value / the paper's sustained 1e8 DOF/node/s for its Sec. 5.1 test problems "
                                      "on one CPU node (2 x Xeon Gold 6148); other hardware, context only")
     if stats is not None:
         extra["learned_stats"] = {"stencils": stats[0], "fallbacks": stats[1],
                                   "fallback_fraction": stats[1] / max(stats[0], 1)}
-    if args.compare and args.config.startswith("paper_ex"):
+    if compare and name.startswith("paper_ex"):
         # the reduced-precision form of the same problem: speed and final error
-        rp = M.PREC_F32_F64UPDATE if args.config == "paper_ex2_diffusion" else M.PREC_F32
-        ms_r, _, _, _ = _timed_steps(args.config, args.steps, args.warmup, prec=rp)
+        rp = M.PREC_F32_F64UPDATE if name == "paper_ex2_diffusion" else M.PREC_F32
+        ms_r = _timed_steps(name, steps, warmup, prec=rp)[0]
         extra["reduced_precision_form"] = {
             "prec": "f32 sweeps + f64 update" if rp == M.PREC_F32_F64UPDATE else "f32",
             "value": dof / (ms_r / 1e3), "ms_per_step": ms_r, "speedup_vs_fp64": ms / ms_r}
         if PAPER_N == 5277:
-            err_r, tf_r, _ = _paper_final_error(args.config, rp)
+            err_r, tf_r, _ = _paper_final_error(name, rp)
             extra["reduced_precision_form"].update(linf_vs_exact=err_r, t_final=tf_r)
-    elif args.compare:
-        ms64, us64, _, _ = _timed_steps(args.config, args.steps, args.warmup, prec=M.PREC_F64)
+    elif compare and name != "heat256":
+        ms64, us64 = _timed_steps(name, steps, warmup, prec=M.PREC_F64)[:2]
         num = sum(float(torch.linalg.norm(a.double() - b.double()) ** 2) for a, b in zip(us, us64))
         den = sum(float(torch.linalg.norm(b.double()) ** 2) for b in us64)
         extra["vs_plain_fp64_gpu"] = {"fp64_value": dof / (ms64 / 1e3), "fp64_ms_per_step": ms64,
                                       "speedup": ms64 / ms, "rel_l2_vs_fp64": (num / max(den, 1e-300)) ** 0.5,
-                                      "steps_compared": args.warmup + args.steps}
+                                      "steps_compared": warmup + steps}
+        del us64
+    if compare and name == "hj8192_learned":
+        ms32 = _timed_steps("hj8192", steps, warmup)[0]
+        extra["vs_plain_fp32_wenoz_gpu"] = {"wenoz_ms_per_step": ms32, "speedup": ms32 / ms,
+                                            "note": "the same 8192^2 problem with the WENO-Z formula in FP32"}
     line.update(extra)
-    print(json.dumps(line))
+    del us
+    torch.cuda.empty_cache()
+    return line
+
+
+# workloads nested in the default line (BASELINE configs 1, 3, 4, 5, and the
+# plain WENO-Z form of config 5's problem)
+DEFAULT_OTHER = (("heat256", 100, 3), ("batch64", 20, 3), ("hj4096", 20, 3), ("hj8192", 10, 2),
+                 ("hj8192_learned", 10, 2))
 
 
 def main():
@@ -714,23 +1026,33 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the error statements against the oracle")
+    ap.add_argument("--headline-only", action="store_true", help="do not run the other workloads")
     ap.add_argument("--grid", type=lambda t: [int(v) for v in t.split(",")], default=[N, N, N],
                     help="nx,ny,nz (smaller grids are for profiler captures; the metric is quoted at 512^3)")
     ap.add_argument("--config", default="wave512", choices=["wave512", "nonuniform4096", "nonuniform4096_wenoz"] + sorted(CONFIGS),
                     help="workload (default: the 3-D wave step the metric is quoted on)")
     ap.add_argument("--size", type=int, default=None,
                     help="grid side of the paper_ex* configs (default: the paper's 5277)")
-    ap.add_argument("--compare", action="store_true",
-                    help="also time the plain FP64 GPU form and report the speedup and the difference")
+    ap.add_argument("--no-compare", dest="compare", action="store_false",
+                    help="skip the plain FP64 GPU form (speedup and difference)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.config.startswith("nonuniform4096"):
-        run_nonuniform(args)
+        print(json.dumps(run_nonuniform(args)))
     elif args.config != "wave512":
-        run_config(args)
+        print(json.dumps(config_line(args.config, args.steps, args.warmup, args.compare, not args.no_oracle,
+                                     args.size)))
     else:
-        run_ours(args)
+        line = run_ours(args)
+        if line is None:
+            return
+        ws = dist_env()[0]
+        if not args.headline_only and ws == 1 and args.grid == [N, N, N]:
+            line["other_configs"] = [config_line(nm, st, wu, args.compare, not args.no_oracle)
+                                     for nm, st, wu in DEFAULT_OTHER]
+        print(json.dumps(line))
 
 
 if __name__ == "__main__":
