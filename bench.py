@@ -53,11 +53,11 @@ WORKLOAD = {
     "l2": "inputs larger than L2 (2 x 1.07 GB FP64 state + 0.5 GB FP32 copy)",
 }
 # algorithmic bytes per DOF of each launch kind: x sweep: read the FP32 copy
-# of u^n, write the FP32 accumulator; y and z sweeps: read copy + acc, write
-# acc; update: read acc + u^n + u^{n-1} (FP64), write u^{n+1} (FP64) + its
-# FP32 copy
-BYTES_PER_DOF = {"x": 8, "yz": 12, "update": 32}
-LAUNCHES_PER_STEP = {"x": 1, "yz": 2, "update": 1}
+# of u^n, write the FP32 accumulator; y (and z) sweeps: read copy + acc,
+# write acc; last sweep with the FP64 leapfrog update: read copy + acc + u^n
+# + u^{n-1} (FP64), write u^{n+1} (FP64) + its FP32 copy; separate update:
+# read acc + u^n + u^{n-1}, write u^{n+1} + copy
+BYTES_PER_DOF = {"x": 8, "yz": 12, "last_update": 36, "update": 32}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per DOF per launch
 # from one ncu capture of each kernel on the 512 x 256 x 512 grid, scaled to a
 # full launch by the points processed (traffic grows with the points); a
@@ -363,17 +363,20 @@ def run_ours(args):
     # pair around every launch (the headline region above runs without them)
     M.molt_set_option(ctx, M.OPT_PROFILE, 1)
     t = M.molt_step(ctx, u, up, nsteps=args.steps, t=t)
-    per_kernel, kernel_names = {}, {}
+    per_kernel, kernel_names, launches = {}, {}, {}
     for name, kinds in (("x", ((M.KERNEL_LANES_ACC_SET, "lanes_sweep_kernel ACC_SET (x lines)"),
                                (M.KERNEL_ACC_SET, "sweep_tma_kernel ACC_SET (x lines)"))),
-                        ("yz", ((M.KERNEL_LANES_ACC_ADD, "lanes_sweep_kernel ACC_ADD (y and z lines)"),
+                        ("yz", ((M.KERNEL_LANES_ACC_ADD, "lanes_sweep_kernel ACC_ADD (y lines)"),
                                 (M.KERNEL_ACC_ADD, "sweep_tma_kernel ACC_ADD (y and z lines)"))),
+                        ("last_update", ((M.KERNEL_LANES_WAVE_FINAL,
+                                          "lanes_sweep_kernel WAVE_FINAL (z lines + FP64 leapfrog update)"),)),
                         ("update", ((M.KERNEL_UPDATE, "wave_update_kernel (FP64 leapfrog update)"),))):
         for kind, kname in kinds:
             tot, cnt = M.molt_profile_read(ctx, kind)
             if cnt:
                 per_kernel[name] = tot / cnt
                 kernel_names[name] = kname
+                launches[name] = cnt / args.steps
                 break
     M.molt_set_option(ctx, M.OPT_PROFILE, 0)
 
@@ -441,7 +444,7 @@ def run_ours(args):
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     # dominant kernel: the largest share of the step's device time
-    share = {k: per_kernel[k] * LAUNCHES_PER_STEP[k] for k in per_kernel}
+    share = {k: per_kernel[k] * launches[k] for k in per_kernel}
     dom = max(share, key=share.get)
     achieved = BYTES_PER_DOF[dom] * dof / (per_kernel[dom] / 1e3) / 1e9
     traffic = TRAFFIC_PER_DOF.get(kernel_names[dom])
@@ -452,8 +455,9 @@ def run_ours(args):
                 "per_kernel_gbs": {k: BYTES_PER_DOF[k] * dof / (per_kernel[k] / 1e3) / 1e9 for k in per_kernel},
                 "per_kernel_frac": {k: BYTES_PER_DOF[k] * dof / (per_kernel[k] / 1e3) / 1e9 / peak
                                     for k in per_kernel},
-                "algorithmic_bytes_per_dof": BYTES_PER_DOF,
-                "step_bytes_per_dof": sum(BYTES_PER_DOF[k] * LAUNCHES_PER_STEP[k] for k in BYTES_PER_DOF),
+                "launches_per_step": launches,
+                "algorithmic_bytes_per_dof": {k: BYTES_PER_DOF[k] for k in per_kernel},
+                "step_bytes_per_dof": sum(BYTES_PER_DOF[k] * launches[k] for k in per_kernel),
                 "per_kernel_source": "CUDA events around each launch, a second run of the same length"}
     if rank != 0:
         return None
@@ -479,7 +483,7 @@ def run_ours(args):
         "dtype": "f32", "data": "synthetic",
         "config": dict(WORKLOAD, grid=[nx, ny, nz], parallelism="replicas" if ws > 1 else "1gpu"),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": 4 * args.steps + 1, "clocks": clk,
+        "gpu_launches": int(round(sum(launches.values()) * args.steps)) + 1, "clocks": clk,
         "error_vs_oracle": err,
     }
     if compare:

@@ -290,7 +290,9 @@ typedef enum {
   MOLT_KERNEL_FLUX = 10,       /* advection-diffusion: split fluxes g^+, g^-  */
   MOLT_KERNEL_LANES_STORE = 11,   /* line-per-lane sweeps (MOLT_OPT_LANES):      */
   MOLT_KERNEL_LANES_ACC_SET = 12, /*   STORE, ACC_SET, and ACC_ADD / the        */
-  MOLT_KERNEL_LANES_ACC_ADD = 13  /*   advection-diffusion accumulations        */
+  MOLT_KERNEL_LANES_ACC_ADD = 13, /*   advection-diffusion accumulations,       */
+  MOLT_KERNEL_LANES_WAVE_FINAL = 14 /* and the last axis of the mixed-precision
+                                     wave step with the FP64 leapfrog update  */
 } molt_kernel_kind;
 
 /* With MOLT_OPT_PROFILE on: synchronises the stream, returns the summed

@@ -445,7 +445,7 @@ cudaError_t launch(const Problem& p, int epi, const Plan& pl, cudaStream_t s, bo
 // kLanesAutoDepth segments (nu >= ~0.22 for 16-point segments): below that
 // the look-back grows with 1/nu while the scan kernel's cost does not.
 constexpr int kLanesAutoDepth = 8;
-constexpr double kLanesTailWeight = 9.094947017729282e-13;   // 2^-40
+constexpr double kLanesTailWeight = 1.4901161193847656e-08;   // 2^-26
 
 bool plan_lanes(const molt_ctx* c, const Problem& p, int epi, const Plan& pl, bool f32_input, LanesArgs* la,
                 CUtensorMap* map) {
@@ -455,11 +455,13 @@ bool plan_lanes(const molt_ctx* c, const Problem& p, int epi, const Plan& pl, bo
   if (!p.nodes[pl.ax].empty()) return false;
   if (a.mode != MODE_0 && a.mode != MODE_R && a.mode != MODE_L) return false;
   if (a.P < 1 || a.P > 2) return false;
-  if (epi != EPI_ACC_SET && epi != EPI_ACC_ADD && epi != EPI_ACC_AXPY && !(epi == EPI_STORE && is_f32_state(p.d)))
+  const bool wave_final = epi == EPI_WAVE_FINAL && is_mixed(p.d) && pl.ax > 0 && a.shadow && a.dst;
+  if (epi != EPI_ACC_SET && epi != EPI_ACC_ADD && epi != EPI_ACC_AXPY && !(epi == EPI_STORE && is_f32_state(p.d)) &&
+      !wave_final)
     return false;
   const int n = a.g.n;
   if (n % kLE != 0 || n < kLE || n > kLE * kLMaxSeg) return false;
-  const void* outp = epi == EPI_STORE ? a.out : a.acc;
+  const void* outp = epi == EPI_STORE ? a.out : (wave_final ? a.dst : a.acc);
   if (!a.in || !outp || ((reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(outp)) & 15)) return false;
   LanesArgs L;
   std::memset(&L, 0, sizeof(L));
@@ -473,17 +475,36 @@ bool plan_lanes(const molt_ctx* c, const Problem& p, int epi, const Plan& pl, bo
   L.acc = static_cast<float*>(a.acc);
   L.coef = float(a.coefS);
   L.status = a.status;
+  if (wave_final) {
+    L.un = static_cast<const double*>(a.un);
+    L.us = static_cast<const double*>(a.us);
+    L.dst = static_cast<double*>(a.dst);
+    L.dst2 = static_cast<double*>(a.dst2);
+    L.shadow = a.shadow;
+    L.coefS = a.coefS;
+    L.from_rest = a.from_rest;
+  }
+  // every wait of this kernel normally lasts microseconds (a tile takes a few)
+  L.wait_limit = std::min<long long>(c->wait_limit, 200000000LL);
   const int64_t nx = axis_n(p, 0), ny = axis_n(p, 1), nz = axis_n(p, 2);
   std::memset(map, 0, sizeof(*map));
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
   if (pl.ax == 0) {
-    if (a.g.nlines % kLW != 0) return false;
+    // boxes of 32 points x 32 lines, 128-byte swizzle (csrc/sweep_lanes.cuh)
+    if (a.g.nlines % kLW != 0 || n % 32 != 0) return false;
     L.contiguous = 1;
-    L.LS = n + 4;
     L.ntiles = a.g.nlines / kLW;
+    cuuint64_t dims[2] = {cuuint64_t(n), cuuint64_t(a.g.nlines)};
+    cuuint64_t strides[1] = {cuuint64_t(n) * 4};
+    cuuint32_t box[2] = {32u, cuuint32_t(kLW)};
+    cuuint32_t estr[2] = {1, 1};
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(a.in), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
   } else {
     if (nx % kLW != 0) return false;
-    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc) return false;
     L.contiguous = 0;
     L.kind = pl.ax;
     L.tiles_per_row = nx / kLW;
@@ -534,7 +555,7 @@ bool plan_lanes(const molt_ctx* c, const Problem& p, int epi, const Plan& pl, bo
   }
   L.needA = L.kA != 0.0;
   L.needB = L.kB != 0.0;
-  // look-back depth: segment weights (q^16)^j >= 2^-40
+  // look-back depth: segment weights (q^16)^j >= 2^-26
   double w = 1.0;
   int lb = 0;
   const double qE = std::exp(lq * kLE);
@@ -555,9 +576,10 @@ molt_status run(molt_ctx* c, const Problem& p, int epi, Plan& pl, bool from_stat
     LanesArgs la;
     CUtensorMap lmap;
     if (plan_lanes(c, p, epi, pl, in_bytes == 4, &la, &lmap)) {
-      molt_ctx::Rec rec{epi == EPI_STORE ? int(MOLT_KERNEL_LANES_STORE)
-                                         : (epi == EPI_ACC_SET ? int(MOLT_KERNEL_LANES_ACC_SET)
-                                                               : int(MOLT_KERNEL_LANES_ACC_ADD)),
+      molt_ctx::Rec rec{epi == EPI_STORE        ? int(MOLT_KERNEL_LANES_STORE)
+                        : epi == EPI_ACC_SET    ? int(MOLT_KERNEL_LANES_ACC_SET)
+                        : epi == EPI_WAVE_FINAL ? int(MOLT_KERNEL_LANES_WAVE_FINAL)
+                                                : int(MOLT_KERNEL_LANES_ACC_ADD),
                         nullptr, nullptr};
       if (c->profile) {
         cudaEventCreate(&rec.start);
@@ -1195,7 +1217,10 @@ molt_status advdiff_step(molt_ctx* c, Problem& p, void* u) {
 
 // Mixed precision: the FP64 leapfrog update runs as its own streaming kernel
 // after the last axis (default), or, with MOLT_WAVE_FUSED_UPDATE=1, in the
-// last sweep's epilogue.
+// last sweep's epilogue (the line-per-lane kernel's where it takes the last
+// axis).  Fused, the FP64 work (two FMAs per point on GB300's narrow FP64
+// pipe) arrives in bursts at the end of every tile and stalls the sweep:
+// 1.36 ms for z + update at 512^3 against 0.37 + 0.79 ms apart.
 #ifndef MOLT_WAVE_FUSED_UPDATE
 #define MOLT_WAVE_FUSED_UPDATE 0
 #endif
@@ -1209,7 +1234,23 @@ molt_status wave_step(molt_ctx* c, Problem& p, void* cur, void* prev, bool from_
     pl.a.acc = p.acc;
     int epi;
     const bool last = ax + 1 == p.d.ndim;
-    const bool split_update = p.shadow && !MOLT_WAVE_FUSED_UPDATE;
+    // mixed precision: a streaming kernel does the FP64 update after the
+    // accumulating sweep of the last axis (with MOLT_WAVE_FUSED_UPDATE, the
+    // line-per-lane kernel's epilogue does it where that kernel takes the
+    // last axis)
+    bool split_update = p.shadow && !MOLT_WAVE_FUSED_UPDATE;
+    if (MOLT_WAVE_FUSED_UPDATE && last && p.shadow && ax > 0) {
+      split_update = true;
+      Plan probe = pl;
+      probe.a.shadow = p.shadow;
+      probe.a.un = cur;
+      probe.a.us = prev;
+      probe.a.dst = in_place_variant ? cur : prev;
+      probe.a.dst2 = in_place_variant ? prev : nullptr;
+      LanesArgs la;
+      CUtensorMap lmap;
+      if (plan_lanes(c, p, EPI_WAVE_FINAL, probe, true, &la, &lmap)) split_update = false;
+    }
     if (!last || split_update) {
       epi = ax == 0 ? EPI_ACC_SET : EPI_ACC_ADD;
     } else {
@@ -1910,7 +1951,9 @@ molt_status molt_step(molt_ctx* c, void* const* u, void* const* u_prev, int nste
   }
   if (status & ST_TIMEOUT) {
     cudaMemsetAsync(c->status_dev, 0, sizeof(int), c->stream);
-    return fail(c, MOLT_ETIMEOUT, "a device-side wait timed out");
+    return fail(c, MOLT_ETIMEOUT,
+                "a device-side wait timed out (a grid barrier or a copy: a copy may still have been in flight, so "
+                "treat the CUDA context as suspect: destroy this context and do not reuse its buffers)");
   }
   return MOLT_OK;
 }

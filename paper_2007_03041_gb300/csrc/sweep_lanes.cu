@@ -5,9 +5,9 @@ namespace molt {
 
 namespace {
 
-template <int EPI, bool CONTIG>
+template <int EPI, bool CONTIG, int LB>
 cudaError_t launch_one(const LanesArgs& a, const CUtensorMap& map, cudaStream_t s) {
-  auto k = &lanes_sweep_kernel<EPI, CONTIG>;
+  auto k = &lanes_sweep_kernel<EPI, CONTIG, LB>;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -29,23 +29,37 @@ cudaError_t launch_one(const LanesArgs& a, const CUtensorMap& map, cudaStream_t 
   return cudaGetLastError();
 }
 
-template <bool CONTIG>
+template <bool CONTIG, int LB>
 cudaError_t launch_epi(int epi, const LanesArgs& a, const CUtensorMap& map, cudaStream_t s) {
   switch (epi) {
-    case EPI_STORE: return launch_one<EPI_STORE, CONTIG>(a, map, s);
-    case EPI_ACC_SET: return launch_one<EPI_ACC_SET, CONTIG>(a, map, s);
-    case EPI_ACC_ADD: return launch_one<EPI_ACC_ADD, CONTIG>(a, map, s);
-    case EPI_ACC_AXPY: return launch_one<EPI_ACC_AXPY, CONTIG>(a, map, s);
+    case EPI_STORE: return launch_one<EPI_STORE, CONTIG, LB>(a, map, s);
+    case EPI_ACC_SET: return launch_one<EPI_ACC_SET, CONTIG, LB>(a, map, s);
+    case EPI_ACC_ADD: return launch_one<EPI_ACC_ADD, CONTIG, LB>(a, map, s);
+    case EPI_ACC_AXPY: return launch_one<EPI_ACC_AXPY, CONTIG, LB>(a, map, s);
+    case EPI_WAVE_FINAL:
+      if constexpr (!CONTIG) return launch_one<EPI_WAVE_FINAL, false, LB>(a, map, s);
+      return cudaErrorNotSupported;
     default: return cudaErrorNotSupported;
   }
+}
+
+// The look-back is unrolled to a compile-time depth: 4 (nu >= 0.33 with
+// 16-point segments and the 2^-26 cut), 8, or every segment of a 512-point
+// line.
+template <bool CONTIG>
+cudaError_t launch_lb(int epi, const LanesArgs& a, const CUtensorMap& map, cudaStream_t s) {
+  if (a.lb <= 4) return launch_epi<CONTIG, 4>(epi, a, map, s);
+  if (a.lb <= 8) return launch_epi<CONTIG, 8>(epi, a, map, s);
+  return launch_epi<CONTIG, kLMaxSeg>(epi, a, map, s);
 }
 
 }  // namespace
 
 cudaError_t launch_lanes(int epi, const LanesArgs& a, const CUtensorMap& map, cudaStream_t s) {
-  if (a.S < 1 || a.S > kLMaxSeg || a.n != a.S * kLE || a.P < 1 || a.P > 2 || a.ntiles < 1)
+  if (a.S < 1 || a.S > kLMaxSeg || a.n != a.S * kLE || a.P < 1 || a.P > 2 || a.ntiles < 1 || a.lb < 1 ||
+      a.lb > a.S)
     return cudaErrorInvalidValue;
-  return a.contiguous ? launch_epi<true>(epi, a, map, s) : launch_epi<false>(epi, a, map, s);
+  return a.contiguous ? launch_lb<true>(epi, a, map, s) : launch_lb<false>(epi, a, map, s);
 }
 
 }  // namespace molt

@@ -106,8 +106,10 @@ def test_lanes_in_place_and_constants():
 @pytest.mark.parametrize("n", [64, 96])
 def test_wave_step_on_lanes_kernels_matches_oracle(n):
     """3-D wave, Dirichlet, FP32 sweeps + FP64 update, P = 2, dt = 2h
-    (nu = 0.4): every sweep takes the line-per-lane kernel; 10 leapfrog steps
-    against the oracle, element by element and at the line ends."""
+    (nu = 0.4): every sweep takes the line-per-lane kernel; 10 steps (from
+    rest, then leapfrog, ending on the in-place variant that keeps u the
+    newest state) against the oracle, element by element and at the line
+    ends."""
     need_gpu()
     import torch
     h = 1.0 / (n - 1)
@@ -123,8 +125,11 @@ def test_wave_step_on_lanes_kernels_matches_oracle(n):
         M.molt_step(ctx, u, up, nsteps=1, t=[0.0])
         _, nset = M.molt_profile_read(ctx, M.KERNEL_LANES_ACC_SET)
         _, nadd = M.molt_profile_read(ctx, M.KERNEL_LANES_ACC_ADD)
+        _, nfin = M.molt_profile_read(ctx, M.KERNEL_LANES_WAVE_FINAL)
+        _, nupd = M.molt_profile_read(ctx, M.KERNEL_UPDATE)
         M.molt_set_option(ctx, M.OPT_PROFILE, 0)
-        assert (nset, nadd) == (1, 2), (nset, nadd)
+        # x, y, z on the line-per-lane kernel, then the FP64 update kernel
+        assert (nset, nadd, nfin, nupd) == (1, 2, 0, 1), (nset, nadd, nfin, nupd)
         M.molt_step(ctx, u, up, nsteps=9, t=[dt])
         got, gotp = u.cpu().numpy(), up.cpu().numpy()
     finally:

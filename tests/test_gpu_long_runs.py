@@ -14,7 +14,7 @@
 The wave and heat states are held to the FP32 path's stated tolerance:
 relative L2 1e-5, plus the largest pointwise error over the largest value
 (2e-5) and the first and last 4 points of every line.  The Hamilton-Jacobi
-state is held to it until the kinks form; after that, to a bound measured
+state is held to it before the kinks form; after that, to a bound measured
 with the oracle itself (see the test)."""
 import math
 
@@ -113,18 +113,18 @@ def test_batched_64_problems_200_steps_closed_form():
 
 
 def test_hj_wenoz_500_steps():
-    """The FP32-state form over the stated 500 steps.  Until the kinks form
-    (50 steps) it is held to the stated 1e-5.  Near the kinks the problem
-    amplifies any perturbation of FP32 size by about 10^4 (the oracle itself,
-    run with its state rounded to FP32 after every step, departs from the
-    pure FP64 oracle by 2.6e-3 at step 100 and 4.4e-5 at step 500), so at step
-    500 the bound is taken from that measurement: the GPU result may be at
-    most twice as far from the FP64 oracle as the oracle's own FP32-state run
-    is (relative L2 and largest pointwise error)."""
+    """The FP32-state form over the stated 500 steps.  Near the kinks (t ~ 1,
+    past step 40 on this grid) the problem amplifies perturbations of FP32
+    size by about 10^4: the oracle itself, run with its state rounded to FP32
+    after every step, departs from the pure FP64 oracle by 2.6e-3 at step 100
+    and 4.4e-5 at step 500.  So at each checkpoint (step 20, before the kinks,
+    and step 500) the GPU result is held to the stated tolerance or to twice
+    the distance of the oracle's own FP32-state run from the FP64 oracle,
+    whichever is larger (relative L2 and largest pointwise error)."""
     need_gpu()
     import torch
     from oracle.parallel import LinePool
-    n, early, nsteps = 256, 50, 500
+    n, early, nsteps = 256, 20, 500
     h = 2 * np.pi / n
     u0 = workloads.hj_initial(n)
     d = M.make_desc((n, n), lo=[0, 0], hi=[2 * np.pi] * 2, P=1, quad_points=5, weights=M.W_WENOZ, beta=1.0,
@@ -141,6 +141,7 @@ def test_hj_wenoz_500_steps():
     start = u0.astype(np.float32).astype(np.float64)
     a, b = start, start          # FP64 oracle; oracle with FP32 state storage
     ta = 0.0
+    checks = {}
     with LinePool() as pool:
         sa = sb = pool.hj_initial_speeds(start, [h, h])
         for k in range(1, nsteps + 1):
@@ -148,11 +149,11 @@ def test_hj_wenoz_500_steps():
             b, _, sb = pool.hj_step(b, [h, h], sb)
             b = b.astype(np.float32).astype(np.float64)
             ta += dta
-            if k == early:
-                for ax in range(2):
-                    assert_parity(got_early, a, TOL_F32, MAX_F32, line_axis=ax, what="HJ u^%d" % early)
-    bound_l2 = 2 * rel_l2(b, a)
-    bound_max = 2 * max_rel(b, a)
-    for ax in range(2):
-        assert_parity(got, a, bound_l2, bound_max, line_axis=ax, what="HJ u^%d" % nsteps)
+            if k in (early, nsteps):
+                checks[k] = (a, max(TOL_F32, 2 * rel_l2(b, a)), max(MAX_F32, 2 * max_rel(b, a)))
+    for k, got_k in ((early, got_early), (nsteps, got)):
+        want, tl2, tmax = checks[k]
+        for ax in range(2):
+            assert_parity(got_k, want, tl2, tmax, line_axis=ax, what="HJ u^%d" % k)
+    assert checks[early][1] == TOL_F32      # before the kinks FP32 storage alone stays below the stated bound
     assert abs(t[0] - ta) < 1e-3 * ta
