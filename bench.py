@@ -799,21 +799,35 @@ def _paper_final_error(config, prec=None):
     return err, t[0], steps
 
 
-def run_nonuniform(args):
+NONUNIFORM_CONFIGS = ("nonuniform4096", "nonuniform4096_wenoz", "nonuniform4096_dirichlet")
+
+
+def nonuniform_line(name, steps, warmup, error=True):
     """S_2 = D_0 + D_0^2 along x, then along y, of a 4096^2 FP32 field on a
-    stretched non-uniform periodic grid (point-local weights: the 6-point
-    linear rule, or with the _wenoz workload WENO-Z on the 5-point rule with
-    point-local d_r); a step is the two applications."""
+    stretched non-uniform grid (point-local weights): periodic axes with the
+    6-point linear rule, or WENO-Z on the 5-point rule with point-local d_r
+    (_wenoz), or Dirichlet axes whose nodes include both ends (_dirichlet);
+    a step is the two applications.  Error against the FP64 oracle on four
+    sampled x lines of the timed step's first pass and four y lines of one
+    more y pass over the input (untimed)."""
     import math
     import numpy as np
     import torch
     from paper_2007_03041_gb300 import molt as M
     from paper_2007_03041_gb300 import workloads
     n, L = 4096, 2 * math.pi
-    xi = L * np.arange(n) / n
-    nodes = xi + 0.3 * np.sin(xi)
-    weno = args.config.endswith("_wenoz")
-    d = M.make_desc((n, n), lo=[0, 0], hi=[L, L], P=2, quad_points=5 if weno else 6, prec=M.PREC_F32,
+    weno = name.endswith("_wenoz")
+    dirichlet = name.endswith("_dirichlet")
+    if dirichlet:
+        t = np.linspace(0.0, 1.0, n)
+        nodes = L * (t + 0.3 * np.sin(2 * np.pi * t) / (2 * np.pi))
+        nodes[0], nodes[-1] = 0.0, L
+    else:
+        xi = L * np.arange(n) / n
+        nodes = xi + 0.3 * np.sin(xi)
+    npts = 5 if weno else 6
+    bc = M.BC_DIRICHLET if dirichlet else M.BC_PERIODIC
+    d = M.make_desc((n, n), lo=[0, 0], hi=[L, L], bc=[bc, bc], P=2, quad_points=npts, prec=M.PREC_F32,
                     weights=M.W_WENOZ if weno else M.W_LINEAR)
     alpha = 0.6 * n / L
     stream = torch.cuda.Stream()
@@ -822,45 +836,74 @@ def run_nonuniform(args):
         try:
             M.molt_set_grid_axis(ctx, 0, 0, nodes)
             M.molt_set_grid_axis(ctx, 0, 1, nodes)
-            u = torch.tensor(workloads.hj_initial(n), dtype=torch.float32, device="cuda")
+            u0 = workloads.hj_initial(n).astype(np.float32)
+            u = torch.tensor(u0, dtype=torch.float32, device="cuda")
             a, b = torch.empty_like(u), torch.empty_like(u)
 
             def step():
                 M.molt_apply_D(ctx, 0, 0, M.OP_0, 2, alpha, u, a)
                 M.molt_apply_D(ctx, 0, 1, M.OP_0, 2, alpha, a, b)
-            for _ in range(args.warmup):
+            for _ in range(warmup):
                 step()
             stream.synchronize()
             clocks = ClockSampler(0)
             clocks.start()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 step()
             e1.record(stream)
             stream.synchronize()
             clk = clocks.stop()
-            ms = e0.elapsed_time(e1) / args.steps
+            ms = e0.elapsed_time(e1) / steps
+            err = None
+            if error:
+                rows = [0, 1, n // 2, n - 1]
+                gx = a.cpu().numpy()[rows]
+                M.molt_apply_D(ctx, 0, 1, M.OP_0, 2, alpha, u, b)
+                gy = b.cpu().numpy()[:, rows].T
+                err = _nonuniform_error(u0.astype(np.float64), rows, nodes, None if dirichlet else L, alpha, npts,
+                                        "wenoz" if weno else "linear", gx, gy)
         finally:
             M.molt_destroy(ctx)
     dof = n * n
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = 16 * dof / (ms / 1e3) / 1e9
+    kind = "Dirichlet" if dirichlet else "periodic"
     line = {
-        "metric": "DOF updates/sec (S_2 along x and y, 4096^2 non-uniform periodic grid, FP32%s) on GB300"
-                  % (", WENO-Z" if weno else ""),
-        "value": dof / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "metric": "DOF updates/sec (S_2 along x and y, 4096^2 non-uniform %s grid, FP32%s) on GB300"
+                  % (kind, ", WENO-Z" if weno else ""),
+        "value": dof / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": {"workload": args.config, "dof": dof, "grid": "x = xi + 0.3 sin xi",
-                                        "weights": "wenoz" if weno else "linear"},
+        "data": "synthetic", "config": {"workload": name, "dof": dof, "bc": kind.lower(),
+                                        "grid": ("x = L (t + 0.3 sin(2 pi t)/(2 pi)), t = i/(n-1)" if dirichlet
+                                                 else "x = xi + 0.3 sin xi, xi = 2 pi i/n"),
+                                        "weights": "wenoz" if weno else "linear", "l2_flush": "inputs > L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "scope": "two apply_D calls per step (x: one sweep; y: transpose, sweep, transpose), "
                               "8 algorithmic B/DOF each",
                      "peak_source": "measured" if peaks else "fallback"},
-        "gpu_launches": 4 * args.steps, "clocks": clk,
+        "gpu_launches": 4 * steps, "clocks": clk,
     }
+    if err is not None:
+        line["error_vs_oracle"] = err
     return line
+
+
+def _nonuniform_error(u, rows, nodes, L, alpha, npts, weights, gx, gy):
+    """Error of sampled x lines (rows of S_x[u]) and y lines (columns of
+    S_y[u]) against the FP64 oracle."""
+    import numpy as np
+    from oracle import nonuniform
+    tables = nonuniform.weights(nodes, L, alpha, npts)
+    weno = nonuniform.weno_tables(nodes, L, alpha, npts) if weights == "wenoz" else None
+    wx = np.stack([nonuniform.partial_sum(u[j], nodes, L, alpha, "0", npts, 2, weights, tables, weno) for j in rows])
+    wy = np.stack([nonuniform.partial_sum(u[:, i], nodes, L, alpha, "0", npts, 2, weights, tables, weno)
+                   for i in rows])
+    st = error_stats(np.concatenate([gx.ravel(), gy.ravel()]), np.concatenate([wx.ravel(), wy.ravel()]))
+    st["sample"] = "x lines %s of S_x[u] and y lines %s of S_y[u] (4096 points each)" % (rows, rows)
+    return st
 
 
 def config_line(name, steps, warmup, compare=True, error=True, size=None):
@@ -1019,7 +1062,8 @@ def config_line(name, steps, warmup, compare=True, error=True, size=None):
 # workloads nested in the default line (BASELINE configs 1, 3, 4, 5, and the
 # plain WENO-Z form of config 5's problem)
 DEFAULT_OTHER = (("heat256", 100, 3), ("batch64", 20, 3), ("hj4096", 20, 3), ("hj8192", 10, 2),
-                 ("hj8192_learned", 10, 2))
+                 ("hj8192_learned", 10, 2), ("nonuniform4096", 20, 3), ("nonuniform4096_wenoz", 20, 3),
+                 ("nonuniform4096_dirichlet", 20, 3))
 
 
 def main():
@@ -1034,7 +1078,7 @@ def main():
     ap.add_argument("--headline-only", action="store_true", help="do not run the other workloads")
     ap.add_argument("--grid", type=lambda t: [int(v) for v in t.split(",")], default=[N, N, N],
                     help="nx,ny,nz (smaller grids are for profiler captures; the metric is quoted at 512^3)")
-    ap.add_argument("--config", default="wave512", choices=["wave512", "nonuniform4096", "nonuniform4096_wenoz"] + sorted(CONFIGS),
+    ap.add_argument("--config", default="wave512", choices=["wave512"] + list(NONUNIFORM_CONFIGS) + sorted(CONFIGS),
                     help="workload (default: the 3-D wave step the metric is quoted on)")
     ap.add_argument("--size", type=int, default=None,
                     help="grid side of the paper_ex* configs (default: the paper's 5277)")
@@ -1043,8 +1087,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.config.startswith("nonuniform4096"):
-        print(json.dumps(run_nonuniform(args)))
+    elif args.config in NONUNIFORM_CONFIGS:
+        print(json.dumps(nonuniform_line(args.config, args.steps, args.warmup, not args.no_oracle)))
     elif args.config != "wave512":
         print(json.dumps(config_line(args.config, args.steps, args.warmup, args.compare, not args.no_oracle,
                                      args.size)))
@@ -1054,8 +1098,9 @@ def main():
             return
         ws = dist_env()[0]
         if not args.headline_only and ws == 1 and args.grid == [N, N, N]:
-            line["other_configs"] = [config_line(nm, st, wu, args.compare, not args.no_oracle)
-                                     for nm, st, wu in DEFAULT_OTHER]
+            line["other_configs"] = [
+                nonuniform_line(nm, st, wu, not args.no_oracle) if nm in NONUNIFORM_CONFIGS
+                else config_line(nm, st, wu, args.compare, not args.no_oracle) for nm, st, wu in DEFAULT_OTHER]
         print(json.dumps(line))
 
 

@@ -158,6 +158,10 @@ molt_status molt_apply_D(molt_ctx* ctx, int problem, int axis, int op, int P, do
  * so dt F = -(beta/c) sum_d (S_R[g_d^+] - S_L[g_d^-]) - beta^2 sum_d S_0[u];
  * 3-stage SSP Runge-Kutta (MOLT_INT_DEFAULT) or forward Euler.  Linear or
  * WENO-Z weights (WENO-Z: 5 points, MOLT_PREC_F64 or MOLT_PREC_F32).
+ * Heat, wave and advection-diffusion problems may have non-uniform axes
+ * (molt_set_grid_axis): their S_{P,d} are the point-local sums of
+ * molt_apply_D, the steps' formulas unchanged; Hamilton-Jacobi problems with
+ * a non-uniform axis return MOLT_EUNSUPPORTED.
  * Synchronous at the end (reads t and the device status). */
 molt_status molt_step(molt_ctx* ctx, void* const* u, void* const* u_prev, int nsteps, double* t_inout);
 
@@ -172,19 +176,27 @@ molt_status molt_step(molt_ctx* ctx, void* const* u, void* const* u_prev, int ns
  * alignment, or a problem that is not Hamilton-Jacobi.  Synchronous. */
 molt_status molt_set_source(molt_ctx* ctx, int problem, const void* coef, int degree);
 
-/* Non-uniform periodic axis: the n = desc.n[axis] nodes of one period, host
- * array, strictly increasing, x[n-1] - x[0] < hi - lo (the period); copied.
+/* Non-uniform axis: the n = desc.n[axis] nodes, host array, strictly
+ * increasing; copied.  Periodic axis: the nodes of one period,
+ * x[n-1] - x[0] < hi - lo (the period).  Dirichlet axis: every node of the
+ * line, boundary nodes included, x[0] = a .. x[n-1] = b (n >= 4).
  * molt_apply_D along that axis then uses point-local quadrature weights
  * (each point's stencil nodes integrated against the exponential kernel,
  * the non-uniform case of Sec. 2.4) and cell decays e^{-alpha (x_i - x_{i-1})},
- * closed over the period with mu = e^{-alpha (hi - lo)} (Sec. 2.3).  With
- * MOLT_W_WENOZ (5-point rule) the local integrals are the WENO-Z combination
- * of the substencil rules, with point-local linear weights and smoothness
- * indicators (see molt_nonuniform_weno_weights); MOLT_W_LEARNED is
- * MOLT_EUNSUPPORTED on non-uniform axes.  x == NULL makes the axis
- * uniform again.  molt_step on a problem with a non-uniform axis returns
- * MOLT_EUNSUPPORTED.  MOLT_EINVAL: bad index, count or nodes;
- * MOLT_EUNSUPPORTED: a Dirichlet axis.  Synchronous. */
+ * closed over the period with mu = e^{-alpha (hi - lo)} (Sec. 2.3), or on a
+ * Dirichlet axis started at the ends, I_R(x_0) = I_L(x_{n-1}) = 0, with
+ * ghost nodes mirrored about the ends holding the odd reflection of the
+ * data, and the boundary constants that make L^{-1} take the boundary values
+ * at a and b (mu = e^{-alpha (x_{n-1} - x_0)}; for L_0 the 2x2 system of
+ * determinant 1 - mu^2).  With MOLT_W_WENOZ (5-point rule) the local
+ * integrals are the WENO-Z combination of the substencil rules, with
+ * point-local linear weights and smoothness indicators (see
+ * molt_nonuniform_weno_weights); MOLT_W_LEARNED is MOLT_EUNSUPPORTED on
+ * non-uniform axes.  molt_step runs heat, wave and advection-diffusion
+ * problems on such axes.  x == NULL makes the axis uniform again.
+ * The first call on a problem allocates one state-sized array of the
+ * compute type (the axis sums of molt_step).  MOLT_EINVAL: bad index,
+ * count or nodes; MOLT_ENOMEM.  Synchronous. */
 molt_status molt_set_grid_axis(molt_ctx* ctx, int problem, int axis, const double* x, int64_t n);
 
 /* The point tables of a non-uniform line (host only, no device work): for

@@ -215,9 +215,10 @@ def flux(kind, u, a=1.0):
     return a * u if kind == FLUX_LINEAR else 0.5 * u * u
 
 
-def advdiff_rhs_dt(u, dxs, dt, kind, a, c, kappa, beta, npts, P, bc=None, weights="linear"):
+def advdiff_rhs_dt(u, dxs, dt, kind, a, c, kappa, beta, npts, P, bc=None, weights="linear", grids=None):
     """dt * F(u); a[d] per array axis (linear flux), c the splitting bound;
-    weights: the local-quadrature weights of every sweep (linear or WENO-Z)."""
+    weights: the local-quadrature weights of every sweep (linear or WENO-Z);
+    grids: non-uniform axes as for the heat and wave steps."""
     bc = bc or [BC_PERIODIC] * u.ndim
     alpha = beta / (c * dt)
     out = np.zeros_like(u)
@@ -225,24 +226,27 @@ def advdiff_rhs_dt(u, dxs, dt, kind, a, c, kappa, beta, npts, P, bc=None, weight
         g = flux(kind, u, a[ax] if kind == FLUX_LINEAR else 1.0)
         gp = 0.5 * (g + c * u)
         gm = 0.5 * (g - c * u)
-        dminus = alpha * partial_sum(gp, ax, alpha, dxs[ax], "R", bc[ax], npts, P, weights)
-        dplus = -alpha * partial_sum(gm, ax, alpha, dxs[ax], "L", bc[ax], npts, P, weights)
+        dminus = alpha * axis_sum(gp, ax, alpha, dxs[ax], "R", bc[ax], npts, P, weights, grids=grids)
+        dplus = -alpha * axis_sum(gm, ax, alpha, dxs[ax], "L", bc[ax], npts, P, weights, grids=grids)
         out = out - dt * (dminus + dplus)
     if kappa > 0:
         an = beta / np.sqrt(kappa * dt)
         for ax in range(u.ndim):
-            out = out - kappa * dt * an * an * partial_sum(u, ax, an, dxs[ax], "0", bc[ax], npts, P, weights)
+            out = out - kappa * dt * an * an * axis_sum(u, ax, an, dxs[ax], "0", bc[ax], npts, P, weights,
+                                                        grids=grids)
     return out
 
 
-def advdiff_step(u, dxs, dt, kind, a, c, kappa=0.0, beta=1.0, npts=6, P=1, rk3=False, weights="linear"):
+def advdiff_step(u, dxs, dt, kind, a, c, kappa=0.0, beta=1.0, npts=6, P=1, rk3=False, weights="linear",
+                 grids=None):
     """One step: forward Euler, or the 3-stage SSP Runge-Kutta method (Shu-Osher form)."""
     un = np.asarray(u, dtype=np.float64)
     if not rk3:
-        return un + advdiff_rhs_dt(un, dxs, dt, kind, a, c, kappa, beta, npts, P, None, weights)
+        return un + advdiff_rhs_dt(un, dxs, dt, kind, a, c, kappa, beta, npts, P, None, weights, grids)
     us = un
     for a0, a1 in SSPRK3:
-        us = a0 * un + a1 * (us + advdiff_rhs_dt(us, dxs, dt, kind, a, c, kappa, beta, npts, P, None, weights))
+        us = a0 * un + a1 * (us + advdiff_rhs_dt(us, dxs, dt, kind, a, c, kappa, beta, npts, P, None, weights,
+                                                 grids))
     return us
 
 

@@ -43,8 +43,10 @@ struct Problem {
   void* gp = nullptr;       // advection-diffusion: split fluxes g^+, g^- (compute type)
   void* gm = nullptr;
   void* hv[4] = {nullptr, nullptr, nullptr, nullptr};  // HJ with RK3: S_R, S_L per axis (state type)
-  // non-uniform periodic axes: the nodes of one period (empty = uniform) and
-  // the device tables of the last (alpha, rule) applied
+  // non-uniform axes: the nodes of one period or of a Dirichlet line (empty =
+  // uniform), and device caches (mutable: filled on first use by sweeps that
+  // see the problem as const) -- the tables of the last (alpha, rule)
+  // applied, transposed copies and the axis sums of molt_step
   std::vector<double> nodes[3];
   struct NuCache {
     double alpha = 0.0;
@@ -52,8 +54,10 @@ struct Problem {
     int weights = -1;
     void* dev = nullptr;         // cR[K n], cL[K n], q[n] of the compute type (K = 6, WENO-Z 30)
     size_t count = 0;            // values allocated
-  } nu[3];
-  void* nu_tmp[2] = {nullptr, nullptr};   // transposed copies for strided non-uniform 2-D sweeps
+  };
+  mutable NuCache nu[3];
+  mutable void* nu_tmp[2] = {nullptr, nullptr};   // transposed copies for strided non-uniform 2-D sweeps
+  mutable void* nu_sum = nullptr;                 // S of one axis in the compute type (molt_step)
   int64_t hj_steps = 0;     // HJ steps taken (rotates the speed slots)
   bool hj_lag_ready = false;
 };
@@ -569,7 +573,10 @@ bool plan_lanes(const molt_ctx* c, const Problem& p, int epi, const Plan& pl, bo
   return true;
 }
 
+molt_status run_nonuniform(molt_ctx* c, const Problem& p, int epi, const Plan& pl);
+
 molt_status run(molt_ctx* c, const Problem& p, int epi, Plan& pl, bool from_state_copy = true) {
+  if (!p.nodes[pl.ax].empty()) return run_nonuniform(c, p, epi, pl);
   // element size of the sweep input: FP64 except FP32 state or the FP32 copy
   const size_t in_bytes = is_f32_state(p.d) || (is_mixed(p.d) && from_state_copy) ? 4 : 8;
   {
@@ -631,9 +638,10 @@ bool hj_transposed_y(molt_ctx* c, const Problem& p);
 }  // namespace
 
 namespace {
-molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int P, double alpha,
-                               const void* in, void* out);
-molt_status transpose(molt_ctx* c, const Problem& p, const void* in, void* out, long long ny, long long nx);
+molt_status apply_D_nonuniform(molt_ctx* c, const Problem& p, int axis, int mode, int P, double alpha,
+                               const void* in, void* out, bool io_compute = false);
+molt_status transpose(molt_ctx* c, const Problem& p, const void* in, void* out, long long ny, long long nx,
+                      size_t elem = 0);
 Problem transposed(const Problem& p);
 
 // Sizes and spacings of a validated descriptor (periodic axes: n intervals,
@@ -941,19 +949,24 @@ void record_end(molt_ctx* c, molt_ctx::Rec* rec) {
   }
 }
 
-// sum_{p<=P} D^p along a non-uniform periodic axis (point-local weights).
-molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int P, double alpha, const void* in,
-                               void* out) {
+// sum_{p<=P} D^p along a non-uniform axis, periodic or Dirichlet (point-local
+// weights).
+// io_compute: in and out hold the compute type (molt_step's FP32 copy and
+// axis sums), else the state type (molt_apply_D).
+molt_status apply_D_nonuniform(molt_ctx* c, const Problem& p, int axis, int mode, int P, double alpha, const void* in,
+                               void* out, bool io_compute) {
   if (p.d.weights == MOLT_W_LEARNED) return fail(c, MOLT_EUNSUPPORTED, "non-uniform axes run linear or WENO-Z weights");
   if (!(alpha > 0) || !std::isfinite(alpha)) return fail(c, MOLT_EINVAL, "alpha must be positive and finite");
   const std::vector<double>& x = p.nodes[axis];
   const int n = int(x.size());
-  const double L = p.d.hi[axis] - p.d.lo[axis];
+  const bool dir = p.d.bc[axis] == MOLT_BC_DIRICHLET;
+  const double L = dir ? 0.0 : p.d.hi[axis] - p.d.lo[axis];   // 0: the tables of a Dirichlet line
   const bool f64 = is_f64_sweep(p.d);
   const bool weno = p.d.weights == MOLT_W_WENOZ;
   const size_t slots = weno ? size_t(kNuWeno) : 6;
   const size_t tb = f64 ? 8 : 4;
   Problem::NuCache& cch = p.nu[axis];
+  const size_t io_bytes = io_compute ? compute_bytes(p.d) : state_bytes(p.d);
   cudaError_t e;
   if (!cch.dev || cch.alpha != alpha || cch.npts != p.d.quad_points || cch.weights != int(p.d.weights)) {
     std::vector<double> cR, cL, q;
@@ -1002,7 +1015,7 @@ molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int 
         t = nullptr;
         return fail(c, MOLT_ENOMEM, "non-uniform transposed copies");
       }
-    molt_status st = transpose(c, p, in, p.nu_tmp[0], ny, nx);
+    molt_status st = transpose(c, p, in, p.nu_tmp[0], ny, nx, io_bytes);
     if (st != MOLT_OK) return st;
     kin = p.nu_tmp[0];
     kout = p.nu_tmp[1];
@@ -1011,7 +1024,14 @@ molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int 
   a.g = trans ? geom(transposed(p), 0) : geom(p, axis);
   a.mode = mode;
   a.P = P;
-  a.inv1mmu = 1.0 / (-std::expm1(-alpha * L));
+  a.bc = dir ? 1 : 0;
+  if (dir) {
+    const double w = x[size_t(n - 1)] - x[0];
+    a.mu = std::exp(-alpha * w);
+    a.kdir = 2.0 / (-std::expm1(-2.0 * alpha * w));
+  } else {
+    a.inv1mmu = 1.0 / (-std::expm1(-alpha * L));
+  }
   a.in = kin;
   a.out = kout;
   a.status = c->status_dev;
@@ -1038,7 +1058,7 @@ molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int 
   } else {
     const float* d = static_cast<const float*>(cch.dev);
     NuTables<float> t{d, d + slots * n, d + 2 * slots * n};
-    if (is_f32_state(p.d)) {
+    if (io_bytes == 4) {
       if (weno) launch(nonuniform_kernel<float, float, true>, t);
       else launch(nonuniform_kernel<float, float, false>, t);
     } else {
@@ -1049,7 +1069,59 @@ molt_status apply_D_nonuniform(molt_ctx* c, Problem& p, int axis, int mode, int 
   record_end(c, &rec);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "non-uniform sweep");
-  return trans ? transpose(c, p, p.nu_tmp[1], out, nx, ny) : MOLT_OK;
+  return trans ? transpose(c, p, p.nu_tmp[1], out, nx, ny, io_bytes) : MOLT_OK;
+}
+
+// A sweep's epilogue applied point by point to axis sums that another kernel
+// wrote (the non-uniform axes of molt_step): the arithmetic of the fused
+// epilogues, with S[i] in the compute type and the natural layout.
+template <typename T, typename TST, int EPI>
+__global__ void point_epilogue_kernel(const SweepArgs a, const T* __restrict__ S, long long n) {
+  const Epilogue<T, TST, EPI> ep{a, 0.0, 0.0};
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const EpiOps<T, TST> o = ep.load(i);
+    ep.store(i, S[i], o);
+  }
+}
+
+template <typename T, typename TST>
+cudaError_t launch_point_epilogue(int epi, const SweepArgs& a, const void* S, long long n, cudaStream_t s) {
+  const T* sp = static_cast<const T*>(S);
+  const int g = stream_grid(n);
+  switch (epi) {
+    case EPI_ACC_SET: point_epilogue_kernel<T, TST, EPI_ACC_SET><<<g, 256, 0, s>>>(a, sp, n); break;
+    case EPI_ACC_ADD: point_epilogue_kernel<T, TST, EPI_ACC_ADD><<<g, 256, 0, s>>>(a, sp, n); break;
+    case EPI_ACC_AXPY: point_epilogue_kernel<T, TST, EPI_ACC_AXPY><<<g, 256, 0, s>>>(a, sp, n); break;
+    case EPI_HEAT_FINAL: point_epilogue_kernel<T, TST, EPI_HEAT_FINAL><<<g, 256, 0, s>>>(a, sp, n); break;
+    case EPI_WAVE_FINAL: point_epilogue_kernel<T, TST, EPI_WAVE_FINAL><<<g, 256, 0, s>>>(a, sp, n); break;
+    default: return cudaErrorNotSupported;
+  }
+  return cudaGetLastError();
+}
+
+// One axis of a heat, wave or advection-diffusion step along a non-uniform
+// axis: S = sum_{p<=P} D^p of the planned operator into the problem's sum
+// buffer by the non-uniform sweep, then the planned epilogue point by point.
+molt_status run_nonuniform(molt_ctx* c, const Problem& p, int epi, const Plan& pl) {
+  if (epi != EPI_ACC_SET && epi != EPI_ACC_ADD && epi != EPI_ACC_AXPY && epi != EPI_HEAT_FINAL &&
+      epi != EPI_WAVE_FINAL)
+    return fail(c, MOLT_EUNSUPPORTED, "non-uniform axes run heat, wave and advection-diffusion steps");
+  if (!p.nu_sum) return fail(c, MOLT_EINVAL, "non-uniform axis without its sum buffer");
+  molt_status st = apply_D_nonuniform(c, p, pl.ax, pl.a.mode, pl.a.P, pl.a.alpha, pl.a.in, p.nu_sum, true);
+  if (st != MOLT_OK) return st;
+  molt_ctx::Rec rec;
+  record_begin(c, &rec, epi == EPI_ACC_AXPY ? int(MOLT_KERNEL_ACC_ADD) : epi);
+  cudaError_t e;
+  if (is_f64_sweep(p.d))
+    e = launch_point_epilogue<double, double>(epi, pl.a, p.nu_sum, p.total, c->stream);
+  else if (is_f32_state(p.d))
+    e = launch_point_epilogue<float, float>(epi, pl.a, p.nu_sum, p.total, c->stream);
+  else
+    e = launch_point_epilogue<float, double>(epi, pl.a, p.nu_sum, p.total, c->stream);
+  record_end(c, &rec);
+  if (e != cudaSuccess) return cuda_fail(c, e, "non-uniform step epilogue");
+  return MOLT_OK;
 }
 
 
@@ -1308,11 +1380,12 @@ __global__ void transpose_kernel(const T* __restrict__ in, T* __restrict__ out, 
   }
 }
 
-molt_status transpose(molt_ctx* c, const Problem& p, const void* in, void* out, long long ny, long long nx) {
+molt_status transpose(molt_ctx* c, const Problem& p, const void* in, void* out, long long ny, long long nx,
+                      size_t elem) {
   molt_ctx::Rec rec;
   record_begin(c, &rec, MOLT_KERNEL_TRANSPOSE);
   const dim3 grid(unsigned((nx + 63) / 64), unsigned((ny + 63) / 64)), block(32, 8);
-  if (state_bytes(p.d) == 4)
+  if ((elem ? elem : state_bytes(p.d)) == 4)
     transpose_kernel<float><<<grid, block, 0, c->stream>>>(static_cast<const float*>(in), static_cast<float*>(out),
                                                            ny, nx);
   else
@@ -1885,6 +1958,7 @@ molt_status molt_step(molt_ctx* c, void* const* u, void* const* u_prev, int nste
   if (!c) return fail(nullptr, MOLT_EINVAL, "null context");
   if (!u || !t_inout || nsteps < 0) return fail(c, MOLT_EINVAL, "null u/t_inout or negative nsteps");
   const int np = int(c->probs.size());
+  bool any_nonuniform = false;   // the batched heat step runs uniform grids
   for (int i = 0; i < np; ++i) {
     if (!u[i]) return fail(c, MOLT_EINVAL, "null state pointer");
     if (c->probs[i].d.pde == MOLT_PDE_WAVE && (!u_prev || !u_prev[i]))
@@ -1892,8 +1966,11 @@ molt_status molt_step(molt_ctx* c, void* const* u, void* const* u_prev, int nste
     if (c->probs[i].d.pde != MOLT_PDE_HJ && !(c->probs[i].d.dt > 0))
       return fail(c, MOLT_EINVAL, "heat and wave steps need dt > 0");
     for (int ax = 0; ax < 3; ++ax)
-      if (!c->probs[i].nodes[ax].empty())
-        return fail(c, MOLT_EUNSUPPORTED, "molt_step runs uniform grids (non-uniform axes: molt_apply_D)");
+      if (!c->probs[i].nodes[ax].empty()) {
+        if (c->probs[i].d.pde == MOLT_PDE_HJ)
+          return fail(c, MOLT_EUNSUPPORTED, "Hamilton-Jacobi steps run uniform grids");
+        any_nonuniform = true;
+      }
   }
   cudaError_t e;
   std::vector<double> t0(np);
@@ -1907,11 +1984,12 @@ molt_status molt_step(molt_ctx* c, void* const* u, void* const* u_prev, int nste
   }
   molt_status bst = batch_prepare(c);
   if (bst != MOLT_OK) return bst;
-  if (c->batch.supported && nsteps > 0) {
+  const bool batched = c->batch.supported && !any_nonuniform;
+  if (batched && nsteps > 0) {
     if ((bst = batch_steps(c, u, nsteps)) != MOLT_OK) return bst;
     for (int i = 0; i < np; ++i) t_inout[i] += nsteps * c->probs[i].d.dt;
   }
-  for (int k = 0; k < (c->batch.supported ? 0 : nsteps); ++k) {
+  for (int k = 0; k < (batched ? 0 : nsteps); ++k) {
     for (int i = 0; i < np; ++i) {
       Problem& p = c->probs[i];
       molt_status st = MOLT_OK;
@@ -2039,14 +2117,20 @@ molt_status molt_set_grid_axis(molt_ctx* c, int problem, int axis, const double*
     p.nodes[axis].clear();
     return MOLT_OK;
   }
-  if (p.d.bc[axis] != MOLT_BC_PERIODIC) return fail(c, MOLT_EUNSUPPORTED, "non-uniform axes are periodic");
   if (n != p.n[axis]) return fail(c, MOLT_EINVAL, "node count differs from the axis size");
+  const bool dir = p.d.bc[axis] == MOLT_BC_DIRICHLET;
   const double L = p.d.hi[axis] - p.d.lo[axis];
+  if (dir && n < 4) return fail(c, MOLT_EINVAL, "a Dirichlet axis needs at least 4 nodes");
   for (int64_t i = 0; i < n; ++i) {
     if (!std::isfinite(x[i])) return fail(c, MOLT_EINVAL, "nodes must be finite");
     if (i > 0 && !(x[i] > x[i - 1])) return fail(c, MOLT_EINVAL, "nodes must increase strictly");
   }
-  if (!(x[n - 1] - x[0] < L)) return fail(c, MOLT_EINVAL, "nodes must lie within one period");
+  if (!dir && !(x[n - 1] - x[0] < L)) return fail(c, MOLT_EINVAL, "nodes must lie within one period");
+  if (!p.nu_sum && (e = cudaMalloc(&p.nu_sum, compute_bytes(p.d) * size_t(p.total))) != cudaSuccess) {
+    cudaGetLastError();
+    p.nu_sum = nullptr;
+    return fail(c, MOLT_ENOMEM, "non-uniform axis sums");
+  }
   p.nodes[axis].assign(x, x + n);
   return MOLT_OK;
 }
@@ -2139,6 +2223,7 @@ molt_status molt_destroy(molt_ctx* c) {
     cudaFree(p.gm);
     for (auto& cch : p.nu) cudaFree(cch.dev);
     for (void* t : p.nu_tmp) cudaFree(t);
+    cudaFree(p.nu_sum);
     for (void* v : p.hv) cudaFree(v);
     cudaFree(p.tu);
     cudaFree(p.thx);

@@ -1,9 +1,10 @@
-// Fast summation on non-uniform periodic lines (the point-local quadrature
-// that Sec. 2.4 describes for non-uniform meshes): per point i the J_R / J_L
+// Fast summation on non-uniform lines (the point-local quadrature that
+// Sec. 2.4 describes for non-uniform meshes): per point i the J_R / J_L
 // weights of its own stencil nodes and the cell decay q_i = e^{-alpha (x_i -
 // x_{i-1})}; the recurrences I_R(x_i) = q_i I_R(x_{i-1}) + J_R(x_i),
 // I_L(x_i) = q_{i+1} I_L(x_{i+1}) + J_L(x_i) close over the period with
-// mu = prod q_i = e^{-alpha L} (Sec. 2.3).
+// mu = prod q_i = e^{-alpha L} (Sec. 2.3), or on a Dirichlet line start at
+// the ends with the boundary constants fixed by the boundary values.
 //
 // Host side: build_nonuniform_tables() integrates the Lagrange basis of each
 // point's stencil against the exponential by 16-point Gauss-Legendre
@@ -36,7 +37,9 @@ struct NuTables {
 struct NuArgs {
   LineGeom g;
   int mode, P;
-  double inv1mmu;       // 1/(1 - mu), mu = e^{-alpha L}
+  int bc;               // 0 periodic, 1 Dirichlet (nodes x_0 = a .. x_{n-1} = b)
+  double inv1mmu;       // periodic: 1/(1 - mu), mu = e^{-alpha L}
+  double mu, kdir;      // Dirichlet: mu = e^{-alpha (b - a)}, kdir = 2/(1 - mu^2)
   const void* in;
   void* out;
   int* status;
@@ -212,13 +215,16 @@ inline void build_nonuniform_weno_tables(const std::vector<double>& x, double L,
 }
 
 // WENO-Z local integral of point i from its point tables tw ([30][n], layout
-// of build_nonuniform_weno_tables): the five stencil values in the
-// orientation of the direction (J_L reads the mirrored nodes), per
-// substencil r its rule, a = p_t(0) and b = p_tt, beta_r = a^2 - a b +
-// 4/3 b^2, and the WENO-Z map w~_r = d_r (1 + tau/(eps + beta_r)),
-// tau = |beta_0 - beta_2|, eps = 1e-6 (Sec. 2.4).
+// of build_nonuniform_weno_tables), in difference form: returns
+// (1 - q) v_i - J(x_i) = sum_r w_r sum_j c^{(r)}_j (v_i - v_j), exact since
+// every substencil rule integrates the constant to 1 - q and the normalised
+// weights sum to one.  The five stencil values are taken in the orientation
+// of the direction (J_L reads the mirrored nodes); per substencil r its
+// rule, a = p_t(0) and b = p_tt, beta_r = a^2 - a b + 4/3 b^2, and the
+// WENO-Z map w~_r = d_r (1 + tau/(eps + beta_r)), tau = |beta_0 - beta_2|,
+// eps = 1e-6 (Sec. 2.4).
 template <typename T, bool LEFT>
-__device__ __forceinline__ T nu_wenoz_integral(const T* tw, const T* v, int n, int i) {
+__device__ __forceinline__ T nu_wenoz_defect(const T* tw, const T* v, int n, int i) {
   T w[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) w[k] = LEFT ? v[3 + i - (k - 3)] : v[3 + i + (k - 3)];
@@ -228,10 +234,14 @@ __device__ __forceinline__ T nu_wenoz_integral(const T* tw, const T* v, int n, i
     T J = T(0), a = T(0), b = T(0);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      const T val = w[r + j];
-      J = fma(tw[(3 * r + j) * n + i], val, J);
-      a = fma(tw[(12 + 3 * r + j) * n + i], val, a);
-      b = fma(tw[(21 + 3 * r + j) * n + i], val, b);
+      // differences from the centre: the derivative rows sum to zero, so a
+      // and b change sign only (beta is even in (a, b)), and the centre's
+      // term drops
+      if (r + j == 3) continue;
+      const T dj = w[3] - w[r + j];
+      J = fma(tw[(3 * r + j) * n + i], dj, J);
+      a = fma(tw[(12 + 3 * r + j) * n + i], dj, a);
+      b = fma(tw[(21 + 3 * r + j) * n + i], dj, b);
     }
     Jr[r] = J;
     beta[r] = fma(a, a - b, T(4.0 / 3.0) * b * b);
@@ -249,18 +259,27 @@ __device__ __forceinline__ T nu_wenoz_integral(const T* tw, const T* v, int n, i
   return num * weight_rcp(sum);
 }
 
-// One direction with the periodic closure, split over the `nw` warps of the
-// line (segment `seg` <= 512 scan positions each, R ascending, L
-// descending).  Each warp computes the local integrals J and decays q of its
-// segment once (chunks of 32 x 4 points, kept in registers), the per-lane
-// affine maps x -> q x + J composed by a warp scan per chunk; the segments'
-// maps meet in shared memory (maps[2 * nw]); the line's last value from
-// I = 0 closes the period (x = I_end / (1 - mu)); each warp then replays its
-// chunks from its closed start value and stores by OUT: 1 I in w, 2 D = v - I
-// in w, 3 D = v - (w + I)/2 in w (w holding I_R: the L pass of L_0).
+// One direction, split over the `nw` warps of the line (segment `seg` <= 512
+// scan positions each, R ascending, L descending), in difference form: the
+// scan carries W = v - I, which obeys the recurrence of I with the forcing
+// K_i = v_i - q_i v_{i-1} - J_R(x_i) = sum_l c_{i,l} (v_i - v_{i+l}) +
+// q_i (v_i - v_{i-1}) (mirrored for L; the rules integrate constants to
+// 1 - q_i), so W of constant data is exactly zero and on smooth data its
+// rounding error scales with the differences, not with v.  Each warp
+// computes K and the decays of its segment once (chunks of 32 x 4 points,
+// kept in registers), the per-lane affine maps x -> q x + K composed by a
+// warp scan per chunk; the segments' maps meet in shared memory
+// (maps[2 * nw]) and give the line's end value from W = 0, `all`.  The value
+// entering the line is then k1 * all + start0: the periodic closure (k1 =
+// 1/(1 - mu), start0 = 0) or a Dirichlet line's boundary value of W (the
+// recurrence starts at the end node, whose decay is taken as 1 so that the
+// scan passes the start value on unchanged; K there is zero).  Each warp
+// replays its chunks from its start value and stores by OUT: 0 nothing (the
+// total only), 1 W in w (D_R or D_L, or W_R of L_0), 3 D_0 = (w + W)/2 in w
+// (w holding W_R: the L pass of L_0).  Returns `all`.
 template <typename T, bool LEFT, int OUT, bool WENO>
-__device__ __forceinline__ void nu_direction(const NuTables<T>& tb, const T* v, T* w, int n, int nw, int part,
-                                             int seg, T k1, T* maps, int lane) {
+__device__ __forceinline__ T nu_direction(const NuTables<T>& tb, const T* v, T* w, int n, int nw, int part, int seg,
+                                          double k1, double start0, bool dirichlet, T* maps, int lane) {
   constexpr int kPer = 4, kChunks = 4;          // seg <= kChunks * 32 * kPer
   const int s0 = min(n, part * seg), s1 = min(n, s0 + seg);
   T jk[kChunks][kPer], qk[kChunks][kPer];
@@ -277,20 +296,24 @@ __device__ __forceinline__ void nu_direction(const NuTables<T>& tb, const T* v, 
       jk[c][k] = T(0);
       if (step < s1) {
         const int i = LEFT ? n - 1 - step : step;
-        T J = T(0);
+        const T vc = v[3 + i];
+        T K = T(0);
         if constexpr (WENO) {
-          J = nu_wenoz_integral<T, LEFT>(LEFT ? tb.cL : tb.cR, v, n, i);
+          K = nu_wenoz_defect<T, LEFT>(LEFT ? tb.cL : tb.cR, v, n, i);
         } else {
 #pragma unroll
           for (int m = 0; m < 6; ++m) {
             const int off = m - 3;
-            if (LEFT) J = fma(tb.cL[m * n + i], v[3 + i - off], J);
-            else J = fma(tb.cR[m * n + i], v[3 + i + off], J);
+            if (off == 0) continue;          // the centre's difference is 0
+            if (LEFT) K = fma(tb.cL[m * n + i], vc - v[3 + i - off], K);
+            else K = fma(tb.cR[m * n + i], vc - v[3 + i + off], K);
           }
         }
-        qk[c][k] = LEFT ? tb.q[i + 1 < n ? i + 1 : 0] : tb.q[i];
-        jk[c][k] = J;
-        B = fma(qk[c][k], B, J);
+        const T qi = LEFT ? tb.q[i + 1 < n ? i + 1 : 0] : tb.q[i];
+        K = fma(qi, vc - v[3 + i + (LEFT ? 1 : -1)], K);
+        qk[c][k] = (dirichlet && step == 0) ? T(1) : qi;
+        jk[c][k] = K;
+        B = fma(qk[c][k], B, K);
         A *= qk[c][k];
       }
     }
@@ -319,15 +342,21 @@ __device__ __forceinline__ void nu_direction(const NuTables<T>& tb, const T* v, 
     maps[2 * part + 1] = sB;
   }
   __syncthreads();
-  // value before this segment from I = 0 before the line, and the line's end value
+  // value before this segment from W = 0 before the line, and the line's end value
   T pre = T(0), all = T(0), gA = T(1);
   for (int j = 0; j < nw; ++j) {
     if (j == part) pre = all;
     if (j < part) gA *= maps[2 * j];
     all = fma(maps[2 * j], all, maps[2 * j + 1]);
   }
-  // closed start: the closure value carried through the earlier segments
-  T carry = fma(gA, all * k1, pre);
+  if constexpr (OUT == 0) {
+    __syncthreads();   // maps[] is reused by the next pass
+    return all;
+  }
+  // the start value carried through the earlier segments
+  // (the boundary algebra in FP64: 1/(1 - mu) and 2/(1 - mu^2) grow large as
+  // alpha times the line length shrinks)
+  T carry = fma(gA, T(fma(double(all), k1, start0)), pre);
 #pragma unroll
   for (int c = 0; c < kChunks; ++c) {
     const int c0 = s0 + c * 32 * kPer;
@@ -339,22 +368,22 @@ __device__ __forceinline__ void nu_direction(const NuTables<T>& tb, const T* v, 
         y = fma(qk[c][k], y, jk[c][k]);
         const int i = LEFT ? n - 1 - step : step;
         if constexpr (OUT == 1) w[i] = y;
-        if constexpr (OUT == 2) w[i] = v[3 + i] - y;
-        if constexpr (OUT == 3) w[i] = v[3 + i] - T(0.5) * (w[i] + y);
+        if constexpr (OUT == 3) w[i] = T(0.5) * (w[i] + y);
       }
     }
     carry = fma(At[c], carry, Bt[c]);
   }
   __syncthreads();
+  return all;
 }
 
-// S_P along non-uniform periodic lines: one CTA of `nw` warps per line (the
+// S_P along non-uniform lines, periodic or Dirichlet: one CTA of `nw` warps per line (the
 // scan positions split into nw segments of at most 512); shared memory: v
 // (n + 6) and w (n) of T plus the segment maps.  WENO: local integrals by
 // WENO-Z with the point-local tables, else the linear point weights.
 template <typename T, typename TIO, bool WENO>
 __global__ void __launch_bounds__(512, 1) nonuniform_kernel(const NuArgs a, const NuTables<T> tb) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int n = a.g.n;
   const int nw = blockDim.x >> 5, part = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long line = blockIdx.x;
@@ -368,19 +397,44 @@ __global__ void __launch_bounds__(512, 1) nonuniform_kernel(const NuArgs a, cons
   TIO* out = static_cast<TIO*>(a.out);
   for (int i = threadIdx.x; i < n; i += blockDim.x) v[3 + i] = T(in[base + i * st]);
   __syncthreads();
-  const T k1 = T(a.inv1mmu);
+  const bool dir = a.bc == 1;
+  const double k1 = dir ? 0.0 : a.inv1mmu;
   for (int p = 0; p < a.P; ++p) {
     if (threadIdx.x < 3) {
       const int j = threadIdx.x + 1;
-      v[3 - j] = v[3 + ((n - j) % n + n) % n];
-      v[3 + n - 1 + j] = v[3 + (j - 1) % n];
+      if (dir) {
+        // odd reflection about the end values (mirrored ghost nodes, Sec. 2.3)
+        v[3 - j] = T(2) * v[3] - v[3 + j];
+        v[3 + n - 1 + j] = T(2) * v[3 + n - 1] - v[3 + n - 1 - j];
+      } else {
+        v[3 - j] = v[3 + ((n - j) % n + n) % n];
+        v[3 + n - 1 + j] = v[3 + (j - 1) % n];
+      }
     }
     __syncthreads();
-    // D into w: R alone, L alone, or I_R first and then the L pass of L_0
-    if (a.mode == MODE_R) nu_direction<T, false, 2, WENO>(tb, v, w, n, nw, part, seg, k1, maps, lane);
-    if (a.mode == MODE_0) nu_direction<T, false, 1, WENO>(tb, v, w, n, nw, part, seg, k1, maps, lane);
-    if (a.mode == MODE_L) nu_direction<T, true, 2, WENO>(tb, v, w, n, nw, part, seg, k1, maps, lane);
-    if (a.mode == MODE_0) nu_direction<T, true, 3, WENO>(tb, v, w, n, nw, part, seg, k1, maps, lane);
+    // D into w: R alone, L alone, or W_R first and then the L pass of L_0.
+    // Dirichlet start values (Sec. 2.3, the 2x2 algebra of Sec. 3.3):
+    // L_R^{-1}(a) = v(a) and L_L^{-1}(b) = v(b), so W starts from 0; for L_0
+    // the passes start from 2A and 2B with [[1, mu], [mu, 1]] (A, B) =
+    // (v(a) - I_0(a), v(b) - I_0(b)), which in terms of the W totals from
+    // zero starts, W_R^0(b) and W_L^0(a), is W_R(a) = (kd/2) (mu W_R^0(b) -
+    // W_L^0(a)) and W_L(b) = (kd/2) (mu W_L^0(a) - W_R^0(b)), kd =
+    // 2/(1 - mu^2): the L total comes first
+    if (a.mode == MODE_R) nu_direction<T, false, 1, WENO>(tb, v, w, n, nw, part, seg, k1, 0.0, dir, maps, lane);
+    if (a.mode == MODE_L) nu_direction<T, true, 1, WENO>(tb, v, w, n, nw, part, seg, k1, 0.0, dir, maps, lane);
+    if (a.mode == MODE_0) {
+      if (!dir) {
+        nu_direction<T, false, 1, WENO>(tb, v, w, n, nw, part, seg, k1, 0.0, false, maps, lane);
+        nu_direction<T, true, 3, WENO>(tb, v, w, n, nw, part, seg, k1, 0.0, false, maps, lane);
+      } else {
+        const double hk = 0.5 * a.kdir, km = hk * a.mu;
+        const double WL =
+            double(nu_direction<T, true, 0, WENO>(tb, v, w, n, nw, part, seg, 0.0, 0.0, true, maps, lane));
+        const double WR =
+            double(nu_direction<T, false, 1, WENO>(tb, v, w, n, nw, part, seg, km, -hk * WL, true, maps, lane));
+        nu_direction<T, true, 3, WENO>(tb, v, w, n, nw, part, seg, km, -hk * WR, true, maps, lane);
+      }
+    }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const T d = w[i];
       TIO* o = out + base + i * st;

@@ -102,3 +102,36 @@ def test_hj_on_stretched_grids_converges_first_order():
         errs.append(np.abs(u - exact(x, t)).max())
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert all(0.7 < r < 1.8 for r in rates), (errs, rates)
+
+
+def test_uniform_nodes_reproduce_the_uniform_advection_diffusion_step():
+    ny, nx, L = 10, 14, 2.0
+    u = 1.0 + 0.3 * np.random.default_rng(37).standard_normal((ny, nx))
+    hx, hy = L / nx, L / ny
+    grids = ((L * np.arange(ny) / ny, L), (L * np.arange(nx) / nx, L))
+    for kind, kappa, rk3 in (("burgers", 0.05, True), ("linear", 0.0, False)):
+        got = schemes.advdiff_step(u, [hy, hx], 0.05, kind, [0.5, -1.0], 2.0, kappa=kappa, beta=0.6, npts=6,
+                                   P=3 if rk3 else 1, rk3=rk3, grids=grids)
+        want = schemes.advdiff_step(u, [hy, hx], 0.05, kind, [0.5, -1.0], 2.0, kappa=kappa, beta=0.6, npts=6,
+                                    P=3 if rk3 else 1, rk3=rk3)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+
+
+def test_advection_diffusion_on_a_stretched_grid_converges_at_third_order():
+    """u_t + u_x = kappa u_xx on a stretched periodic grid, u0 = sin x, SSP-RK3
+    with P = 3, dt = h/2, to T = 0.5: the exact solution is
+    e^{-kappa t} sin(x - t); halving h cuts the error about 8 times (third
+    order in time, Sec. 2.5: an s-stage method with s-term sums)."""
+    L, kappa, T = 2 * np.pi, 0.1, 0.5
+    errs = []
+    for n in (24, 48):
+        x = _stretch(L * np.arange(n) / n, L, 0.3)
+        dt = 0.5 * L / n
+        steps = int(round(T / dt))
+        u = np.sin(x)
+        for _ in range(steps):
+            u = schemes.advdiff_step(u, [L / n], dt, "linear", [1.0], 1.0, kappa=kappa, beta=0.6, npts=6, P=3,
+                                     rk3=True, grids=((x, L),))
+        errs.append(np.abs(u - math.exp(-kappa * steps * dt) * np.sin(x - steps * dt)).max())
+    assert errs[1] < 1e-3
+    assert errs[0] / errs[1] > 6.5, errs
