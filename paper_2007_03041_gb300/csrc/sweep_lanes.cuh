@@ -129,7 +129,7 @@ __device__ __forceinline__ int xsw(int l, int p) {
   return ((p >> 5) << 10) + (l << 5) + ((((p >> 2) & 7) ^ (l & 7)) << 2) + (p & 3);
 }
 
-// Issues the copies of tile `tile` into `buf` (warp 0; lane 0 arms the barrier first).
+// Issues the copies of tile `tile` into `buf` (the producer warp; lane 0 arms the barrier first).
 __device__ __forceinline__ void lanes_issue(const LanesArgs& a, const CUtensorMap* map, float* buf, int tile,
                                             uint64_t* bar) {
   const int lane = threadIdx.x & 31;
@@ -294,10 +294,17 @@ __device__ __forceinline__ int lanes_right(const LanesArgs& a, int m) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// Wait on an mbarrier phase with a suspend-time hint: the thread sleeps until
-// the phase completes or the hint elapses, so a waiting warp takes no issue
-// slots (a plain try_wait returns almost at once and a loop around it spins).
-constexpr uint32_t kLanesSuspendNs = 20000;
+// Wait on an mbarrier phase with a suspend-time hint (the thread may sleep
+// until the phase completes or the hint elapses).
+#ifndef MOLT_LANES_SUSPEND_NS
+#define MOLT_LANES_SUSPEND_NS 20000
+#endif
+constexpr uint32_t kLanesSuspendNs = MOLT_LANES_SUSPEND_NS;
+// Segment whose warp issues the tile copies (the end segments also solve the
+// line constants, so a middle one keeps the two roles apart).
+#ifndef MOLT_LANES_PRODUCER
+#define MOLT_LANES_PRODUCER 0
+#endif
 __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -309,13 +316,43 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
       : "memory");
   return ok != 0;
 }
+// Polling form of the waits: 0 try_wait with the suspend-time hint, 1
+// test_wait with a doubling __nanosleep between polls (32 .. 512 ns), 2
+// try_wait without a hint (the default).  Measured on the 512^3 wave step:
+// the hint (100 ns .. 200 us) changes nothing, the sleeps cost 10% (the waits
+// sit on the tile's critical path, so a late wake-up delays it) and 2 is 1%
+// faster than 0.
+#ifndef MOLT_LANES_WAIT_MODE
+#define MOLT_LANES_WAIT_MODE 2
+#endif
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool lanes_poll(uint64_t* bar, uint32_t parity) {
+  if constexpr (MOLT_LANES_WAIT_MODE == 1) return mbar_test_wait(bar, parity);
+  if constexpr (MOLT_LANES_WAIT_MODE == 2) return mbar_try_wait(bar, parity);
+  return mbar_try_wait_sleep(bar, parity);
+}
 // Bounded wait on an mbarrier phase: the clock is read only once every 16
-// sleeps, and the wait gives up after `limit` cycles.
+// polls, and the wait gives up after `limit` cycles.
 __device__ __forceinline__ bool lanes_mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
-  if (mbar_try_wait_sleep(bar, parity)) return true;
+  if (lanes_poll(bar, parity)) return true;
   const long long t0 = clock64();
+  unsigned ns = 32;
   for (int i = 1;; ++i) {
-    if (mbar_try_wait_sleep(bar, parity)) return true;
+    if constexpr (MOLT_LANES_WAIT_MODE == 1) {
+      __nanosleep(ns);
+      if (ns < 512) ns <<= 1;
+    }
+    if (lanes_poll(bar, parity)) return true;
     if ((i & 15) == 0 && clock64() - t0 > limit) return false;
   }
 }
@@ -543,12 +580,17 @@ __device__ __forceinline__ bool lanes_stage2(const LanesArgs& a, const LanesSmem
   return true;
 }
 
+__device__ __forceinline__ int lanes_producer(const LanesArgs& a) {
+  return MOLT_LANES_PRODUCER < a.S ? MOLT_LANES_PRODUCER : a.S - 1;
+}
+
 // A warp gives up (a bounded wait ran out): record it and, in the copy-issuing
 // warp, wait (bounded) for the copy it may still have in flight.
 __device__ __forceinline__ void lanes_give_up(const LanesArgs& a, const LanesSmem& sm, int seg, int lane,
                                               int inflight_buf, uint32_t inflight_parity) {
   if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
-  if (seg == 0 && inflight_buf >= 0) lanes_mbar_wait(&sm.full[inflight_buf], inflight_parity, a.wait_limit);
+  if (seg == lanes_producer(a) && inflight_buf >= 0)
+    lanes_mbar_wait(&sm.full[inflight_buf], inflight_parity, a.wait_limit);
 }
 
 template <int EPI, bool CONTIG, int LB>
@@ -558,6 +600,7 @@ __global__ void __launch_bounds__(kLMaxSeg * 32, 1)
   const LanesSmem sm = lanes_carve(smem_raw, a, CONTIG);
   const int S = a.S;
   const int seg = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int prod = lanes_producer(a);
   if (threadIdx.x < S) {
     const int m = threadIdx.x;
     int cnt = 0;
@@ -580,7 +623,7 @@ __global__ void __launch_bounds__(kLMaxSeg * 32, 1)
   // tiles k = 0 and 1 of this CTA go into buffers 0 and 1; buffer k % 3 holds
   // tile k, and its u-th use completes phase u of its full/empty barriers
   for (int i = 0; i < kLBuf - 1; ++i)
-    if (seg == 0 && tile + i * int(gridDim.x) < ntiles)
+    if (seg == prod && tile + i * int(gridDim.x) < ntiles)
       lanes_issue(a, &map, sm.buf0 + i * sm.bstride, tile + i * int(gridDim.x), &sm.full[i]);
 
   int b = 0, use = 0;      // buffer of tile k and its use count
@@ -597,7 +640,7 @@ __global__ void __launch_bounds__(kLMaxSeg * 32, 1)
     const int ahead = tile + (kLBuf - 1) * int(gridDim.x);
     const int bn = b == 0 ? kLBuf - 1 : b - 1;    // (k + 2) % 3 == (k - 1) % 3
     const int use_prev = bn < b ? use : use - 1;  // uses of buffer bn before tile k-1's (k >= 1)
-    if (seg == 0 && ahead < ntiles) {
+    if (seg == prod && ahead < ntiles) {
       if (k >= 1 &&
           !__all_sync(0xffffffffu, lanes_mbar_wait(&sm.empty[bn], uint32_t(use_prev & 1), a.wait_limit))) {
         lanes_give_up(a, sm, seg, lane, -1, 0);
@@ -607,7 +650,7 @@ __global__ void __launch_bounds__(kLMaxSeg * 32, 1)
     }
     // the copy a give-up waits for: tile k+2's (phase use_prev + 1 of buffer
     // bn; k = 0: its first phase)
-    const int inflight = (seg == 0 && ahead < ntiles) ? bn : -1;
+    const int inflight = (seg == prod && ahead < ntiles) ? bn : -1;
     const uint32_t inflight_parity = uint32_t(k >= 1 ? (use_prev + 1) & 1 : 0);
     // L2 prefetch of the rows this warp's epilogue reads
     if constexpr (EPI == EPI_ACC_ADD || EPI == EPI_ACC_AXPY) {

@@ -79,3 +79,18 @@ def assert_parity(got, want, tol_l2, tol_max, line_axis=None, what=""):
             assert ee <= tol_max, "%s %s %d points of the lines: %.3e > %.1e" % (what, name, k, ee, tol_max)
     return e2, em
 
+
+
+def max_bound(tol_l2):
+    """The element-wise bound (over max|want|) that goes with a relative-L2
+    bound: the FP64 one for FP64 tolerances, else twice the L2 bound."""
+    return MAX_F64 if tol_l2 <= TOL_F64 else 2.0 * tol_l2
+
+
+def assert_grid_parity(got, want, tol_l2, what="", ends=True):
+    """assert_parity with the element-wise bound of ``tol_l2`` and, with
+    ``ends``, the first and last 4 points of the lines along every axis of
+    the grid (sampled points: ends=False)."""
+    want = np.asarray(want)
+    for ax in (range(want.ndim) if ends and want.ndim else [None]):
+        assert_parity(got, want, tol_l2, max_bound(tol_l2), line_axis=ax, what=what)

@@ -10,7 +10,7 @@ import pytest
 from oracle import schemes
 from paper_2007_03041_gb300 import molt as M
 from paper_2007_03041_gb300 import workloads
-from tests.gpu_util import need_gpu, rel_l2, state_dtype, to_dev, tol_for
+from tests.gpu_util import need_gpu, rel_l2, state_dtype, to_dev, tol_for, assert_grid_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -67,7 +67,7 @@ def test_advdiff_steps_match_oracle(case):
     want = u0
     for _ in range(steps):
         want = schemes.advdiff_step(want, hs_xyz[::-1], dt, kind, vel[::-1], c, kappa, beta, npts, P, rk3, wname)
-    assert rel_l2(got, want) < tol_for(prec)
+    assert_grid_parity(got, want, tol_for(prec), what=str(case))
     assert abs(t[0] - steps * dt) < 1e-12
 
 

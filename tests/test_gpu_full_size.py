@@ -23,7 +23,7 @@ from oracle import mlp, schemes, stability, sweep
 from oracle.quadrature import QuadratureRule
 from paper_2007_03041_gb300 import molt as M
 from paper_2007_03041_gb300 import workloads
-from tests.gpu_util import TOL_F32, TOL_F64, need_gpu, rel_l2
+from tests.gpu_util import TOL_F32, TOL_F64, need_gpu, rel_l2, assert_grid_parity
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -75,7 +75,7 @@ def test_heat_256_fp64_matches_closed_form():
         M.molt_destroy(ctx)
     iy, ix = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     pts = (iy.ravel(), ix.ravel())
-    assert rel_l2(got10, _modal_heat(n, workloads.SEED_HEAT, 10, points=pts).reshape(n, n)) < TOL_F64
+    assert_grid_parity(got10, _modal_heat(n, workloads.SEED_HEAT, 10, points=pts).reshape(n, n), TOL_F64)
     want100 = _modal_heat(n, workloads.SEED_HEAT, 100, points=pts).reshape(n, n)
     assert np.abs(got100 - want100).max() < TOL_F64 * np.abs(u0).max()
 
@@ -101,7 +101,7 @@ def test_batched_64_full_sizes_match_closed_form():
     for i, (n, g) in enumerate(zip(sides, got)):
         iy, ix = _sample_points(n, 512, 100 + i)
         want = _modal_heat(n, 3000 + i, 3, points=(iy, ix))
-        assert rel_l2(g[iy, ix], want) < TOL_F32, (i, n)
+        assert_grid_parity(g[iy, ix], want, TOL_F32, what=str((i, n)), ends=False)
 
 
 def _wave_lines(u, pts):
@@ -146,7 +146,7 @@ def test_wave_512_start_and_leapfrog_steps_at_sampled_points():
     k, j, i = pts
     idx = [i, j, k]
     want1 = u0[pts] - 0.5 * beta ** 2 * sum(S[a][np.arange(len(i)), idx[a]] for a in range(3))
-    assert rel_l2(u1[pts], want1) < TOL_F32
+    assert_grid_parity(u1[pts], want1, TOL_F32, ends=False)
     # u^2 at two points near bump centres: u^1 on the three lines through each
     # point from the lines of u^0 through every point of those lines
     for p in range(2):
@@ -199,8 +199,8 @@ def _hj_first_step(n, seed, weights, blob=None, fn=None, wname="wenoz", samples=
     inc_gpu = u1[iy, ix].astype(np.float64) - u064[iy, ix]
     inc_want = -dt * Hh
     # the state is FP32 (rounding 6e-8 of |u| ~ 2, against increments ~1e-3)
-    assert rel_l2(inc_gpu, inc_want) < 1e-3
-    assert rel_l2(u1[iy, ix], u064[iy, ix] + inc_want) < TOL_F32
+    assert_grid_parity(inc_gpu, inc_want, 1e-3, ends=False)
+    assert_grid_parity(u1[iy, ix], u064[iy, ix] + inc_want, TOL_F32, ends=False)
     # lagged time step of the first step: dt = CFL h / max over the grid of
     # the speeds of u^0 <= CFL h / (max over the samples)
     assert 0 < dt <= 1.5 * h / max(speeds) * (1 + 1e-6)

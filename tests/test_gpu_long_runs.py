@@ -9,7 +9,10 @@
   at sampled points;
 * 2-D Hamilton-Jacobi (WENO-Z, FP32, CFL 1.5, lagged adaptive dt): all 500
   steps on a 256^2 grid (the oracle's partial sums on blocks of lines in a
-  process pool), well past the formation of the kinks.
+  process pool), well past the formation of the kinks;
+* the same with learned WENO weights (the network, trained by the oracle's
+  own Adam on stencils of the oracle's states, with the WENO-Z fallback):
+  50 steps on a 512^2 grid against the oracle's BF16-emulated forward.
 
 The wave and heat states are held to the FP32 path's stated tolerance:
 relative L2 1e-5, plus the largest pointwise error over the largest value
@@ -21,10 +24,11 @@ import math
 import numpy as np
 import pytest
 
-from oracle import dense, stability
+from oracle import dense, mlp, stability, sweep
+from oracle.quadrature import QuadratureRule
 from paper_2007_03041_gb300 import molt as M
 from paper_2007_03041_gb300 import workloads
-from tests.gpu_util import need_gpu, to_dev, assert_parity, rel_l2, max_rel, TOL_F32, MAX_F32
+from tests.gpu_util import need_gpu, to_dev, assert_parity, rel_l2, max_rel, TOL_F32, MAX_F32, assert_grid_parity
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -109,7 +113,7 @@ def test_batched_64_problems_200_steps_closed_form():
         err = np.abs(gi[iy, ix] - want).max()
         assert err <= TOL_F32 * np.abs(a0).max(), (i, n, err)
         if np.abs(want).max() > 1e-3 * np.abs(a0).max():
-            assert rel_l2(gi[iy, ix], want) < TOL_F32, (i, n)
+            assert_grid_parity(gi[iy, ix], want, TOL_F32, what=str((i, n)), ends=False)
 
 
 def test_hj_wenoz_500_steps():
@@ -157,3 +161,89 @@ def test_hj_wenoz_500_steps():
             assert_parity(got_k, want, tl2, tmax, line_axis=ax, what="HJ u^%d" % k)
     assert checks[early][1] == TOL_F32      # before the kinks FP32 storage alone stays below the stated bound
     assert abs(t[0] - ta) < 1e-3 * ta
+
+
+NU_HJ = 1.0 / 1.5   # nu = alpha h = beta / CFL of the Hamilton-Jacobi runs
+
+
+def _oracle_trained_theta(states, seed=workloads.SEED_MLP, steps=300, batch=2048, lr=3e-3):
+    """A network trained entirely by the oracle: stencils of the given states
+    (both axes and sides, seeded positions), WENO-Z targets, minibatch Adam in
+    FP64 on the BF16-emulated loss.  Returns the FP32 master parameters."""
+    rule = QuadratureRule(NU_HJ, 5)
+    X = []
+    for k, u in enumerate(states):
+        ny, nx = u.shape
+        for axis in (0, 1):
+            for side in (0, 1):
+                pos = workloads.mlp_positions(batch * steps // (4 * len(states)) + 1, nx, ny,
+                                              seed + 4 * k + 2 * axis + side)
+                X.append(mlp.stencils(u, pos, axis, side))
+    X = np.concatenate(X)
+    X = X[workloads.rng(seed).permutation(len(X))]
+    Y = sweep._weno_weights(rule, X)
+    theta = workloads.mlp_initial_params(seed).astype(np.float64)
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    for s in range(1, steps + 1):
+        r0 = ((s - 1) * batch) % (len(X) - batch)
+        _, g = mlp.loss_and_grad(theta, mlp.normalise(X[r0:r0 + batch]), Y[r0:r0 + batch], emulate_bf16=True)
+        theta, m, v = mlp.adam_step(theta, m, v, g, s, lr)
+    return theta.astype(np.float32)
+
+
+def test_hj_learned_50_steps():
+    """The learned-weight form (BF16 network + WENO-Z fallback, FP32) over 50
+    steps at 512^2.  Held as the WENO-Z run is: to the stated tolerance, or to
+    twice the distance of the oracle's own FP32-state run from the FP64
+    oracle where that is larger -- here a fallback decision taken on the other
+    side of the 1e-2 threshold is one more FP32-size perturbation -- at step
+    20 and at step 50.  The network falls back on part of the stencils only."""
+    need_gpu()
+    import torch
+    from oracle.parallel import LinePool
+    n, early, nsteps = 512, 20, 50
+    h = 2 * np.pi / n
+    u0 = workloads.hj_initial(n)
+    start = u0.astype(np.float32).astype(np.float64)
+    with LinePool() as pool:
+        # training states: u^0 and the oracle's WENO-Z state after 40 steps
+        sp = pool.hj_initial_speeds(start, [h, h])
+        w = start
+        for _ in range(40):
+            w, _, sp = pool.hj_step(w, [h, h], sp)
+        theta32 = _oracle_trained_theta([start, w])
+        theta = theta32.astype(np.float64)
+        d = M.make_desc((n, n), lo=[0, 0], hi=[2 * np.pi] * 2, P=1, quad_points=5, weights=M.W_LEARNED,
+                        beta=1.0, pde=M.PDE_HJ, cfl=1.5, dt=0.0, prec=M.PREC_F32)
+        ctx = M.molt_create(d)
+        try:
+            th = torch.tensor(theta32, device="cuda")
+            blob = torch.empty(M.MLP_BLOB_BYTES, dtype=torch.uint8, device="cuda")
+            M.molt_mlp_pack(th, blob)
+            M.molt_set_mlp(ctx, blob)
+            u = to_dev(u0, torch.float32)
+            t = M.molt_step(ctx, u, None, nsteps=early, t=[0.0])
+            got_early = u.double().cpu().numpy()
+            t = M.molt_step(ctx, u, None, nsteps=nsteps - early, t=t)
+            got = u.double().cpu().numpy()
+            evaluated, fallbacks = M.molt_mlp_stats(ctx)
+        finally:
+            M.molt_destroy(ctx)
+        a, b = start, start
+        ta = 0.0
+        checks = {}
+        sa = sb = pool.hj_initial_speeds(start, [h, h], 1.5, 1.0, 5, "learned", theta)
+        for k in range(1, nsteps + 1):
+            a, dta, sa = pool.hj_step(a, [h, h], sa, 1.5, 1.0, 5, "learned", theta)
+            b, _, sb = pool.hj_step(b, [h, h], sb, 1.5, 1.0, 5, "learned", theta)
+            b = b.astype(np.float32).astype(np.float64)
+            ta += dta
+            if k in (early, nsteps):
+                checks[k] = (a, max(TOL_F32, 2 * rel_l2(b, a)), max(MAX_F32, 2 * max_rel(b, a)))
+    for k, got_k in ((early, got_early), (nsteps, got)):
+        want, tl2, tmax = checks[k]
+        for ax in range(2):
+            assert_parity(got_k, want, tl2, tmax, line_axis=ax, what="learned HJ u^%d" % k)
+    assert abs(t[0] - ta) < 1e-3 * ta
+    assert 0 < fallbacks < evaluated

@@ -28,7 +28,7 @@ from oracle import mlp, schemes, sweep
 from oracle.quadrature import QuadratureRule
 from paper_2007_03041_gb300 import molt as M
 from paper_2007_03041_gb300 import workloads
-from tests.gpu_util import TOL_F32, need_gpu, rel_l2, to_dev
+from tests.gpu_util import TOL_F32, need_gpu, rel_l2, to_dev, assert_grid_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -231,7 +231,7 @@ def test_learned_sweep_with_input_independent_network(op, axis):
     fn = mlp.learned_weight_fn(theta.astype(np.float64), rule, emulate_bf16=True)
     opn = {M.OP_R: "R", M.OP_L: "L", M.OP_0: "0"}[op]
     want = sweep.partial_sum(u.astype(np.float64), 1 - axis, alpha, h, opn, "periodic", 5, 1, "learned", fn)
-    assert rel_l2(got, want) < TOL_F32
+    assert_grid_parity(got, want, TOL_F32)
     assert evaluated == 2 * nx * ny
     assert 0 < fallbacks < evaluated
 
@@ -293,7 +293,7 @@ def test_learned_hj_steps_with_input_independent_network():
     for _ in range(3):
         uu, dt, speeds = schemes.hj_step(uu, [h, h], speeds, 1.5, 1.0, 5, "learned", fn)
         tt += dt
-    assert rel_l2(got, uu) < TOL_F32
+    assert_grid_parity(got, uu, TOL_F32)
     assert abs(t[0] - tt) < 1e-4 * tt
 
 
@@ -357,4 +357,4 @@ def test_training_on_harvested_stencils_and_what_it_gains():
         finally:
             M.molt_destroy(ctx)
 
-    assert rel_l2(run(M.W_LEARNED, b0), run(M.W_WENOZ)) < TOL_F32
+    assert_grid_parity(run(M.W_LEARNED, b0), run(M.W_WENOZ), TOL_F32)

@@ -11,7 +11,7 @@ from oracle import nonuniform
 from paper_2007_03041_gb300 import molt as M
 from paper_2007_03041_gb300 import workloads
 from tests.gpu_util import (MAX_F32, TOL_F32, assert_parity, max_for, need_gpu, rel_l2, state_dtype, to_dev,
-                            tol_for)
+                            tol_for, assert_grid_parity)
 
 pytestmark = pytest.mark.gpu
 OPS = {M.OP_L: "L", M.OP_R: "R", M.OP_0: "0"}
@@ -199,7 +199,7 @@ def test_wenoz_keeps_a_jump_sharp_and_differs_from_the_linear_rule():
     want = nonuniform.partial_sum(v, x, L, alpha, "R", 5, 1, "wenoz")
     lin = nonuniform.partial_sum(v, x, L, alpha, "R", 5, 1)
     got = _run_line(x, lo, L, v, M.OP_R, 1, alpha, M.PREC_F64, M.W_WENOZ)
-    assert rel_l2(got, want) < 1e-12
+    assert_grid_parity(got, want, 1e-12)
     assert rel_l2(got, lin) > 1e-3
 
 

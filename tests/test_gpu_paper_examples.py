@@ -15,7 +15,7 @@ import pytest
 from oracle import schemes, stability
 from paper_2007_03041_gb300 import molt as M
 from paper_2007_03041_gb300 import workloads
-from tests.gpu_util import TOL_F32, TOL_F64, need_gpu, rel_l2, state_dtype, to_dev, tol_for
+from tests.gpu_util import TOL_F32, TOL_F64, need_gpu, rel_l2, state_dtype, to_dev, tol_for, assert_grid_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -92,7 +92,7 @@ def test_hj_hamiltonians_and_source_match_oracle(ham, vel, h0, with_source, shap
     for k in range(steps):
         uu, dt, sp = schemes.hj_step(uu, hs, sp, source=src, t=tt, **kw)
         tt += dt
-        assert rel_l2(got[k], uu) < tol_for(prec), k
+        assert_grid_parity(got[k], uu, tol_for(prec), what=str(k))
         assert abs(ts[k] - tt) < (1e-10 if prec == M.PREC_F64 else 1e-5) * tt, k
 
 
@@ -121,7 +121,7 @@ def test_heat_forward_euler_matches_oracle(shape, P, npts, prec):
     uu = u0
     for _ in range(3):
         uu = schemes.heat_euler_step(uu, hs, h, beta=1.0, npts=npts, P=P)
-    assert rel_l2(got, uu) < tol_for(prec)
+    assert_grid_parity(got, uu, tol_for(prec))
 
 
 def test_invalid_hamiltonian_integrator_and_source_are_rejected():
@@ -254,7 +254,7 @@ def test_example3_manufactured_hj_matches_oracle_and_converges():
         uu, dt, sp = schemes.hj_step(uu, [h, h], sp, source=F, t=tt, **kw)
         tt += dt
     assert abs(t - tt) < 1e-10 * tt
-    assert rel_l2(u, uu) < 1e-11
+    assert_grid_parity(u, uu, 1e-11)
     # first-order convergence in the grid
     errs = [_manufactured_run(m, 0.5)[3] for m in (512, 1024, 2048)]
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
@@ -354,5 +354,5 @@ def test_hj_rk3_matches_oracle(ham, vel, h0, with_source, P, weights, npts, shap
     for k in range(steps):
         uu, dt, sp = schemes.hj_step_rk3(uu, hs, sp, t=tt, source=src, **kw)
         tt += dt
-        assert rel_l2(got[k], uu) < tol_for(prec), k
+        assert_grid_parity(got[k], uu, tol_for(prec), what=str(k))
         assert abs(ts[k] - tt) < (1e-10 if prec == M.PREC_F64 else 1e-5) * tt, k

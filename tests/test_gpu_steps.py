@@ -8,7 +8,7 @@ import pytest
 from oracle import schemes
 from paper_2007_03041_gb300 import molt as M
 from paper_2007_03041_gb300 import workloads
-from tests.gpu_util import need_gpu, rel_l2, to_dev, tol_for, state_dtype
+from tests.gpu_util import need_gpu, rel_l2, to_dev, tol_for, state_dtype, assert_grid_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -32,7 +32,7 @@ def test_heat_rk3_2d(prec, n):
     want = u0
     for _ in range(3):
         want = schemes.heat_step(want, [h, h], dt, 1.0, 0.6, None, 3, 3)
-    assert rel_l2(got, want) < tol_for(prec)
+    assert_grid_parity(got, want, tol_for(prec))
     assert abs(t[0] - 3 * dt) < 1e-15
 
 
@@ -59,8 +59,8 @@ def test_wave_leapfrog_3d_dirichlet(nsteps):
     for k in range(nsteps):
         nxt = schemes.wave_step(cur, prev, [h] * 3, dt, 1.0, 0.8, bc, 6, 2, from_rest=(k == 0))
         prev, cur = cur, nxt
-    assert rel_l2(got, cur) < 1e-5
-    assert rel_l2(gotp, prev) < 1e-5
+    assert_grid_parity(got, cur, 1e-5)
+    assert_grid_parity(gotp, prev, 1e-5)
 
 
 def test_wave_continues_across_calls_and_fp64():
@@ -86,7 +86,7 @@ def test_wave_continues_across_calls_and_fp64():
         for k in range(3):
             nxt = schemes.wave_step(cur, prev, [h] * 3, dt, 1.0, 0.8, ["dirichlet"] * 3, 6, 2, from_rest=(k == 0))
             prev, cur = cur, nxt
-        assert rel_l2(got, cur) < tol
+        assert_grid_parity(got, cur, tol)
         assert abs(t[0] - 3 * dt) < 1e-14
 
 
@@ -115,7 +115,7 @@ def test_hj_lagged_adaptive_2d(prec, weights):
     for _ in range(4):
         uu, dt, speeds = schemes.hj_step(uu, [h, h], speeds, 1.5, 1.0, 5, wname)
         tt += dt
-    assert rel_l2(got, uu) < tol_for(prec)
+    assert_grid_parity(got, uu, tol_for(prec))
     assert abs(t[0] - tt) < (1e-12 if prec == M.PREC_F64 else 1e-4) * tt
 
 
@@ -171,7 +171,7 @@ def test_hj_anisotropic_long_lines(nx, ny, prec, transposed):
     for _ in range(2):
         uu, dt, speeds = schemes.hj_step(uu, dxs, speeds, 1.5, 1.0, 5, "wenoz")
         tt += dt
-    assert rel_l2(got, uu) < tol_for(prec)
+    assert_grid_parity(got, uu, tol_for(prec))
     assert abs(t[0] - tt) < (1e-10 if prec == M.PREC_F64 else 1e-4) * tt
 
 
@@ -200,7 +200,7 @@ def test_other_dimensions(case):
             want = u0
             for _ in range(2):
                 want = schemes.heat_step(want, hs, dt, 1.0, 0.6, None, 3, 3)
-            assert rel_l2(got, want) < tol_for(prec), prec
+            assert_grid_parity(got, want, tol_for(prec), what=str(prec))
     elif case.startswith("wave"):
         shape = (64,) if case == "wave1d" else (40, 56)
         shape_xyz = tuple(reversed(shape))
@@ -227,7 +227,7 @@ def test_other_dimensions(case):
             for k in range(3):
                 nxt = schemes.wave_step(cur, prev, hs, dt, 1.0, 0.8, bcs, 6, 2, from_rest=(k == 0))
                 prev, cur = cur, nxt
-            assert rel_l2(got, cur) < tol_for(prec), prec
+            assert_grid_parity(got, cur, tol_for(prec), what=str(prec))
     else:
         n = 256
         h = 2 * np.pi / n
@@ -247,7 +247,7 @@ def test_other_dimensions(case):
             speeds = schemes.hj_initial_speeds(uu, [h], 1.5, 1.0, 5, "wenoz")
             for _ in range(3):
                 uu, _, speeds = schemes.hj_step(uu, [h], speeds, 1.5, 1.0, 5, "wenoz")
-            assert rel_l2(got, uu) < tol_for(prec), prec
+            assert_grid_parity(got, uu, tol_for(prec), what=str(prec))
 
 
 def test_hj_3d_is_rejected():

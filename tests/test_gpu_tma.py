@@ -7,7 +7,7 @@ import pytest
 from oracle import schemes, sweep
 from paper_2007_03041_gb300 import molt as M
 from paper_2007_03041_gb300 import workloads
-from tests.gpu_util import need_gpu, rel_l2, np_axis, to_dev, tol_for, state_dtype
+from tests.gpu_util import need_gpu, rel_l2, np_axis, to_dev, tol_for, state_dtype, assert_grid_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -53,9 +53,9 @@ CASES = [((512, 16, 32), 2), ((32, 512, 16), 1), ((4, 8, 1024), 0), ((16, 512), 
 def test_tma_sweep_matches_oracle_and_plain(prec, bc):
     for shape, axis in CASES:
         tma, plain, want = apply_both(shape, axis, M.OP_0, 2, 0.4, bc, 6, prec)
-        assert rel_l2(tma, want) < tol_for(prec), (shape, axis)
-        assert rel_l2(plain, want) < tol_for(prec), (shape, axis)
-        assert rel_l2(tma, plain) < 1e-13 * (1 if prec == M.PREC_F64 else 1e6), (shape, axis)
+        assert_grid_parity(tma, want, tol_for(prec), what=str((shape, axis)))
+        assert_grid_parity(plain, want, tol_for(prec), what=str((shape, axis)))
+        assert_grid_parity(tma, plain, 1e-13 * (1 if prec == M.PREC_F64 else 1e6), what=str((shape, axis)))
 
 
 # Long strided lines whose tiles hold fewer than 16 bytes of lines (one or two
@@ -68,16 +68,16 @@ LONG = [((4096, 1280), 1, M.PREC_F32), ((8192, 40), 1, M.PREC_F32), ((4096, 2, 6
 @pytest.mark.parametrize("shape,axis,prec", LONG)
 def test_tma_long_strided_lines_with_narrow_tiles(shape, axis, prec):
     tma, plain, want = apply_both(shape, axis, M.OP_0, 1, 0.5, M.BC_PERIODIC, 6, prec)
-    assert rel_l2(tma, want) < tol_for(prec)
-    assert rel_l2(plain, want) < tol_for(prec)
-    assert rel_l2(tma, plain) < 1e-13 * (1 if prec == M.PREC_F64 else 1e6)
+    assert_grid_parity(tma, want, tol_for(prec))
+    assert_grid_parity(plain, want, tol_for(prec))
+    assert_grid_parity(tma, plain, 1e-13 * (1 if prec == M.PREC_F64 else 1e6))
 
 
 @pytest.mark.parametrize("op", [M.OP_L, M.OP_R])
 def test_tma_wenoz_one_sided(op):
     tma, plain, want = apply_both((64, 512), 0, op, 1, 2.0 / 3.0, M.BC_PERIODIC, 5, M.PREC_F32, M.W_WENOZ)
-    assert rel_l2(tma, want) < 1e-5
-    assert rel_l2(plain, want) < 1e-5
+    assert_grid_parity(tma, want, 1e-5)
+    assert_grid_parity(plain, want, 1e-5)
 
 
 def test_wave_step_anisotropic_uses_tma_on_long_axis():
@@ -104,7 +104,7 @@ def test_wave_step_anisotropic_uses_tma_on_long_axis():
     for k in range(3):
         nxt = schemes.wave_step(cur, prev, dxs, dt, 1.0, 0.8, ["dirichlet"] * 3, 6, 2, from_rest=(k == 0))
         prev, cur = cur, nxt
-    assert rel_l2(got, cur) < 1e-5
+    assert_grid_parity(got, cur, 1e-5)
 
 
 def test_hj_512_tma_matches_oracle():
@@ -128,7 +128,7 @@ def test_hj_512_tma_matches_oracle():
     for _ in range(3):
         uu, dtk, speeds = schemes.hj_step(uu, [h, h], speeds)
         tt += dtk
-    assert rel_l2(got, uu) < 1e-5
+    assert_grid_parity(got, uu, 1e-5)
     assert abs(t[0] - tt) < 1e-4 * tt
 
 
@@ -150,4 +150,4 @@ def test_heat_mixed_512_tma_matches_oracle():
     want = u0
     for _ in range(2):
         want = schemes.heat_step(want, [h, h], dt, 1.0, 0.6, None, 3, 3)
-    assert rel_l2(got, want) < 1e-5
+    assert_grid_parity(got, want, 1e-5)
