@@ -42,9 +42,13 @@ def state_dtype(prec):
 
 # Element-wise bound next to the relative L2 norm: the largest pointwise error
 # over the largest value.  An error confined to a few points of a long line
-# (the ghost-affected ends) is diluted in the L2 norm but not here.
+# (the ghost-affected ends) is diluted in the L2 norm but not here.  FP32:
+# D = v - L^{-1}[v] loses about 2^-24 / nu^2 of |v| to cancellation at small
+# nu (1.1e-5 at nu = 0.075, the heat problems' 128^2 grid with dt = h/2), and
+# the largest point of a field sits a few times above its RMS, so 5e-5; an
+# error at the line ends from a wrong ghost or boundary term is 1e-3 or more.
 MAX_F64 = 1e-11
-MAX_F32 = 2e-5
+MAX_F32 = 5e-5
 
 
 def max_for(prec):
@@ -83,8 +87,9 @@ def assert_parity(got, want, tol_l2, tol_max, line_axis=None, what=""):
 
 def max_bound(tol_l2):
     """The element-wise bound (over max|want|) that goes with a relative-L2
-    bound: the FP64 one for FP64 tolerances, else twice the L2 bound."""
-    return MAX_F64 if tol_l2 <= TOL_F64 else 2.0 * tol_l2
+    bound: the FP64 one for FP64 tolerances, else five times the L2 bound
+    (the ratio of MAX_F32 to TOL_F32)."""
+    return MAX_F64 if tol_l2 <= TOL_F64 else 5.0 * tol_l2
 
 
 def assert_grid_parity(got, want, tol_l2, what="", ends=True):
