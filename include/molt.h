@@ -277,12 +277,18 @@ typedef enum {
   MOLT_OPT_TEST_SKIP_ARRIVE = 3,  /* test hook: 1 makes one CTA of the batched step
                                      skip its first grid barrier, so the others'
                                      bounded waits run out (MOLT_ETIMEOUT)       */
-  MOLT_OPT_LANES = 4              /* line-per-lane FP32 sweeps (one lane per line,
+  MOLT_OPT_LANES = 4,             /* line-per-lane FP32 sweeps (one lane per line,
                                      one warp per 16-point segment, difference
                                      form of the recurrences): 1 (default) when
                                      the line shape allows and nu*16 >= ~3.5;
                                      2 whenever the shape allows; 0 never.
                                      Both kernels compute the same values      */
+  MOLT_OPT_AXIS_STREAMS = 5       /* heat problems of up to 2^18 points in 2-D
+                                     or 3-D: 1 (default) runs the x sweep of a
+                                     stage on the context's stream and the y
+                                     (and z) sweeps on a second stream at the
+                                     same time, then one update kernel; 0 runs
+                                     the axes one after another.  Same values */
 } molt_option;
 molt_status molt_set_option(molt_ctx* ctx, int option, int64_t value);
 

@@ -58,6 +58,7 @@ struct Problem {
   mutable NuCache nu[3];
   mutable void* nu_tmp[2] = {nullptr, nullptr};   // transposed copies for strided non-uniform 2-D sweeps
   mutable void* nu_sum = nullptr;                 // S of one axis in the compute type (molt_step)
+  void* acc2 = nullptr;     // heat with concurrent axes: the y (and z) sums (compute type)
   int64_t hj_steps = 0;     // HJ steps taken (rotates the speed slots)
   bool hj_lag_ready = false;
 };
@@ -94,6 +95,11 @@ struct molt_ctx {
   unsigned long long* mlp_stats = nullptr;  // [stencils evaluated, fallbacks]
   bool mlp_ready = false;          // molt_set_mlp has been called
   bool profile = false;
+  // small heat problems: the axes' sweeps of a stage on two streams at once
+  // (MOLT_OPT_AXIS_STREAMS), joined by events before the stage update
+  int axis_streams = 1;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   struct Rec { int kind; cudaEvent_t start, stop; };
   std::vector<Rec> recs;
   std::string err;
@@ -115,6 +121,11 @@ bool is_f32_state(const molt_desc& d) { return d.prec == MOLT_PREC_F32; }
 bool is_mixed(const molt_desc& d) { return d.prec == MOLT_PREC_F32_F64UPDATE; }
 size_t state_bytes(const molt_desc& d) { return is_f32_state(d) ? 4 : 8; }
 size_t compute_bytes(const molt_desc& d) { return is_f64_sweep(d) ? 8 : 4; }
+
+// Small heat problems run a stage's axis sweeps on two streams at once: one
+// sweep launch covers too few lines to fill the GPU, and the axes read the
+// same stage input and write their own accumulators.
+constexpr long long kAxisStreamsMaxPoints = 1LL << 18;
 
 std::string validate(const molt_desc& d) {
   if (d.ndim < 1 || d.ndim > 3) return "ndim must be 1, 2 or 3";
@@ -575,7 +586,10 @@ bool plan_lanes(const molt_ctx* c, const Problem& p, int epi, const Plan& pl, bo
 
 molt_status run_nonuniform(molt_ctx* c, const Problem& p, int epi, const Plan& pl);
 
-molt_status run(molt_ctx* c, const Problem& p, int epi, Plan& pl, bool from_state_copy = true) {
+// s: the launch stream (nullptr: the context's)
+molt_status run(molt_ctx* c, const Problem& p, int epi, Plan& pl, bool from_state_copy = true,
+                cudaStream_t s = nullptr) {
+  if (!s) s = c->stream;
   if (!p.nodes[pl.ax].empty()) return run_nonuniform(c, p, epi, pl);
   // element size of the sweep input: FP64 except FP32 state or the FP32 copy
   const size_t in_bytes = is_f32_state(p.d) || (is_mixed(p.d) && from_state_copy) ? 4 : 8;
@@ -591,11 +605,11 @@ molt_status run(molt_ctx* c, const Problem& p, int epi, Plan& pl, bool from_stat
       if (c->profile) {
         cudaEventCreate(&rec.start);
         cudaEventCreate(&rec.stop);
-        cudaEventRecord(rec.start, c->stream);
+        cudaEventRecord(rec.start, s);
       }
-      const cudaError_t e = launch_lanes(epi, la, lmap, c->stream);
+      const cudaError_t e = launch_lanes(epi, la, lmap, s);
       if (c->profile) {
-        cudaEventRecord(rec.stop, c->stream);
+        cudaEventRecord(rec.stop, s);
         c->recs.push_back(rec);
       }
       if (e != cudaSuccess) return cuda_fail(c, e, "line-per-lane sweep launch");
@@ -611,11 +625,11 @@ molt_status run(molt_ctx* c, const Problem& p, int epi, Plan& pl, bool from_stat
   if (c->profile) {
     cudaEventCreate(&rec.start);
     cudaEventCreate(&rec.stop);
-    cudaEventRecord(rec.start, c->stream);
+    cudaEventRecord(rec.start, s);
   }
-  cudaError_t e = launch(p, epi, pl, c->stream, from_state_copy);
+  cudaError_t e = launch(p, epi, pl, s, from_state_copy);
   if (c->profile) {
-    cudaEventRecord(rec.stop, c->stream);
+    cudaEventRecord(rec.stop, s);
     c->recs.push_back(rec);
   }
   if (e == cudaErrorNotSupported)
@@ -766,11 +780,21 @@ molt_status molt_create(const molt_desc* descs, int count, void* cuda_stream, mo
       ok = cudaMalloc(&p.tu, sb * tot) == cudaSuccess && cudaMalloc(&p.thx, sb * tot) == cudaSuccess;
     }
     if (is_mixed(p.d) && p.d.pde != MOLT_PDE_HJ) ok = ok && cudaMalloc(&p.shadow, 4 * tot) == cudaSuccess;
+    if (p.d.pde == MOLT_PDE_HEAT && p.d.ndim > 1 && p.total <= kAxisStreamsMaxPoints)
+      ok = ok && cudaMalloc(&p.acc2, cb * tot) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       molt_destroy(c);
       return fail(nullptr, MOLT_ENOMEM, "workspace allocation failed");
     }
+  }
+  bool any_acc2 = false;
+  for (const auto& p : c->probs) any_acc2 = any_acc2 || p.acc2;
+  if (any_acc2 && ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess ||
+                   (e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+                   (e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess)) {
+    molt_destroy(c);
+    return fail(nullptr, MOLT_ECUDA, std::string("side stream: ") + cudaGetErrorString(e));
   }
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
     molt_destroy(c);
@@ -1141,7 +1165,83 @@ molt_status refresh_shadow(molt_ctx* c, Problem& p, const void* u) {
 // Sweep input of molt_step: the FP32 copy in mixed precision, else the state.
 const void* sweep_input(const Problem& p, const void* state) { return p.shadow ? p.shadow : state; }
 
+// Runge-Kutta stage of a heat step whose axis sums sit in two accumulators
+// (x in acc, y and z in acc2): dst = a0 u^n + a1 (u_s + coefS (acc + acc2)),
+// the arithmetic of the fused last-axis epilogue (acc + S in the compute
+// type first); FP32 copy for mixed precision.
+template <typename TC, typename TS>
+__global__ void heat_update2_kernel(const TC* __restrict__ acc, const TC* __restrict__ acc2, const TS* un,
+                                    const TS* us, TS* dst, float* __restrict__ shadow, double a0, double a1,
+                                    double coefS, long long n, int* status) {
+  bool bad = false;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const TC tot = acc[i] + acc2[i];
+    const TS r = fma(TS(a0), un[i], TS(a1) * fma(TS(coefS), cvt<TS>(tot), us[i]));
+    dst[i] = r;
+    if (shadow) shadow[i] = cvt<float>(r);
+    bad |= nonfinite(r);
+  }
+  if (bad) atomicOr(status, ST_NONFINITE);
+}
+
+bool heat_axis_streams(const molt_ctx* c, const Problem& p) {
+  if (!c->axis_streams || !c->side || !p.acc2) return false;
+  for (int ax = 0; ax < p.d.ndim; ++ax)
+    if (!p.nodes[ax].empty()) return false;
+  return true;
+}
+
+molt_status heat_step_axis_streams(molt_ctx* c, Problem& p, void* u) {
+  const double alpha = step_alpha(p);
+  const double coefS = -p.d.beta * p.d.beta;
+  static const double rk[3][2] = {{0.0, 1.0}, {0.75, 0.25}, {1.0 / 3.0, 2.0 / 3.0}};
+  const bool euler = p.d.integrator == MOLT_INT_EULER;
+  void* ins[3] = {u, p.stage1, p.stage2};
+  void* dsts[3] = {euler ? u : p.stage1, p.stage2, u};
+  cudaError_t e;
+  for (int s = 0; s < (euler ? 1 : 3); ++s) {
+    if ((e = cudaEventRecord(c->ev_fork, c->stream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(c->side, c->ev_fork, 0)) != cudaSuccess)
+      return cuda_fail(c, e, "stream fork");
+    for (int ax = 0; ax < p.d.ndim; ++ax) {
+      Plan pl;
+      molt_status st = plan_axis(c, p, ax, MODE_0, p.d.P, alpha, &pl);
+      if (st != MOLT_OK) return st;
+      pl.a.in = sweep_input(p, ins[s]);
+      pl.a.acc = ax == 0 ? p.acc : p.acc2;
+      if ((st = run(c, p, ax <= 1 ? EPI_ACC_SET : EPI_ACC_ADD, pl, true, ax == 0 ? c->stream : c->side)) != MOLT_OK)
+        return st;
+    }
+    if ((e = cudaEventRecord(c->ev_join, c->side)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(c->stream, c->ev_join, 0)) != cudaSuccess)
+      return cuda_fail(c, e, "stream join");
+    molt_ctx::Rec rec;
+    record_begin(c, &rec, MOLT_KERNEL_UPDATE);
+    const int g = stream_grid(p.total);
+    if (is_f64_sweep(p.d))
+      heat_update2_kernel<double, double><<<g, 256, 0, c->stream>>>(
+          static_cast<const double*>(p.acc), static_cast<const double*>(p.acc2), static_cast<const double*>(u),
+          static_cast<const double*>(ins[s]), static_cast<double*>(dsts[s]), nullptr, rk[s][0], rk[s][1], coefS,
+          p.total, c->status_dev);
+    else if (is_f32_state(p.d))
+      heat_update2_kernel<float, float><<<g, 256, 0, c->stream>>>(
+          static_cast<const float*>(p.acc), static_cast<const float*>(p.acc2), static_cast<const float*>(u),
+          static_cast<const float*>(ins[s]), static_cast<float*>(dsts[s]), nullptr, rk[s][0], rk[s][1], coefS,
+          p.total, c->status_dev);
+    else
+      heat_update2_kernel<float, double><<<g, 256, 0, c->stream>>>(
+          static_cast<const float*>(p.acc), static_cast<const float*>(p.acc2), static_cast<const double*>(u),
+          static_cast<const double*>(ins[s]), static_cast<double*>(dsts[s]), p.shadow, rk[s][0], rk[s][1], coefS,
+          p.total, c->status_dev);
+    record_end(c, &rec);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "heat update");
+  }
+  return MOLT_OK;
+}
+
 molt_status heat_step(molt_ctx* c, Problem& p, void* u) {
+  if (heat_axis_streams(c, p)) return heat_step_axis_streams(c, p, u);
   const double alpha = step_alpha(p);
   const double coefS = -p.d.beta * p.d.beta;
   static const double rk[3][2] = {{0.0, 1.0}, {0.75, 0.25}, {1.0 / 3.0, 2.0 / 3.0}};
@@ -2145,6 +2245,9 @@ molt_status molt_set_option(molt_ctx* c, int option, int64_t value) {
   } else if (option == MOLT_OPT_LANES) {
     if (value < 0 || value > 2) return fail(c, MOLT_EINVAL, "MOLT_OPT_LANES takes 0, 1 or 2");
     c->lanes = int(value);
+  } else if (option == MOLT_OPT_AXIS_STREAMS) {
+    if (value != 0 && value != 1) return fail(c, MOLT_EINVAL, "option value must be 0 or 1");
+    c->axis_streams = int(value);
   } else {
     if (value != 0 && value != 1) return fail(c, MOLT_EINVAL, "option value must be 0 or 1");
     if (option == MOLT_OPT_TMA) c->no_tma = value == 0;
@@ -2224,6 +2327,7 @@ molt_status molt_destroy(molt_ctx* c) {
     for (auto& cch : p.nu) cudaFree(cch.dev);
     for (void* t : p.nu_tmp) cudaFree(t);
     cudaFree(p.nu_sum);
+    cudaFree(p.acc2);
     for (void* v : p.hv) cudaFree(v);
     cudaFree(p.tu);
     cudaFree(p.thx);
@@ -2239,6 +2343,12 @@ molt_status molt_destroy(molt_ctx* c) {
   cudaFree(c->tnow_dev);
   cudaFree(c->mlp_blob);
   cudaFree(c->mlp_stats);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
   return MOLT_OK;
 }

@@ -256,3 +256,41 @@ def test_hj_3d_is_rejected():
     with pytest.raises(M.MoltError) as e:
         M.molt_create(d)
     assert e.value.status == M.MOLT_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", [M.PREC_F64, M.PREC_F32_F64UPDATE, M.PREC_F32])
+@pytest.mark.parametrize("shape_xyz", [(96, 80), (24, 20, 16)])
+def test_heat_axis_streams_match_serial_axes(prec, shape_xyz):
+    """Small heat problems sweep their axes on two streams at once
+    (MOLT_OPT_AXIS_STREAMS, default on): in 2-D the same values as the axes
+    one after another, bit for bit (S_x + S_y either way); in 3-D the sums
+    add as S_x + (S_y + S_z) instead of (S_x + S_y) + S_z, so the two differ
+    by rounding only; both match the oracle's SSP-RK3 step."""
+    need_gpu()
+    import torch
+    nd = len(shape_xyz)
+    hs = [1.0 / n for n in shape_xyz]
+    dt = 0.5 * min(hs)
+    shape_np = tuple(reversed(shape_xyz))
+    u0 = np.cos(2 * np.pi * np.arange(shape_np[-1]) / shape_np[-1]) + 0.1 * workloads.rng(21).standard_normal(shape_np)
+    if prec == M.PREC_F32:
+        u0 = u0.astype(np.float32).astype(np.float64)
+    d = M.make_desc(shape_xyz, P=3, quad_points=3, beta=0.6, pde=M.PDE_HEAT, diffusivity=1.0, dt=dt, prec=prec)
+    out = {}
+    for mode in (1, 0):
+        ctx = M.molt_create(d)
+        try:
+            M.molt_set_option(ctx, M.OPT_AXIS_STREAMS, mode)
+            u = to_dev(u0, state_dtype(prec))
+            M.molt_step(ctx, u, None, nsteps=3, t=[0.0])
+            out[mode] = u.double().cpu().numpy()
+        finally:
+            M.molt_destroy(ctx)
+    if nd == 2:
+        assert np.array_equal(out[0], out[1])
+    else:
+        assert_grid_parity(out[1], out[0], 1e-14 if prec == M.PREC_F64 else 1e-6, what="streams vs serial")
+    want = u0
+    for _ in range(3):
+        want = schemes.heat_step(want, hs[::-1], dt, 1.0, 0.6, None, 3, 3)
+    assert_grid_parity(out[1], want, tol_for(prec), what="%dD" % nd)
