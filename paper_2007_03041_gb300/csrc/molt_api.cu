@@ -61,6 +61,7 @@ struct Problem {
   void* acc2 = nullptr;     // heat with concurrent axes: the y (and z) sums (compute type)
   int64_t hj_steps = 0;     // HJ steps taken (rotates the speed slots)
   bool hj_lag_ready = false;
+  bool hj_flipped = false;  // HJ with a transposed y pass: the state sits in tu (transposed) between steps
 };
 
 }  // namespace
@@ -1524,6 +1525,7 @@ Problem transposed(const Problem& p) {
   std::swap(t.d.lo[0], t.d.lo[1]);
   std::swap(t.d.hi[0], t.d.hi[1]);
   std::swap(t.d.bc[0], t.d.bc[1]);
+  std::swap(t.d.velocity[0], t.d.velocity[1]);
   return t;
 }
 
@@ -1786,6 +1788,33 @@ molt_status hj_step(molt_ctx* c, Problem& p, int idx, void* u) {
   const unsigned long long* lag = slots + (cur ^ 1);
   if ((e = cudaMemsetAsync(slot, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "memset");
+  if (ty) {
+    // The y lines run as rows of the transposed state.  The state alternates
+    // between the layouts from step to step, so a step transposes twice (the
+    // state and the first pass's H^ part) and molt_step transposes the state
+    // back once at the end of an odd run:
+    //   natural u:     x pass on u -> hx; u, hx -> tu, thx; y pass on tu
+    //                  (reads thx) writes u^{n+1} into tu
+    //   transposed tu: y pass on tu -> thx; tu, thx -> u, hx; x pass on u
+    //                  (reads hx) writes u^{n+1} into u
+    // The two one-axis parts of H^ add in either order (the sum is exact in
+    // either order), and the speeds are one maximum over both axes.
+    molt_status st;
+    if (!p.hj_flipped) {
+      if ((st = hj_pass(c, p, idx, u, 0, EPI_HJ_X, slot, lag, hxp)) != MOLT_OK) return st;
+      if ((st = transpose(c, p, u, p.tu, ny, nx)) != MOLT_OK) return st;
+      if ((st = transpose(c, p, p.hx, p.thx, ny, nx)) != MOLT_OK) return st;
+      if ((st = hj_pass(c, pt, idx, p.tu, 0, EPI_HJ_Y, slot, lag, p.thx, p.tu)) != MOLT_OK) return st;
+    } else {
+      if ((st = hj_pass(c, pt, idx, p.tu, 0, EPI_HJ_X, slot, lag, p.thx)) != MOLT_OK) return st;
+      if ((st = transpose(c, p, p.tu, u, nx, ny)) != MOLT_OK) return st;
+      if ((st = transpose(c, p, p.thx, p.hx, nx, ny)) != MOLT_OK) return st;
+      if ((st = hj_pass(c, p, idx, u, 0, EPI_HJ_Y, slot, lag, hxp)) != MOLT_OK) return st;
+    }
+    p.hj_flipped = !p.hj_flipped;
+    p.hj_steps++;
+    return MOLT_OK;
+  }
   for (int ax = 0; ax < p.d.ndim; ++ax) {
     const bool last = ax + 1 == p.d.ndim;
     const int epi = last ? EPI_HJ_Y : EPI_HJ_X;
@@ -1794,20 +1823,19 @@ molt_status hj_step(molt_ctx* c, Problem& p, int idx, void* u) {
         (e = cudaMemcpyAsync(c->tnow_dev + idx, c->t_dev + idx, sizeof(double), cudaMemcpyDeviceToDevice,
                              c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "time copy");
-    if (ty && ax == 1) {
-      // y pass on the transposed state: rows of u^T; H^_x^T is read and
-      // u^{n+1 T} written in its place, then transposed back into u
-      if ((st = transpose(c, p, u, p.tu, ny, nx)) != MOLT_OK) return st;
-      if ((st = transpose(c, p, p.hx, p.thx, ny, nx)) != MOLT_OK) return st;
-      if ((st = hj_pass(c, pt, idx, p.tu, 0, epi, slot, lag, p.thx, p.thx)) != MOLT_OK) return st;
-      st = transpose(c, p, p.thx, u, nx, ny);
-    } else {
-      st = hj_pass(c, p, idx, u, ax, epi, slot, lag, hxp);
-    }
+    st = hj_pass(c, p, idx, u, ax, epi, slot, lag, hxp);
     if (st != MOLT_OK) return st;
   }
   p.hj_steps++;
   return MOLT_OK;
+}
+
+// A Hamilton-Jacobi state left in the transposed layout goes back into u.
+molt_status hj_unflip(molt_ctx* c, Problem& p, void* u) {
+  if (!p.hj_flipped) return MOLT_OK;
+  molt_status st = transpose(c, p, p.tu, u, p.n[0], p.n[1]);
+  if (st == MOLT_OK) p.hj_flipped = false;
+  return st;
 }
 
 // ------------------------------------------------------------------ batch
@@ -2112,6 +2140,10 @@ molt_status molt_step(molt_ctx* c, void* const* u, void* const* u_prev, int nste
       }
       if (st != MOLT_OK) return st;
     }
+  }
+  for (int i = 0; i < np; ++i) {
+    molt_status st = hj_unflip(c, c->probs[i], u[i]);
+    if (st != MOLT_OK) return st;
   }
   int status = 0;
   std::vector<double> tdev(np);

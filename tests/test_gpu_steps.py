@@ -11,6 +11,7 @@ from paper_2007_03041_gb300 import workloads
 from tests.gpu_util import need_gpu, rel_l2, to_dev, tol_for, state_dtype, assert_grid_parity
 
 pytestmark = pytest.mark.gpu
+TOL_F64_STEPS = 1e-12
 
 
 @pytest.mark.parametrize("prec", [M.PREC_F64, M.PREC_F32_F64UPDATE])
@@ -158,21 +159,63 @@ def test_hj_anisotropic_long_lines(nx, ny, prec, transposed):
     try:
         u = to_dev(u0, state_dtype(prec))
         M.molt_set_option(ctx, M.OPT_PROFILE, 1)
+        # three steps in two calls: the transposed form alternates the
+        # state's layout and returns it in u after an odd count
         t = M.molt_step(ctx, u, None, nsteps=2, t=[0.0])
+        got2 = u.double().cpu().numpy()
+        t = M.molt_step(ctx, u, None, nsteps=1, t=t)
         _, ntr = M.molt_profile_read(ctx, M.KERNEL_TRANSPOSE)
         got = u.double().cpu().numpy()
     finally:
         M.molt_destroy(ctx)
-    assert (ntr > 0) == transposed
+    # one for the speeds of u^0, two per step, one back after the odd run
+    assert ntr == (8 if transposed else 0)
     uu = u0.astype(np.float32).astype(np.float64) if prec == M.PREC_F32 else u0
     dxs = [hy_, hx_]            # numpy axis order: y, x
     speeds = schemes.hj_initial_speeds(uu, dxs, 1.5, 1.0, 5, "wenoz")
     tt = 0.0
-    for _ in range(2):
+    for k in range(3):
         uu, dt, speeds = schemes.hj_step(uu, dxs, speeds, 1.5, 1.0, 5, "wenoz")
         tt += dt
-    assert_grid_parity(got, uu, tol_for(prec))
+        if k == 1:
+            assert_grid_parity(got2, uu, tol_for(prec), what="after 2 steps")
+    assert_grid_parity(got, uu, tol_for(prec), what="after 3 steps")
     assert abs(t[0] - tt) < (1e-10 if prec == M.PREC_F64 else 1e-4) * tt
+
+
+def test_hj_linear_hamiltonian_on_long_y_lines():
+    """H = a.grad u with a_x != a_y on long y lines (the transposed y pass):
+    the transposed problem carries the swapped velocities."""
+    need_gpu()
+    import torch
+    nx, ny = 128, 4096
+    hx_, hy_ = 2 * np.pi / nx, 2 * np.pi / ny
+    x = 2 * np.pi * np.arange(nx) / nx
+    y = 2 * np.pi * np.arange(ny) / ny
+    u0 = np.sin(x)[None, :] + 0.5 * np.cos(3 * y)[:, None]
+    vel = (0.7, -1.3)
+    d = M.make_desc((nx, ny), lo=[0, 0], hi=[2 * np.pi] * 2, P=1, quad_points=6, beta=1.0, pde=M.PDE_HJ, cfl=0.5,
+                    dt=0.0, prec=M.PREC_F64, hamiltonian=M.H_LINEAR, velocity=vel)
+    ctx = M.molt_create(d)
+    try:
+        u = to_dev(u0, torch.float64)
+        M.molt_set_option(ctx, M.OPT_PROFILE, 1)
+        t = M.molt_step(ctx, u, None, nsteps=3, t=[0.0])
+        _, ntr = M.molt_profile_read(ctx, M.KERNEL_TRANSPOSE)
+        got = u.cpu().numpy()
+    finally:
+        M.molt_destroy(ctx)
+    assert ntr == 8
+    dxs = [hy_, hx_]
+    a = [vel[1], vel[0]]        # numpy axis order
+    uu = u0
+    speeds = schemes.hj_initial_speeds(uu, dxs, 0.5, 1.0, 6, "linear", hamiltonian=schemes.H_LINEAR, a=a)
+    tt = 0.0
+    for _ in range(3):
+        uu, dt, speeds = schemes.hj_step(uu, dxs, speeds, 0.5, 1.0, 6, "linear", hamiltonian=schemes.H_LINEAR, a=a)
+        tt += dt
+    assert_grid_parity(got, uu, TOL_F64_STEPS)
+    assert abs(t[0] - tt) < 1e-10 * tt
 
 
 @pytest.mark.parametrize("case", ["heat1d", "heat3d", "wave1d", "wave2d_periodic", "hj1d"])
