@@ -229,6 +229,9 @@ __device__ __forceinline__ TO cvt(FROM x) {
 // ---------------------------------------------------------------- arithmetic
 // y <- a*y + b on y = hi + lo.  FP32: compensated (exact product error by FMA,
 // TwoSum for the addition).  FP64: plain FMA.
+#ifndef MOLT_SHARED_BETA
+#define MOLT_SHARED_BETA 1   // WENO-Z: smoothness indicators from per-triple products shared by neighbouring points
+#endif
 #ifndef MOLT_COMPENSATED
 #define MOLT_COMPENSATED 1
 #endif
@@ -275,6 +278,42 @@ __device__ __forceinline__ float weight_rcp(float x) {
   return y;
 }
 __device__ __forceinline__ double weight_rcp(double x) { return 1.0 / x; }
+
+template <typename T>
+__device__ __forceinline__ T wenoz_from_beta(const T* w, const T (&beta)[3], const T (&sub)[3][3], const T (&d)[3]) {
+  T J[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) J[r] = sub[r][0] * w[r] + sub[r][1] * w[r + 1] + sub[r][2] * w[r + 2];
+  const T tau = fabs(beta[0] - beta[2]);
+  const T eps = T(1e-6);
+  T wt[3], sum = T(0);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    wt[r] = fma(d[r] * tau, weight_rcp(eps + beta[r]), d[r]);   // d_r (1 + tau/(eps+beta_r))
+    sum += wt[r];
+  }
+  return (wt[0] * J[0] + wt[1] * J[1] + wt[2] * J[2]) * weight_rcp(sum);
+}
+
+// The smoothness indicator of substencil r from the products of its node
+// triple (a, b, c): with s1 = (c - a)/2 and s2 = a - 2b + c, beta_r = s1^2 +
+// k_r s1 s2 + m_r s2^2 (k = 3, 1, -1; m = 10/3, 4/3, 4/3).  A triple serves
+// three points' J_R and, mirrored (s1 -> -s1), three points' J_L, so the
+// products are formed once per triple.
+template <typename T>
+__device__ __forceinline__ void triple_products(T a, T b, T c, T* p11, T* p12, T* p22) {
+  const T s1 = T(0.5) * (c - a);
+  const T s2 = a - T(2) * b + c;
+  *p11 = s1 * s1;
+  *p12 = s1 * s2;
+  *p22 = s2 * s2;
+}
+template <typename T>
+__device__ __forceinline__ T beta_from_products(int r, T p11, T p12, T p22, bool mirrored) {
+  const T k = r == 0 ? T(3) : (r == 1 ? T(1) : T(-1));
+  const T m = r == 0 ? T(10.0 / 3.0) : T(4.0 / 3.0);
+  return p11 + (mirrored ? -k : k) * p12 + m * p22;
+}
 
 template <typename T>
 __device__ __forceinline__ T wenoz_integral(const T* w, const T (&sub)[3][3], const T (&d)[3]) {
@@ -686,6 +725,13 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
       T win[E + 6];
 #pragma unroll
       for (int k = 0; k < E + 6; ++k) win[k] = cbase[chunk_off<E>(k - 3)];
+#if MOLT_SHARED_BETA
+      T p11[E + 4], p12[E + 4], p22[E + 4];   // products of the node triples win[t..t+2]
+      if constexpr (JQ == JQ_WENOZ) {
+#pragma unroll
+        for (int t = 0; t < E + 4; ++t) triple_products<T>(win[t], win[t + 1], win[t + 2], &p11[t], &p12[t], &p22[t]);
+      }
+#endif
 #pragma unroll
       for (int k = 0; k < E; ++k) {
         v[k] = win[k + 3];
@@ -699,8 +745,21 @@ __device__ __forceinline__ double compute_lines(const SweepArgs& a, const TileSm
             wr[j] = win[k + j];        // offsets -3..1
             wl[j] = win[k + 6 - j];    // mirrored: v_{e+3} .. v_{e-1}
           }
+#if MOLT_SHARED_BETA
+          // substencil r of J_R is the triple at k + r; of J_L the triple at
+          // k + 4 - r, reversed
+          T bR[3], bL[3];
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            bR[r] = beta_from_products<T>(r, p11[k + r], p12[k + r], p22[k + r], false);
+            bL[r] = beta_from_products<T>(r, p11[k + 4 - r], p12[k + 4 - r], p22[k + 4 - r], true);
+          }
+          Y[k].x = wenoz_from_beta<T>(wr, bR, sub, dw);
+          Y[E - 1 - (k)].y = wenoz_from_beta<T>(wl, bL, sub, dw);
+#else
           Y[k].x = wenoz_integral<T>(wr, sub, dw);
           Y[E - 1 - (k)].y = wenoz_integral<T>(wl, sub, dw);
+#endif
         } else {
           T r = T(0), l = T(0);
 #pragma unroll
