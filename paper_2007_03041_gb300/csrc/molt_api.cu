@@ -880,7 +880,13 @@ __global__ void shadow_kernel(const double* __restrict__ in, float* __restrict__
 //          from rest: u^1 = u^0 + coefS/2 * acc            (Taylor start)
 // acc holds sum_d S_{P,d} of the stage input in FP32.  Each also refreshes
 // the FP32 copy the next sweeps read and flags non-finite values.
-constexpr int kUpdPer = 4;   // points per thread and iteration; their loads are issued first
+#ifndef MOLT_UPD_PER
+#define MOLT_UPD_PER 8
+#endif
+#ifndef MOLT_UPD_BLOCKS_PER_SM
+#define MOLT_UPD_BLOCKS_PER_SM 8
+#endif
+constexpr int kUpdPer = MOLT_UPD_PER;   // points per thread and iteration; their loads are issued first
 
 __global__ void heat_update_kernel(const float* __restrict__ acc, const double* un, const double* us, double* dst,
                                    float* __restrict__ shadow, double a0, double a1, double coefS, long long n,
@@ -952,7 +958,7 @@ int stream_grid(long long n) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   long long blocks = (n + 255) / 256;
-  if (blocks > 8LL * sms) blocks = 8LL * sms;
+  if (blocks > (long long)MOLT_UPD_BLOCKS_PER_SM * sms) blocks = (long long)MOLT_UPD_BLOCKS_PER_SM * sms;
   return int(blocks < 1 ? 1 : blocks);
 }
 

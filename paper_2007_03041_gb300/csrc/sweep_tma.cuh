@@ -9,7 +9,8 @@
 // tile are prefetched into L2 at the same time.
 //
 // Every wait is bounded: after kWaitLimit cycles the CTA records
-// ST_TIMEOUT in the status word and returns.
+// ST_TIMEOUT in the status word, waits (bounded) once more for the copy it
+// has in flight and returns.
 #pragma once
 
 #include <cuda.h>
@@ -235,7 +236,12 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
     if (threadIdx.x == 0) *flag = mbar_wait_bounded(bar, parity) ? 1 : 0;
     __syncthreads();
     if (!*flag) {
-      if (threadIdx.x == 0) atomicOr(a.status, ST_TIMEOUT);
+      // record the give-up, then wait (bounded) once more for the copy this
+      // CTA issued into its own shared memory, the only one in flight
+      if (threadIdx.x == 0) {
+        atomicOr(a.status, ST_TIMEOUT);
+        mbar_wait_bounded(bar, parity);
+      }
       return;
     }
     parity ^= 1u;
