@@ -359,6 +359,17 @@ def run_ours(args):
         tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
         ms = float(tt.item())
 
+    # five more trials of the same length, each in its own event pair:
+    # fastest, mean and spread of the step time
+    trial_ms = []
+    for _ in range(5 if args.steps else 0):
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        t = M.molt_step(ctx, u, up, nsteps=args.steps, t=t)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        trial_ms.append(f0.elapsed_time(f1) / args.steps)
+
     # per-kernel averages from a second run of the same length with an event
     # pair around every launch (the headline region above runs without them)
     M.molt_set_option(ctx, M.OPT_PROFILE, 1)
@@ -458,7 +469,8 @@ def run_ours(args):
                 "launches_per_step": launches,
                 "algorithmic_bytes_per_dof": {k: BYTES_PER_DOF[k] for k in per_kernel},
                 "step_bytes_per_dof": sum(BYTES_PER_DOF[k] * launches[k] for k in per_kernel),
-                "per_kernel_source": "CUDA events around each launch, a second run of the same length"}
+                "per_kernel_source": "CUDA events around each launch, a second run of the same length",
+                "peak_nominal_gbs": HBM_NOMINAL_GBS, "frac_nominal": achieved / HBM_NOMINAL_GBS}
     if rank != 0:
         return None
     compare = None
@@ -486,6 +498,12 @@ def run_ours(args):
         "gpu_launches": int(round(sum(launches.values()) * args.steps)) + 1, "clocks": clk,
         "error_vs_oracle": err,
     }
+    if trial_ms:
+        mean = sum(trial_ms) / len(trial_ms)
+        line["trials"] = {"n": len(trial_ms), "steps_each": args.steps, "min_ms_per_step": min(trial_ms),
+                          "mean_ms_per_step": mean,
+                          "std_ms_per_step": (sum((x - mean) ** 2 for x in trial_ms) / len(trial_ms)) ** 0.5,
+                          "note": "five further timed regions of the same length after the headline one"}
     if compare:
         line["vs_plain_fp64_gpu"] = compare
     return line
@@ -536,6 +554,8 @@ CONFIGS = {
 # instructions: 2 per SM per cycle, 304 over the GPU, at the 2070 MHz maximum
 # SM clock
 FP64_PEAK_GINST = 304 * 2.070
+# GB300 HBM3e nominal bandwidth (context next to the measured copy peak)
+HBM_NOMINAL_GBS = 7900.0
 # grid side of the paper_ex* configs: the paper's 5277 (--size overrides it for
 # profiling at other sizes; the final-time errors are reported at 5277 only)
 PAPER_N = 5277
