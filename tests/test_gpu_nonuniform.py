@@ -260,16 +260,19 @@ def _run_dir_line(x, v, op, P, alpha, prec, npts, weights=M.W_LINEAR):
 @pytest.mark.parametrize("prec", [M.PREC_F64, M.PREC_F32, M.PREC_F32_F64UPDATE])
 @pytest.mark.parametrize("npts", [3, 5, 6])
 def test_dirichlet_lines_1d(prec, npts):
-    """Dirichlet lines, boundary nodes included: lengths from the shortest
-    the 6-point stencil allows to 4096 (eight warps per line), each
-    operator; in FP64 also a line with alpha (b - a) = 3, where the two
-    boundary constants couple through mu = e^{-3}."""
+    """Dirichlet lines, boundary nodes included: lengths 7 to 4096 (eight
+    warps per line), each operator; in FP64 also a line with alpha (b - a) =
+    3, where the two boundary constants couple through mu = e^{-3}, the
+    shortest line a Dirichlet axis takes (4 nodes: every stencil reaches
+    mirrored ghosts at both ends) and the longest (8192 nodes, 16 warps)."""
     need_gpu()
     a, b = 0.5, 3.5
     cases = [(7, M.OP_0, 1, 0.6), (100, M.OP_R, 2, 0.6), (513, M.OP_L, 3, 0.6), (1000, M.OP_0, 2, 0.6),
              (4096, M.OP_0, 1, 0.6), (300, M.OP_0, 3, 0.3)]
     if prec == M.PREC_F64:
-        cases += [(64, M.OP_0, 2, None), (64, M.OP_R, 1, None), (64, M.OP_L, 2, None)]
+        # alpha (b - a) = 3; the fewest nodes a Dirichlet line takes; the longest line (16 warps)
+        cases += [(64, M.OP_0, 2, None), (64, M.OP_R, 1, None), (64, M.OP_L, 2, None), (4, M.OP_0, 2, 0.6),
+                  (8192, M.OP_0, 1, 0.6)]
     for n, op, P, nu in cases:
         x = _dir_nodes(n, a, b)
         alpha = nu * (n - 1) / (b - a) if nu else 3.0 / (b - a)
