@@ -1110,8 +1110,9 @@ def config_line(name, steps, warmup, compare=True, error=True, size=None):
     return line
 
 
-# workloads nested in the default line (BASELINE configs 1, 3, 4, 5, and the
-# plain WENO-Z form of config 5's problem)
+# workloads nested in the default line: the 256^2 FP64 heat problem, the 64
+# batched heat problems, the 4096^2 and 8192^2 Hamilton-Jacobi problems with
+# WENO-Z and with learned weights, and the 4096^2 non-uniform sweeps
 DEFAULT_OTHER = (("heat256", 100, 3), ("batch64", 20, 3), ("hj4096", 20, 3), ("hj8192", 10, 2),
                  ("hj8192_learned", 10, 2), ("nonuniform4096", 20, 3), ("nonuniform4096_wenoz", 20, 3),
                  ("nonuniform4096_dirichlet", 20, 3))
