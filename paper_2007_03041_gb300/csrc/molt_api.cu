@@ -62,6 +62,12 @@ struct Problem {
   int64_t hj_steps = 0;     // HJ steps taken (rotates the speed slots)
   bool hj_lag_ready = false;
   bool hj_flipped = false;  // HJ with a transposed y pass: the state sits in tu (transposed) between steps
+  // heat with concurrent axis sweeps: one step captured as a CUDA graph (for
+  // the state array it was captured with) and replayed per step
+  cudaGraphExec_t heat_graph = nullptr;
+  const void* heat_graph_u = nullptr;
+  int heat_steps_direct = 0;   // steps launched directly since the state array changed
+  bool heat_graph_off = false; // capture refused (e.g. the legacy default stream)
 };
 
 }  // namespace
@@ -1247,8 +1253,53 @@ molt_status heat_step_axis_streams(molt_ctx* c, Problem& p, void* u) {
   return MOLT_OK;
 }
 
+// One concurrent-axes heat step as a graph launch: the step's launches
+// (sweeps on two streams joined by events, three stage updates) are captured
+// once per state array and replayed, so a step costs one launch on the host
+// and the graph's tighter launch spacing on the device.  The first step on a
+// state array runs its launches directly (it also configures the kernels'
+// attributes outside any capture); profiling, and streams that cannot be
+// captured (the legacy default stream), always run them directly.
+molt_status heat_step_graph(molt_ctx* c, Problem& p, void* u) {
+  cudaError_t e;
+  if (p.heat_graph_u != u) {
+    if (p.heat_graph) cudaGraphExecDestroy(p.heat_graph);
+    p.heat_graph = nullptr;
+    p.heat_graph_u = u;
+    p.heat_steps_direct = 0;
+  }
+  if (p.heat_graph_off || (!p.heat_graph && p.heat_steps_direct == 0)) {
+    ++p.heat_steps_direct;
+    return heat_step_axis_streams(c, p, u);
+  }
+  if (!p.heat_graph) {
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      p.heat_graph_off = true;
+      return heat_step_axis_streams(c, p, u);
+    }
+    const molt_status st = heat_step_axis_streams(c, p, u);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->stream, &g);
+    if (st != MOLT_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "heat step capture");
+    e = cudaGraphInstantiate(&p.heat_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      p.heat_graph = nullptr;
+      return cuda_fail(c, e, "heat step graph");
+    }
+  }
+  if ((e = cudaGraphLaunch(p.heat_graph, c->stream)) != cudaSuccess) return cuda_fail(c, e, "heat step graph launch");
+  return MOLT_OK;
+}
+
 molt_status heat_step(molt_ctx* c, Problem& p, void* u) {
-  if (heat_axis_streams(c, p)) return heat_step_axis_streams(c, p, u);
+  if (heat_axis_streams(c, p))
+    return c->profile ? heat_step_axis_streams(c, p, u) : heat_step_graph(c, p, u);
   const double alpha = step_alpha(p);
   const double coefS = -p.d.beta * p.d.beta;
   static const double rk[3][2] = {{0.0, 1.0}, {0.75, 0.25}, {1.0 / 3.0, 2.0 / 3.0}};
@@ -2366,6 +2417,7 @@ molt_status molt_destroy(molt_ctx* c) {
     for (void* t : p.nu_tmp) cudaFree(t);
     cudaFree(p.nu_sum);
     cudaFree(p.acc2);
+    if (p.heat_graph) cudaGraphExecDestroy(p.heat_graph);
     for (void* v : p.hv) cudaFree(v);
     cudaFree(p.tu);
     cudaFree(p.thx);

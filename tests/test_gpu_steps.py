@@ -337,3 +337,43 @@ def test_heat_axis_streams_match_serial_axes(prec, shape_xyz):
     for _ in range(3):
         want = schemes.heat_step(want, hs[::-1], dt, 1.0, 0.6, None, 3, 3)
     assert_grid_parity(out[1], want, tol_for(prec), what="%dD" % nd)
+
+
+@pytest.mark.parametrize("prec", [M.PREC_F64, M.PREC_F32_F64UPDATE])
+def test_heat_graph_replay_matches_direct_launches(prec):
+    """On a stream that can be captured, small heat problems replay one
+    captured step per step after a first direct one (and re-capture when the
+    state array changes); on the legacy default stream every step launches
+    directly.  Same values bit for bit, and the oracle's steps."""
+    need_gpu()
+    import torch
+    n = 128
+    h = 1.0 / n
+    dt = h / 2
+    u0 = workloads.heat_modes(n)
+    d = M.make_desc((n, n), P=3, quad_points=3, beta=0.6, pde=M.PDE_HEAT, diffusivity=1.0, dt=dt, prec=prec)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = M.molt_create(d, stream)
+        try:
+            a = to_dev(u0, torch.float64)
+            t = M.molt_step(ctx, a, None, nsteps=4, t=[0.0])
+            b = a.clone()                                   # a new state array: captured again
+            t = M.molt_step(ctx, b, None, nsteps=3, t=t)
+            stream.synchronize()
+            got = b.cpu().numpy()
+        finally:
+            M.molt_destroy(ctx)
+    ctx = M.molt_create(d)
+    try:
+        c = to_dev(u0, torch.float64)
+        M.molt_step(ctx, c, None, nsteps=7, t=[0.0])
+        direct = c.cpu().numpy()
+    finally:
+        M.molt_destroy(ctx)
+    assert np.array_equal(got, direct)
+    want = u0
+    for _ in range(7):
+        want = schemes.heat_step(want, [h, h], dt, 1.0, 0.6, None, 3, 3)
+    assert_grid_parity(got, want, tol_for(prec))
+    assert abs(t[0] - 7 * dt) < 1e-14
