@@ -247,6 +247,11 @@ int device_sms() {
 #ifndef MOLT_F64_SMALL_E
 #define MOLT_F64_SMALL_E 1
 #endif
+#ifndef MOLT_SMALL_TILE_THREADS
+#define MOLT_SMALL_TILE_THREADS 256
+#endif
+constexpr int kSmallTileThreads = MOLT_SMALL_TILE_THREADS;
+
 int choose_E(int n, bool f64, long long nlines) {
   auto fits = [n](int E) { return n % (32 * E) == 0 && n / (32 * E) <= kMaxThreads / 32; };
   if (f64 && MOLT_F64_SMALL_E) {
@@ -303,7 +308,13 @@ molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, do
   // tile shape: nwl warps per line, W lines per CTA, <= kMaxThreads threads
   const int nwl = (n + 32 * E - 1) / (32 * E);
   if (nwl > kMaxThreads / 32) return fail(c, MOLT_EUNSUPPORTED, "line longer than 8192 points");
-  int W = (kMaxThreads / 32) / nwl;
+  // contiguous lines: tiles of at most kSmallTileThreads threads where a line
+  // fits in them, so the register-heavy sweeps (128 per thread) keep two CTAs
+  // per SM and one computes while the other waits at a barrier (strided lines
+  // keep the wider tiles: their W lines are the width of every row they read)
+  const int tmax =
+      (auto_shape && a.contiguous && nwl * 32 <= kSmallTileThreads) ? kSmallTileThreads : kMaxThreads;
+  int W = (tmax / 32) / nwl;
   int Wp = 1;
   while (Wp * 2 <= W) Wp *= 2;
   W = Wp;
