@@ -158,10 +158,12 @@ molt_status molt_apply_D(molt_ctx* ctx, int problem, int axis, int op, int P, do
  * so dt F = -(beta/c) sum_d (S_R[g_d^+] - S_L[g_d^-]) - beta^2 sum_d S_0[u];
  * 3-stage SSP Runge-Kutta (MOLT_INT_DEFAULT) or forward Euler.  Linear or
  * WENO-Z weights (WENO-Z: 5 points, MOLT_PREC_F64 or MOLT_PREC_F32).
- * Heat, wave and advection-diffusion problems may have non-uniform axes
- * (molt_set_grid_axis): their S_{P,d} are the point-local sums of
- * molt_apply_D, the steps' formulas unchanged; Hamilton-Jacobi problems with
- * a non-uniform axis return MOLT_EUNSUPPORTED.
+ * Every problem may have non-uniform axes (molt_set_grid_axis): their
+ * S_{P,d} are the point-local sums of molt_apply_D, the steps' formulas
+ * unchanged; a Hamilton-Jacobi step with a non-uniform axis runs from the
+ * one-sided sums of every axis and a pointwise stage kernel, with each
+ * axis's spacing h_d its smallest cell (alpha = beta/(cfl min_d h_d), dt =
+ * cfl min_d h_d / c_d).
  * Synchronous at the end (reads t and the device status). */
 molt_status molt_step(molt_ctx* ctx, void* const* u, void* const* u_prev, int nsteps, double* t_inout);
 
@@ -192,11 +194,12 @@ molt_status molt_set_source(molt_ctx* ctx, int problem, const void* coef, int de
  * integrals are the WENO-Z combination of the substencil rules, with
  * point-local linear weights and smoothness indicators (see
  * molt_nonuniform_weno_weights); MOLT_W_LEARNED is MOLT_EUNSUPPORTED on
- * non-uniform axes.  molt_step runs heat, wave and advection-diffusion
- * problems on such axes.  x == NULL makes the axis uniform again.
- * The first call on a problem allocates one state-sized array of the
- * compute type (the axis sums of molt_step).  MOLT_EINVAL: bad index,
- * count or nodes; MOLT_ENOMEM.  Synchronous. */
+ * non-uniform axes.  molt_step runs every problem on such axes (see there).
+ * x == NULL makes the axis uniform again.  The first call on a problem
+ * allocates one state-sized array of the compute type (the axis sums of
+ * molt_step), and for a Hamilton-Jacobi problem two state-sized arrays per
+ * axis (its one-sided sums).  MOLT_EINVAL: bad index, count or nodes;
+ * MOLT_ENOMEM.  Synchronous. */
 molt_status molt_set_grid_axis(molt_ctx* ctx, int problem, int axis, const double* x, int64_t n);
 
 /* The point tables of a non-uniform line (host only, no device work): for

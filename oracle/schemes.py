@@ -251,7 +251,7 @@ def advdiff_step(u, dxs, dt, kind, a, c, kappa=0.0, beta=1.0, npts=6, P=1, rk3=F
 
 
 def hj_step_rk3(u, dxs, lagged_speeds, t=0.0, cfl=1.5, beta=1.0, npts=5, weights="wenoz", P=3,
-                hamiltonian=H_HALF_SQ, a=None, h0=0.0, source=None):
+                hamiltonian=H_HALF_SQ, a=None, h0=0.0, source=None, grids=None):
     """One step of the 3-stage SSP Runge-Kutta method on u_t = -H^ + F with
     P-term one-sided sums (Sec. 2.5: an s-stage method with s-term sums):
         u1 = u + dt L(u, t), u2 = 3/4 u + 1/4 (u1 + dt L(u1, t + dt)),
@@ -264,7 +264,7 @@ def hj_step_rk3(u, dxs, lagged_speeds, t=0.0, cfl=1.5, beta=1.0, npts=5, weights
     un = np.asarray(u, dtype=np.float64)
     us, speeds0 = un, None
     for (a0, a1), ts in zip(SSPRK3, stage_t):
-        Hh, sp = hj_hamiltonian(hj_derivatives(us, alpha, dxs, npts, weights, None, P), hamiltonian, a, h0)
+        Hh, sp = hj_hamiltonian(hj_derivatives(us, alpha, dxs, npts, weights, None, P, grids), hamiltonian, a, h0)
         if speeds0 is None:
             speeds0 = sp
         if source is not None:
@@ -274,8 +274,8 @@ def hj_step_rk3(u, dxs, lagged_speeds, t=0.0, cfl=1.5, beta=1.0, npts=5, weights
 
 
 def hj_initial_speeds_P(u, dxs, cfl=1.5, beta=1.0, npts=5, weights="wenoz", P=3, hamiltonian=H_HALF_SQ, a=None,
-                        h0=0.0):
+                        h0=0.0, grids=None):
     """Speeds of u^0 with P-term one-sided sums (the first step's lagged speeds)."""
     alpha = beta / (cfl * min(dxs))
-    _, speeds = hj_hamiltonian(hj_derivatives(u, alpha, dxs, npts, weights, None, P), hamiltonian, a, h0)
+    _, speeds = hj_hamiltonian(hj_derivatives(u, alpha, dxs, npts, weights, None, P, grids), hamiltonian, a, h0)
     return speeds

@@ -1150,11 +1150,15 @@ cudaError_t launch_point_epilogue(int epi, const SweepArgs& a, const void* S, lo
 
 // One axis of a heat, wave or advection-diffusion step along a non-uniform
 // axis: S = sum_{p<=P} D^p of the planned operator into the problem's sum
-// buffer by the non-uniform sweep, then the planned epilogue point by point.
+// buffer by the non-uniform sweep, then the planned epilogue point by point
+// (EPI_STORE: S into the output array).
 molt_status run_nonuniform(molt_ctx* c, const Problem& p, int epi, const Plan& pl) {
+  // S straight into the output array (the one-sided sums of the generic
+  // Hamilton-Jacobi step), in the state type
+  if (epi == EPI_STORE) return apply_D_nonuniform(c, p, pl.ax, pl.a.mode, pl.a.P, pl.a.alpha, pl.a.in, pl.a.out);
   if (epi != EPI_ACC_SET && epi != EPI_ACC_ADD && epi != EPI_ACC_AXPY && epi != EPI_HEAT_FINAL &&
       epi != EPI_WAVE_FINAL)
-    return fail(c, MOLT_EUNSUPPORTED, "non-uniform axes run heat, wave and advection-diffusion steps");
+    return fail(c, MOLT_EUNSUPPORTED, "non-uniform axes run heat, wave, advection-diffusion and Hamilton-Jacobi steps");
   if (!p.nu_sum) return fail(c, MOLT_EINVAL, "non-uniform axis without its sum buffer");
   molt_status st = apply_D_nonuniform(c, p, pl.ax, pl.a.mode, pl.a.P, pl.a.alpha, pl.a.in, p.nu_sum, true);
   if (st != MOLT_OK) return st;
@@ -1754,7 +1758,12 @@ molt_status hj_rk3_stage(molt_ctx* c, const Problem& p, HjStageArgs g) {
   return e == cudaSuccess ? MOLT_OK : cuda_fail(c, e, "Hamilton-Jacobi stage");
 }
 
-molt_status hj_rk3_step(molt_ctx* c, Problem& p, int idx, void* u) {
+// The Hamilton-Jacobi step from the one-sided sums S_R, S_L of every axis
+// (EPI_STORE sweeps into hv) and one pointwise stage kernel per stage: the
+// 3-stage SSP Runge-Kutta method, or (stages == 1: a0 = 0, a1 = 1, the stage
+// at t^n) forward Euler -- the form non-uniform axes take, whose sums come
+// from the non-uniform sweep.
+molt_status hj_rk3_step(molt_ctx* c, Problem& p, int idx, void* u, int stages = 3) {
   static const double rk[3][2] = {{0.0, 1.0}, {0.75, 0.25}, {1.0 / 3.0, 2.0 / 3.0}};
   static const double cst[3] = {0.0, 1.0, 0.5};   // stage times t^n + c dt
   unsigned long long* slots = c->speed_dev + 2 * idx;
@@ -1792,8 +1801,8 @@ molt_status hj_rk3_step(molt_ctx* c, Problem& p, int idx, void* u) {
   if ((e = cudaMemsetAsync(slots + cur, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "memset");
   void* ins[3] = {u, p.stage1, p.stage2};
-  void* dsts[3] = {p.stage1, p.stage2, u};
-  for (int s = 0; s < 3; ++s) {
+  void* dsts[3] = {stages == 1 ? u : p.stage1, p.stage2, u};
+  for (int s = 0; s < stages; ++s) {
     if ((st = hj_rk3_sums(c, p, ins[s])) != MOLT_OK) return st;
     HjStageArgs gs = g;
     gs.un = u;
@@ -1805,7 +1814,7 @@ molt_status hj_rk3_step(molt_ctx* c, Problem& p, int idx, void* u) {
     gs.lag = slots + (cur ^ 1);
     gs.speed = s == 0 ? slots + cur : nullptr;
     gs.t_now = c->t_dev + idx;
-    gs.t_next = s == 2 ? c->tnow_dev + idx : nullptr;
+    gs.t_next = s == stages - 1 ? c->tnow_dev + idx : nullptr;
     if (p.src) {
       gs.src = p.src;
       gs.src_deg = p.src_deg;
@@ -1823,6 +1832,8 @@ molt_status hj_rk3_step(molt_ctx* c, Problem& p, int idx, void* u) {
 
 molt_status hj_step(molt_ctx* c, Problem& p, int idx, void* u) {
   if (p.d.integrator == MOLT_INT_RK3) return hj_rk3_step(c, p, idx, u);
+  for (int ax = 0; ax < p.d.ndim; ++ax)
+    if (!p.nodes[ax].empty()) return hj_rk3_step(c, p, idx, u, 1);
   unsigned long long* slots = c->speed_dev + 2 * idx;
   cudaError_t e;
   const bool ty = p.tu && p.thx && hj_transposed_y(c, p);
@@ -2162,11 +2173,7 @@ molt_status molt_step(molt_ctx* c, void* const* u, void* const* u_prev, int nste
     if (c->probs[i].d.pde != MOLT_PDE_HJ && !(c->probs[i].d.dt > 0))
       return fail(c, MOLT_EINVAL, "heat and wave steps need dt > 0");
     for (int ax = 0; ax < 3; ++ax)
-      if (!c->probs[i].nodes[ax].empty()) {
-        if (c->probs[i].d.pde == MOLT_PDE_HJ)
-          return fail(c, MOLT_EUNSUPPORTED, "Hamilton-Jacobi steps run uniform grids");
-        any_nonuniform = true;
-      }
+      if (!c->probs[i].nodes[ax].empty()) any_nonuniform = true;
   }
   cudaError_t e;
   std::vector<double> t0(np);
@@ -2315,6 +2322,7 @@ molt_status molt_set_grid_axis(molt_ctx* c, int problem, int axis, const double*
   p.nu[axis] = Problem::NuCache{};
   if (!x) {
     p.nodes[axis].clear();
+    p.h[axis] = make_problem(p.d).h[axis];
     return MOLT_OK;
   }
   if (n != p.n[axis]) return fail(c, MOLT_EINVAL, "node count differs from the axis size");
@@ -2331,7 +2339,21 @@ molt_status molt_set_grid_axis(molt_ctx* c, int problem, int axis, const double*
     p.nu_sum = nullptr;
     return fail(c, MOLT_ENOMEM, "non-uniform axis sums");
   }
+  // Hamilton-Jacobi on non-uniform axes: the one-sided sums of every axis
+  if (p.d.pde == MOLT_PDE_HJ)
+    for (int k = 0; k < 2 * p.d.ndim; ++k)
+      if (!p.hv[k] && (e = cudaMalloc(&p.hv[k], state_bytes(p.d) * size_t(p.total))) != cudaSuccess) {
+        cudaGetLastError();
+        p.hv[k] = nullptr;
+        return fail(c, MOLT_ENOMEM, "Hamilton-Jacobi axis sums");
+      }
   p.nodes[axis].assign(x, x + n);
+  // the axis's spacing is its smallest cell (the periodic wrap cell
+  // included): the Hamilton-Jacobi alpha = beta/(cfl min h) and dt = cfl
+  // min_d h_d / c_d take it, as on uniform grids
+  double hmin = dir ? x[n - 1] - x[0] : L - (x[n - 1] - x[0]);
+  for (int64_t i = 1; i < n; ++i) hmin = std::min(hmin, x[i] - x[i - 1]);
+  p.h[axis] = hmin;
   return MOLT_OK;
 }
 

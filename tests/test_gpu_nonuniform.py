@@ -111,17 +111,6 @@ def test_rejected_setups():
             M.molt_set_grid_axis(ctx, 0, 0, _dir_nodes(3, 0.0, L))           # Dirichlet: n >= 4
     finally:
         M.molt_destroy(ctx)
-    dh = M.make_desc((n, n), lo=[0, 0], hi=[L, L], prec=M.PREC_F32, pde=M.PDE_HJ, quad_points=5,
-                     weights=M.W_WENOZ, cfl=0.5)
-    ctx = M.molt_create(dh)
-    try:
-        M.molt_set_grid_axis(ctx, 0, 0, _nodes(n, 0.0, L))
-        u = torch.zeros((n, n), dtype=torch.float32, device="cuda")
-        with pytest.raises(M.MoltError) as ei:
-            M.molt_step(ctx, u, None, nsteps=1, t=[0.0])                      # HJ: uniform grids
-        assert ei.value.status == M.MOLT_EUNSUPPORTED
-    finally:
-        M.molt_destroy(ctx)
     dw = M.make_desc((n,), lo=[0], hi=[L], prec=M.PREC_F32, quad_points=5, weights=M.W_LEARNED)
     ctx = M.molt_create(dw)
     try:

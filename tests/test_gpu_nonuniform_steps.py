@@ -2,8 +2,10 @@
 with the same nodes (the ``grids`` of ``oracle.schemes``): the wave
 leapfrog in mixed precision (2-D with a periodic and a Dirichlet
 non-uniform axis; 3-D with a strided Dirichlet z axis), the SSP-RK3 heat
-step in FP64 and mixed precision, and the advection-diffusion step (Burgers
-and linear flux) on stretched periodic axes."""
+step in FP64 and mixed precision, the advection-diffusion step (Burgers
+and linear flux) and the Hamilton-Jacobi step (forward Euler with WENO-Z,
+SSP-RK3 with the linear rule; lagged adaptive dt) on stretched periodic
+axes."""
 import numpy as np
 import pytest
 
@@ -170,3 +172,58 @@ def test_advection_diffusion_on_stretched_periodic_axes(case):
                                     grids=((ys, L), (xs, L)))
     for ax in (0, 1):
         assert_parity(got, want, tol_for(prec), max_for(prec), line_axis=ax, what="advection-diffusion")
+
+
+def _min_cell(x, L):
+    """The smallest cell of a periodic axis (the wrap cell included)."""
+    return float(min(np.diff(x).min(), L - (x[-1] - x[0])))
+
+
+@pytest.mark.parametrize("case", [("wenoz", M.PREC_F32, M.INT_EULER), ("wenoz", M.PREC_F64, M.INT_EULER),
+                                  ("linear", M.PREC_F64, M.INT_RK3)])
+def test_hamilton_jacobi_on_stretched_periodic_axes(case):
+    """H = |grad u|^2/2 with lagged adaptive dt on a stretched grid: the step
+    runs from the one-sided sums of both axes (the non-uniform sweep) and the
+    pointwise stage kernel; alpha and dt take each axis's smallest cell, as
+    the oracle does.  Forward Euler (P = 1) and SSP-RK3 (P = 2)."""
+    need_gpu()
+    import torch
+    weights, prec, integ = case
+    nx, ny, L = 96, 80, 2 * np.pi
+    xs, ys = _nodes(nx, L), _nodes(ny, L, amp=0.4)
+    u0 = (-np.cos(ys)[:, None] - np.cos(xs)[None, :] + 1e-3 * workloads.rng(8).standard_normal((ny, nx)))
+    if prec == M.PREC_F32:
+        u0 = u0.astype(np.float32).astype(np.float64)
+    rk3 = integ == M.INT_RK3
+    P = 2 if rk3 else 1
+    npts = 5 if weights == "wenoz" else 6
+    d = M.make_desc((nx, ny), lo=[0, 0], hi=[L, L], P=P, quad_points=npts,
+                    weights=M.W_WENOZ if weights == "wenoz" else M.W_LINEAR, beta=1.0 if not rk3 else 0.3,
+                    pde=M.PDE_HJ, cfl=1.5 if not rk3 else 0.5, dt=0.0, prec=prec, integrator=integ)
+    steps = 3
+    ctx = M.molt_create(d)
+    try:
+        M.molt_set_grid_axis(ctx, 0, 0, xs)
+        M.molt_set_grid_axis(ctx, 0, 1, ys)
+        u = to_dev(u0, state_dtype(prec))
+        t = M.molt_step(ctx, u, None, nsteps=steps, t=[0.0])
+        got = u.double().cpu().numpy()
+    finally:
+        M.molt_destroy(ctx)
+    grids = ((ys, L), (xs, L))
+    dxs = [_min_cell(ys, L), _min_cell(xs, L)]
+    cfl, beta = (0.5, 0.3) if rk3 else (1.5, 1.0)
+    uu, tt = u0, 0.0
+    if rk3:
+        sp = schemes.hj_initial_speeds_P(uu, dxs, cfl, beta, npts, weights, P, grids=grids)
+        for _ in range(steps):
+            uu, dt, sp = schemes.hj_step_rk3(uu, dxs, sp, tt, cfl, beta, npts, weights, P, grids=grids)
+            tt += dt
+    else:
+        sp = schemes.hj_initial_speeds(uu, dxs, cfl, beta, npts, weights, grids=grids)
+        for _ in range(steps):
+            uu, dt, sp = schemes.hj_step(uu, dxs, sp, cfl, beta, npts, weights, grids=grids)
+            tt += dt
+    for ax in (0, 1):
+        assert_parity(got, uu, tol_for(prec), max_for(prec), line_axis=ax, what="HJ %s" % str(case))
+    assert abs(t[0] - tt) < (1e-12 if prec == M.PREC_F64 else 1e-5) * tt

@@ -135,3 +135,17 @@ def test_advection_diffusion_on_a_stretched_grid_converges_at_third_order():
         errs.append(np.abs(u - math.exp(-kappa * steps * dt) * np.sin(x - steps * dt)).max())
     assert errs[1] < 1e-3
     assert errs[0] / errs[1] > 6.5, errs
+
+
+def test_uniform_nodes_reproduce_the_uniform_hj_rk3_step():
+    n, L = 20, 2 * np.pi
+    h = L / n
+    x = h * np.arange(n)
+    u = -np.cos(x)[None, :] + 0.5 * np.sin(x)[:, None]
+    grids = ((x, L), (x, L))
+    sp = schemes.hj_initial_speeds_P(u, [h, h], P=2, grids=grids)
+    np.testing.assert_allclose(sp, schemes.hj_initial_speeds_P(u, [h, h], P=2), rtol=1e-13)
+    got, dt, _ = schemes.hj_step_rk3(u, [h, h], sp, P=2, grids=grids)
+    want, dt2, _ = schemes.hj_step_rk3(u, [h, h], sp, P=2)
+    assert dt == dt2
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
