@@ -382,7 +382,15 @@ __device__ __forceinline__ T nu_direction(const NuTables<T>& tb, const T* v, T* 
 // (n + 6) and w (n) of T plus the segment maps.  WENO: local integrals by
 // WENO-Z with the point-local tables, else the linear point weights.
 template <typename T, typename TIO, bool WENO>
-__global__ void __launch_bounds__(512, 1) nonuniform_kernel(const NuArgs a, const NuTables<T> tb) {
+// FP32 lines take at most 64 registers (two 512-thread or four 256-thread
+// CTAs per SM: the scans' shuffle chains wait on latency, so more resident
+// warps keep the SM issuing; 4096^2: 1.14 -> 0.94 ms per S_2 step with the
+// linear rule, 2.39 -> 2.20 with WENO-Z); FP64 keeps 128 (it would spill).
+#ifndef MOLT_NU_MIN_BLOCKS_F32
+#define MOLT_NU_MIN_BLOCKS_F32 2
+#endif
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? MOLT_NU_MIN_BLOCKS_F32 : 1)
+    nonuniform_kernel(const NuArgs a, const NuTables<T> tb) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int n = a.g.n;
   const int nw = blockDim.x >> 5, part = threadIdx.x >> 5, lane = threadIdx.x & 31;
