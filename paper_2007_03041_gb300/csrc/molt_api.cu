@@ -235,17 +235,24 @@ int device_sms() {
 
 // Points per lane for a line of n points: the largest of 16, 8, 4 whose
 // tile fits the line exactly (n = 32 * E * nwl, nwl <= 16 warps), else 16
-// with masked (ragged) tiles.  FP64 sweeps of grids with few lines take the
-// largest E that still gives 16 warps per SM, else the smallest that fits:
-// their recurrences wait on the FP64 pipe (2 operations per SM per cycle),
-// so more warps per line hide more of its latency (256^2 heat: 0.129
-// instead of 0.165 ms per step with 4 instead of 8 points per lane), while
-// grids with many lines keep the larger tiles.
+// with masked (ragged) tiles.  FP64 sweeps of grids with few lines (fewer
+// than 16 warps per SM at that E; nlines counts the lines of every sweep
+// running at the same time) are bound by the latency of their recurrences
+// on the FP64 pipe, not by bandwidth, and take a shorter chain per lane:
+// two warps per line from 512 points on, and the largest E that still puts
+// 3 warps per SM in flight, else the smallest that fits.  Measured FP64 heat
+// steps (ms; axes one after another / both at once):
+//   256^2:  E=4 0.130/0.095  E=8 0.166/0.089
+//   512^2:  E=4 0.345/0.285  E=8 0.301/0.255  E=16 0.337/0.588
+//   1024^2: E=8 1.064        E=16 0.996      2048^2: E=8 3.91  E=16 3.68
 #ifndef MOLT_PREFER_E
 #define MOLT_PREFER_E 16
 #endif
 #ifndef MOLT_F64_SMALL_E
 #define MOLT_F64_SMALL_E 1
+#endif
+#ifndef MOLT_F64_WARPS_PER_SM
+#define MOLT_F64_WARPS_PER_SM 3
 #endif
 #ifndef MOLT_SMALL_TILE_THREADS
 #define MOLT_SMALL_TILE_THREADS 256
@@ -254,27 +261,29 @@ constexpr int kSmallTileThreads = MOLT_SMALL_TILE_THREADS;
 
 int choose_E(int n, bool f64, long long nlines) {
   auto fits = [n](int E) { return n % (32 * E) == 0 && n / (32 * E) <= kMaxThreads / 32; };
-  if (f64 && MOLT_F64_SMALL_E) {
-    const long long want = 16LL * device_sms();
+  static const int kOrder[4] = {MOLT_PREFER_E, 16, 8, 4};
+  int first = 0;
+  for (int i = 0; i < 4 && !first; ++i)
+    if (fits(kOrder[i])) first = kOrder[i];
+  if (!first) return kE;
+  const long long sms = device_sms();
+  if (f64 && MOLT_F64_SMALL_E && nlines * (n / (32 * first)) < 16 * sms) {
     int smallest = 0;
     for (int E : {16, 8, 4}) {
-      if (!fits(E)) continue;
-      if (nlines * (n / (32 * E)) >= want) return E;
+      if (!fits(E) || (n >= 512 && n / (32 * E) < 2)) continue;
       smallest = E;
+      if (nlines * (n / (32 * E)) >= (long long)MOLT_F64_WARPS_PER_SM * sms) return E;
     }
-    return smallest ? smallest : kE;
+    if (smallest) return smallest;
   }
-  static const int kOrder[4] = {MOLT_PREFER_E, 16, 8, 4};
-  for (int i = 0; i < 4; ++i)
-    if (fits(kOrder[i])) return kOrder[i];
-  return kE;
+  return first;
 }
 
 // E = 0: the planner chooses E and, for grids with few lines, fewer lines per
 // CTA so that at least two CTAs per SM are launched.  E != 0: that E and the
 // full-CTA tile shape (the batched kernel's tiles).
 molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, double alpha, Plan* out,
-                      int E = 0) {
+                      int E = 0, int concurrent_sweeps = 1) {
   SweepArgs& a = out->a;
   std::memset(&a, 0, sizeof(a));
   out->ax = ax;
@@ -282,7 +291,7 @@ molt_status plan_axis(molt_ctx* c, const Problem& p, int ax, int mode, int P, do
   a.g = geom(p, ax);
   const int n = a.g.n;
   const bool auto_shape = E == 0;
-  if (auto_shape) E = choose_E(n, compute_bytes(p.d) == 8, a.g.nlines);
+  if (auto_shape) E = choose_E(n, compute_bytes(p.d) == 8, a.g.nlines * concurrent_sweeps);
   a.E = E;
   a.bc = p.d.bc[ax];
   a.mode = mode;
@@ -1234,7 +1243,7 @@ molt_status heat_step_axis_streams(molt_ctx* c, Problem& p, void* u) {
       return cuda_fail(c, e, "stream fork");
     for (int ax = 0; ax < p.d.ndim; ++ax) {
       Plan pl;
-      molt_status st = plan_axis(c, p, ax, MODE_0, p.d.P, alpha, &pl);
+      molt_status st = plan_axis(c, p, ax, MODE_0, p.d.P, alpha, &pl, 0, 2);   // two sweeps at once
       if (st != MOLT_OK) return st;
       pl.a.in = sweep_input(p, ins[s]);
       pl.a.acc = ax == 0 ? p.acc : p.acc2;
