@@ -377,7 +377,8 @@ def run_ours(args):
     M.molt_set_option(ctx, M.OPT_PROFILE, 1)
     t = M.molt_step(ctx, u, up, nsteps=args.steps, t=t)
     per_kernel, kernel_names, launches = {}, {}, {}
-    for name, kinds in (("x", ((M.KERNEL_LANES_ACC_SET, "lanes_sweep_kernel ACC_SET (x lines)"),
+    for name, kinds in (("x", ((M.KERNEL_XLINES_ACC_SET, "xline_sweep_kernel ACC_SET (x lines, one warp per line)"),
+                               (M.KERNEL_LANES_ACC_SET, "lanes_sweep_kernel ACC_SET (x lines)"),
                                (M.KERNEL_ACC_SET, "sweep_tma_kernel ACC_SET (x lines)"))),
                         ("yz", ((M.KERNEL_LANES_ACC_ADD, "lanes_sweep_kernel ACC_ADD (y lines)"),
                                 (M.KERNEL_ACC_ADD, "sweep_tma_kernel ACC_ADD (y and z lines)"))),

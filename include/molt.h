@@ -286,12 +286,19 @@ typedef enum {
                                      the line shape allows and nu*16 >= ~3.5;
                                      2 whenever the shape allows; 0 never.
                                      Both kernels compute the same values      */
-  MOLT_OPT_AXIS_STREAMS = 5       /* heat problems of up to 2^18 points in 2-D
+  MOLT_OPT_AXIS_STREAMS = 5,      /* heat problems of up to 2^18 points in 2-D
                                      or 3-D: 1 (default) runs the x sweep of a
                                      stage on the context's stream and the y
                                      (and z) sweeps on a second stream at the
                                      same time, then one update kernel; 0 runs
                                      the axes one after another.  Same values */
+  MOLT_OPT_XLINES = 6             /* x lines of the FP32 sweeps that
+                                     MOLT_OPT_LANES admits: 1 (default) one
+                                     warp per line group (lanes = 16-point
+                                     segments, carries by warp shuffles), for
+                                     any number of lines; 0 the line-per-lane
+                                     tiles.  Same values up to FP32 rounding
+                                     (the carries are summed in another order) */
 } molt_option;
 molt_status molt_set_option(molt_ctx* ctx, int option, int64_t value);
 
@@ -312,8 +319,11 @@ typedef enum {
   MOLT_KERNEL_LANES_STORE = 11,   /* line-per-lane sweeps (MOLT_OPT_LANES):      */
   MOLT_KERNEL_LANES_ACC_SET = 12, /*   STORE, ACC_SET, and ACC_ADD / the        */
   MOLT_KERNEL_LANES_ACC_ADD = 13, /*   advection-diffusion accumulations,       */
-  MOLT_KERNEL_LANES_WAVE_FINAL = 14 /* and the last axis of the mixed-precision
+  MOLT_KERNEL_LANES_WAVE_FINAL = 14, /* and the last axis of the mixed-precision
                                      wave step with the FP64 leapfrog update  */
+  MOLT_KERNEL_XLINES_STORE = 15,   /* warp-per-line x sweeps (MOLT_OPT_XLINES): */
+  MOLT_KERNEL_XLINES_ACC_SET = 16, /*   STORE, ACC_SET, and ACC_ADD / the       */
+  MOLT_KERNEL_XLINES_ACC_ADD = 17  /*   advection-diffusion accumulations       */
 } molt_kernel_kind;
 
 /* With MOLT_OPT_PROFILE on: synchronises the stream, returns the summed

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmolt.so")
 
 SOURCES = ["molt_api.cu", "sweep_f64.cu", "sweep_mixed.cu", "sweep_f32.cu", "sweep_hj_general.cu", "sweep_advdiff.cu",
-           "sweep_lanes.cu", "noalloc.cu", "mlp.cu",
+           "sweep_lanes.cu", "sweep_xlines.cu", "batch.cu", "noalloc.cu", "mlp.cu",
            "coeffs.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]

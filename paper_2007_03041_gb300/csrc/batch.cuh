@@ -222,6 +222,11 @@ __device__ __forceinline__ int find_update(const BatchParams& p, long long chunk
 #ifndef MOLT_BATCH_MIN_BLOCKS
 #define MOLT_BATCH_MIN_BLOCKS 2
 #endif
+#ifndef MOLT_BATCH_KERNEL_TU
+// defined in csrc/batch.cu (its own translation unit: FP32 <-> FP64
+// conversions selected in place, MOLT_CONV_SELECT)
+__global__ void batch_heat_kernel(const BatchParams p);
+#else
 __global__ void __launch_bounds__(512, MOLT_BATCH_MIN_BLOCKS) batch_heat_kernel(const BatchParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SweepArgs sa;
@@ -326,5 +331,7 @@ __global__ void __launch_bounds__(512, MOLT_BATCH_MIN_BLOCKS) batch_heat_kernel(
     }
   }
 }
+
+#endif  // MOLT_BATCH_KERNEL_TU
 
 }  // namespace molt

@@ -98,6 +98,7 @@ struct molt_ctx {
   double* tnow_dev = nullptr;      // per problem time at the start of the step (HJ source)
   bool no_tma = false;             // force the plain kernels (molt_set_option)
   int lanes = 1;                   // line-per-lane FP32 sweeps: 0 off, 1 auto, 2 whenever the shape allows
+  int xlines = 1;                  // x lines of those sweeps one warp per line (0: line-per-lane tiles)
   void* mlp_blob = nullptr;        // learned weights: the BF16 network (MlpBlob)
   unsigned long long* mlp_stats = nullptr;  // [stencils evaluated, fallbacks]
   bool mlp_ready = false;          // molt_set_mlp has been called
@@ -489,6 +490,8 @@ cudaError_t launch(const Problem& p, int epi, const Plan& pl, cudaStream_t s, bo
 constexpr int kLanesAutoDepth = 8;
 constexpr double kLanesTailWeight = 1.4901161193847656e-08;   // 2^-26
 
+bool lane_constants(const Problem& p, const Plan& pl, LanesArgs* Lp);
+
 bool plan_lanes(const molt_ctx* c, const Problem& p, int epi, const Plan& pl, bool f32_input, LanesArgs* la,
                 CUtensorMap* map) {
   if (c->lanes == 0) return false;
@@ -565,6 +568,18 @@ bool plan_lanes(const molt_ctx* c, const Problem& p, int epi, const Plan& pl, bo
       return false;
   }
   if (L.ntiles < 1 || L.ntiles >= (1LL << 31)) return false;
+  if (!lane_constants(p, pl, &L)) return false;
+  if (c->lanes == 1 && L.lb > kLanesAutoDepth) return false;
+  *la = L;
+  return true;
+}
+
+// The FP32 filter taps, decays, FP64 boundary constants and look-back depth
+// of a linear-rule line sweep in difference form (L->n, S, bc, mode set).
+bool lane_constants(const Problem& p, const Plan& pl, LanesArgs* Lp) {
+  LanesArgs& L = *Lp;
+  const SweepArgs& a = pl.a;
+  const int n = L.n;
   // quadrature weights (FP64) and the FP32 decay the kernel runs
   const double nu = a.alpha * p.h[pl.ax];
   QuadTable qt;
@@ -606,8 +621,63 @@ bool plan_lanes(const molt_ctx* c, const Problem& p, int epi, const Plan& pl, bo
     ++lb;
   }
   L.lb = lb;
-  if (c->lanes == 1 && lb > kLanesAutoDepth) return false;
-  *la = L;
+  return true;
+}
+
+// Warp-per-line FP32 sweeps of x lines (csrc/sweep_xlines.cuh): the same
+// operations, inputs and epilogues as the line-per-lane kernel's x lines,
+// for any number of lines; a line of n = 16 S points takes S lanes.
+bool plan_xlines(const molt_ctx* c, const Problem& p, int epi, const Plan& pl, bool f32_input, XLineArgs* xa) {
+  if (c->lanes == 0 || c->xlines == 0 || pl.ax != 0) return false;
+  const SweepArgs& a = pl.a;
+  if (compute_bytes(p.d) != 4 || !f32_input || p.d.weights != MOLT_W_LINEAR) return false;
+  if (!p.nodes[pl.ax].empty() || a.g.stride != 1) return false;
+  if (a.mode != MODE_0 && a.mode != MODE_R && a.mode != MODE_L) return false;
+  if (a.P < 1 || a.P > 2) return false;
+  if (epi != EPI_ACC_SET && epi != EPI_ACC_ADD && epi != EPI_ACC_AXPY && !(epi == EPI_STORE && is_f32_state(p.d)))
+    return false;
+  const int n = a.g.n;
+  if (n % kXlSeg != 0 || n < kXlSeg || n > kXlSeg * 32) return false;
+  const void* outp = epi == EPI_STORE ? a.out : a.acc;
+  if (!a.in || !outp || ((reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(outp)) & 15)) return false;
+  LanesArgs L;
+  std::memset(&L, 0, sizeof(L));
+  L.n = n;
+  L.S = n / kXlSeg;
+  L.bc = a.bc;
+  L.mode = a.mode;
+  L.P = a.P;
+  if (!lane_constants(p, pl, &L)) return false;
+  if (c->lanes == 1 && L.lb > kLanesAutoDepth) return false;
+  XLineArgs X;
+  std::memset(&X, 0, sizeof(X));
+  X.n = n;
+  X.S = L.S;
+  X.G = (L.S & (L.S - 1)) == 0 ? 32 / L.S : 1;
+  X.width = X.G > 1 ? L.S : 32;
+  X.nlines = a.g.nlines;
+  X.ngroups = (X.nlines + X.G - 1) / X.G;
+  X.bc = L.bc;
+  X.mode = L.mode;
+  X.P = L.P;
+  X.lb = L.lb;
+  X.needA = L.needA;
+  X.needB = L.needB;
+  for (int i = 0; i < 5; ++i) {
+    X.bR[i] = L.bR[i];
+    X.bL[i] = L.bL[i];
+  }
+  X.q = L.q;
+  // Kogge-Stone multipliers (q^16)^(2^k), from the FP32 q the scans run
+  double qk = std::pow(double(L.q), double(kXlSeg));
+  for (int k = 0; k < 5; ++k, qk *= qk) X.qd[k] = float(qk);
+  X.kA = L.kA;
+  X.kB = L.kB;
+  X.coef = float(a.coefS);
+  X.in = static_cast<const float*>(a.in);
+  X.out = static_cast<float*>(a.out);
+  X.acc = static_cast<float*>(a.acc);
+  *xa = X;
   return true;
 }
 
@@ -620,6 +690,27 @@ molt_status run(molt_ctx* c, const Problem& p, int epi, Plan& pl, bool from_stat
   if (!p.nodes[pl.ax].empty()) return run_nonuniform(c, p, epi, pl);
   // element size of the sweep input: FP64 except FP32 state or the FP32 copy
   const size_t in_bytes = is_f32_state(p.d) || (is_mixed(p.d) && from_state_copy) ? 4 : 8;
+  {
+    XLineArgs xa;
+    if (plan_xlines(c, p, epi, pl, in_bytes == 4, &xa)) {
+      molt_ctx::Rec rec{epi == EPI_STORE ? int(MOLT_KERNEL_XLINES_STORE)
+                        : epi == EPI_ACC_SET ? int(MOLT_KERNEL_XLINES_ACC_SET)
+                                             : int(MOLT_KERNEL_XLINES_ACC_ADD),
+                        nullptr, nullptr};
+      if (c->profile) {
+        cudaEventCreate(&rec.start);
+        cudaEventCreate(&rec.stop);
+        cudaEventRecord(rec.start, s);
+      }
+      const cudaError_t e = launch_xlines(epi, xa, s);
+      if (c->profile) {
+        cudaEventRecord(rec.stop, s);
+        c->recs.push_back(rec);
+      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "warp-per-line sweep launch");
+      return MOLT_OK;
+    }
+  }
   {
     LanesArgs la;
     CUtensorMap lmap;
@@ -2379,6 +2470,9 @@ molt_status molt_set_option(molt_ctx* c, int option, int64_t value) {
   } else if (option == MOLT_OPT_AXIS_STREAMS) {
     if (value != 0 && value != 1) return fail(c, MOLT_EINVAL, "option value must be 0 or 1");
     c->axis_streams = int(value);
+  } else if (option == MOLT_OPT_XLINES) {
+    if (value != 0 && value != 1) return fail(c, MOLT_EINVAL, "option value must be 0 or 1");
+    c->xlines = int(value);
   } else {
     if (value != 0 && value != 1) return fail(c, MOLT_EINVAL, "option value must be 0 or 1");
     if (option == MOLT_OPT_TMA) c->no_tma = value == 0;
@@ -2389,8 +2483,9 @@ molt_status molt_set_option(molt_ctx* c, int option, int64_t value) {
     else if (option == MOLT_OPT_TEST_SKIP_ARRIVE) c->test_skip_arrive = value == 1;
     else return fail(c, MOLT_EINVAL, "unknown option");
   }
-  // baked into the captured batch step: rebuild it on the next step
+  // baked into the captured batch and heat steps: rebuild them on the next step
   c->batch.last_u.clear();
+  for (auto& p : c->probs) p.heat_graph_u = nullptr;
   return MOLT_OK;
 }
 

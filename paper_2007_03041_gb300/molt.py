@@ -29,10 +29,11 @@ EXPORTS = ("molt_create", "molt_apply_D", "molt_step", "molt_set_option", "molt_
 NU_WENO_SLOTS = 30
 MLP_PARAMS = 1347
 MLP_BLOB_BYTES = 3728
-OPT_TMA, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_TEST_SKIP_ARRIVE, OPT_LANES, OPT_AXIS_STREAMS = 0, 1, 2, 3, 4, 5
+OPT_TMA, OPT_PROFILE, OPT_WAIT_LIMIT, OPT_TEST_SKIP_ARRIVE, OPT_LANES, OPT_AXIS_STREAMS, OPT_XLINES = 0, 1, 2, 3, 4, 5, 6
 (KERNEL_STORE, KERNEL_ACC_SET, KERNEL_ACC_ADD, KERNEL_HEAT_FINAL, KERNEL_WAVE_FINAL, KERNEL_HJ_X, KERNEL_HJ_Y,
  KERNEL_UPDATE, KERNEL_BATCH, KERNEL_TRANSPOSE, KERNEL_FLUX, KERNEL_LANES_STORE, KERNEL_LANES_ACC_SET,
- KERNEL_LANES_ACC_ADD, KERNEL_LANES_WAVE_FINAL) = range(15)
+ KERNEL_LANES_ACC_ADD, KERNEL_LANES_WAVE_FINAL, KERNEL_XLINES_STORE, KERNEL_XLINES_ACC_SET,
+ KERNEL_XLINES_ACC_ADD) = range(18)
 
 
 class molt_desc(ctypes.Structure):

@@ -1,5 +1,6 @@
 """GPU parity of the line-per-lane FP32 sweeps (one lane per line, one warp
-per 16-point segment, difference form of the recurrences) against the FP64
+per 16-point segment, difference form of the recurrences) and of the
+warp-per-line x sweeps (one lane per 16-point segment) against the FP64
 oracle: every axis, both boundary types, the three operators, the 3/5/6-point
 rules, P = 1 and 2, lines of 16 to 512 points, decays with a short look-back
 (nu = 0.4: terms below 2^-40 dropped after 5 segments) and without truncation
@@ -24,23 +25,25 @@ def _shape_for(axis, n):
     return {0: (4, 8, n), 1: (3, n, 32), 2: (n, 2, 64)}[axis]
 
 
-def _apply(u, axis, op, P, alpha, bc, npts, lanes, inplace=False, lanes_launches=None):
+def _apply(u, axis, op, P, alpha, bc, npts, lanes, inplace=False, lanes_launches=None, xlines=1):
     """S_P along `axis` through molt_apply_D (FP32 state); appends to
-    `lanes_launches` how many line-per-lane launches ran."""
+    `lanes_launches` how many (line-per-lane, warp-per-line) launches ran."""
     import torch
     shape_xyz = tuple(reversed(u.shape))
     d = M.make_desc(shape_xyz, bc=[bc] * 3, P=P, quad_points=npts, prec=M.PREC_F32)
     ctx = M.molt_create(d)
     try:
         M.molt_set_option(ctx, M.OPT_LANES, lanes)
+        M.molt_set_option(ctx, M.OPT_XLINES, xlines)
         M.molt_set_option(ctx, M.OPT_PROFILE, 1)
         x = to_dev(u, torch.float32)
         out = x if inplace else torch.empty_like(x)
         M.molt_apply_D(ctx, 0, axis, op, P, alpha, x, out)
         torch.cuda.synchronize()
         _, nl = M.molt_profile_read(ctx, M.KERNEL_LANES_STORE)
+        _, nx = M.molt_profile_read(ctx, M.KERNEL_XLINES_STORE)
         if lanes_launches is not None:
-            lanes_launches.append(nl)
+            lanes_launches.append((nl, nx))
         return out.double().cpu().numpy()
     finally:
         M.molt_destroy(ctx)
@@ -67,25 +70,31 @@ def test_lanes_apply_D_matches_oracle(axis, bc, op):
         N = n if bc == M.BC_PERIODIC else n - 1
         h = 1.0 / N
         alpha = nu / h
-        got = _apply(u, axis, op, P, alpha, bc, npts, lanes=2)
         want = sweep.partial_sum(u, np_axis(3, axis), alpha, h, OPS[op], BCS[bc], npts, P)
-        assert_parity(got, want, TOL_F32, MAX_F32, line_axis=np_axis(3, axis),
-                      what="axis %d n %d npts %d P %d nu %g" % (axis, n, npts, P, nu))
+        # x lines: the warp-per-line kernel and the line-per-lane tiles
+        for xl in ((1, 0) if axis == 0 else (1,)):
+            got = _apply(u, axis, op, P, alpha, bc, npts, lanes=2, xlines=xl)
+            assert_parity(got, want, TOL_F32, MAX_F32, line_axis=np_axis(3, axis),
+                          what="axis %d n %d npts %d P %d nu %g xlines %d" % (axis, n, npts, P, nu, xl))
 
 
 def test_lanes_kernel_runs_and_agrees_with_the_scan_kernel():
-    """The auto choice takes the line-per-lane kernel at nu = 0.4 (and the
-    scan kernel when the option is off); both agree to FP32 rounding."""
+    """The auto choice takes the warp-per-line kernel for x lines and the
+    line-per-lane kernel for y and z lines at nu = 0.4 (the line-per-lane
+    tiles for x lines too with MOLT_OPT_XLINES off, the scan kernel with
+    MOLT_OPT_LANES off); all agree to FP32 rounding."""
     need_gpu()
     n = 512
     for axis in (0, 1, 2):
         u = _case(axis, n, M.BC_DIRICHLET, seed=7 + axis)
         alpha = 0.4 * (n - 1)
-        la, lb = [], []
+        la, lb, lc = [], [], []
         a = _apply(u, axis, M.OP_0, 2, alpha, M.BC_DIRICHLET, 6, lanes=1, lanes_launches=la)
         b = _apply(u, axis, M.OP_0, 2, alpha, M.BC_DIRICHLET, 6, lanes=0, lanes_launches=lb)
-        assert la == [1] and lb == [0], (axis, la, lb)
+        c = _apply(u, axis, M.OP_0, 2, alpha, M.BC_DIRICHLET, 6, lanes=1, lanes_launches=lc, xlines=0)
+        assert la == [(0, 1) if axis == 0 else (1, 0)] and lb == [(0, 0)] and lc == [(1, 0)], (axis, la, lb, lc)
         assert_parity(a, b, 2e-6, 1e-5, line_axis=np_axis(3, axis), what="lanes vs scan axis %d" % axis)
+        assert_parity(c, b, 2e-6, 1e-5, line_axis=np_axis(3, axis), what="tiles vs scan axis %d" % axis)
 
 
 def test_lanes_in_place_and_constants():
@@ -123,12 +132,13 @@ def test_wave_step_on_lanes_kernels_matches_oracle(n):
         up = torch.zeros_like(u)
         M.molt_set_option(ctx, M.OPT_PROFILE, 1)
         M.molt_step(ctx, u, up, nsteps=1, t=[0.0])
-        _, nset = M.molt_profile_read(ctx, M.KERNEL_LANES_ACC_SET)
+        _, nset = M.molt_profile_read(ctx, M.KERNEL_XLINES_ACC_SET)
         _, nadd = M.molt_profile_read(ctx, M.KERNEL_LANES_ACC_ADD)
         _, nfin = M.molt_profile_read(ctx, M.KERNEL_LANES_WAVE_FINAL)
         _, nupd = M.molt_profile_read(ctx, M.KERNEL_UPDATE)
         M.molt_set_option(ctx, M.OPT_PROFILE, 0)
-        # x, y, z on the line-per-lane kernel, then the FP64 update kernel
+        # x on the warp-per-line kernel, y and z on the line-per-lane kernel,
+        # then the FP64 update kernel
         assert (nset, nadd, nfin, nupd) == (1, 2, 0, 1), (nset, nadd, nfin, nupd)
         M.molt_step(ctx, u, up, nsteps=9, t=[dt])
         got, gotp = u.cpu().numpy(), up.cpu().numpy()
