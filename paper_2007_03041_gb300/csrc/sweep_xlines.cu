@@ -5,9 +5,9 @@ namespace molt {
 
 namespace {
 
-template <int EPI>
+template <int EPI, int BC, int SF>
 cudaError_t launch_one(const XLineArgs& a, cudaStream_t s) {
-  auto k = &xline_sweep_kernel<EPI>;
+  auto k = &xline_sweep_kernel<EPI, BC, SF>;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kXlSmemBytes));
@@ -28,18 +28,25 @@ cudaError_t launch_one(const XLineArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int EPI>
+cudaError_t launch_shape(const XLineArgs& a, cudaStream_t s) {
+  const bool full = a.S == 32;
+  if (a.bc == 1) return full ? launch_one<EPI, 1, 32>(a, s) : launch_one<EPI, 1, 0>(a, s);
+  return full ? launch_one<EPI, 0, 32>(a, s) : launch_one<EPI, 0, 0>(a, s);
+}
+
 }  // namespace
 
 cudaError_t launch_xlines(int epi, const XLineArgs& a, cudaStream_t s) {
   if (a.S < 1 || a.S > 32 || a.n != a.S * kXlSeg || a.P < 1 || a.P > 2 || a.nlines < 1 || a.lb < 0 ||
       a.lb > a.S || a.G < 1 || a.G * a.S > 32 || a.ngroups != (a.nlines + a.G - 1) / a.G ||
-      (a.G > 1 && (a.S & (a.S - 1)) != 0) || a.width != (a.G > 1 ? a.S : 32))
+      (a.G > 1 && (a.S & (a.S - 1)) != 0) || a.width != (a.G > 1 ? a.S : 32) || (a.bc != 0 && a.bc != 1))
     return cudaErrorInvalidValue;
   switch (epi) {
-    case EPI_STORE: return launch_one<EPI_STORE>(a, s);
-    case EPI_ACC_SET: return launch_one<EPI_ACC_SET>(a, s);
-    case EPI_ACC_ADD: return launch_one<EPI_ACC_ADD>(a, s);
-    case EPI_ACC_AXPY: return launch_one<EPI_ACC_AXPY>(a, s);
+    case EPI_STORE: return launch_shape<EPI_STORE>(a, s);
+    case EPI_ACC_SET: return launch_shape<EPI_ACC_SET>(a, s);
+    case EPI_ACC_ADD: return launch_shape<EPI_ACC_ADD>(a, s);
+    case EPI_ACC_AXPY: return launch_shape<EPI_ACC_AXPY>(a, s);
     default: return cudaErrorNotSupported;
   }
 }

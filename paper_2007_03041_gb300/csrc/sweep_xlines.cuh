@@ -51,6 +51,13 @@ constexpr int kXlBuf = 512;       // floats of one warp's line group (G n)
 #define MOLT_XL_STAGES 4
 #endif
 constexpr int kXlStages = MOLT_XL_STAGES;
+// 1: the 5-tap filters of both directions as packed FP32x2 operations (same
+// sums in the same order; measured on the 512^3 wave x sweep: 0.304 ms
+// against 0.287 with scalar taps -- building the operand pairs costs more
+// than the halved FMA count saves)
+#ifndef MOLT_XL_PAIRED_TAPS
+#define MOLT_XL_PAIRED_TAPS 0
+#endif
 constexpr size_t kXlSmemBytes = size_t(kXlWarps) * kXlStages * kXlBuf * sizeof(float);
 
 struct XLineArgs {
@@ -93,12 +100,20 @@ __device__ __forceinline__ void xl_wait_ahead() {
 // Copies line group `grp` (G consecutive lines, G n floats) into `buf`;
 // lines past the end of the array are not copied (their lanes' results are
 // never stored).
+template <int SF>
 __device__ __forceinline__ void xl_issue(const XLineArgs& a, long long grp, float* buf, int lane) {
-  const long long line0 = grp * a.G;
-  const long long rem = a.nlines - line0;
-  const int avail = int((rem < a.G ? rem : a.G) * a.n);    // floats
-  const float* src = a.in + line0 * a.n;
-  for (int c = lane; 4 * c < avail; c += 32) xl_cp16(buf + xl_chunk(c), src + 4 * c);
+  if constexpr (SF == 32) {
+    // one 512-point line per group
+    const float* src = a.in + grp * kXlBuf;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) xl_cp16(buf + xl_chunk(lane + 32 * j), src + 4 * (lane + 32 * j));
+  } else {
+    const long long line0 = grp * a.G;
+    const long long rem = a.nlines - line0;
+    const int avail = int((rem < a.G ? rem : a.G) * a.n);    // floats
+    const float* src = a.in + line0 * a.n;
+    for (int c = lane; 4 * c < avail; c += 32) xl_cp16(buf + xl_chunk(c), src + 4 * c);
+  }
 }
 
 // Own 16 points of a lane.
@@ -132,13 +147,17 @@ struct XlLane {
 };
 
 // One application of D on the segment: v (own points, registers) ->
-// D = W_R + W_L (D_0; the 1/2 is in the taps) or W_R / W_L.
+// D = W_R + W_L (D_0; the 1/2 is in the taps) or W_R / W_L.  BC: 0 periodic,
+// 1 Dirichlet; SF: 32 for 512-point lines (one line a warp, every lane
+// active), 0 for the shape in the arguments.
+template <int BC, int SF>
 __device__ __forceinline__ void xl_apply_D(const XLineArgs& a, const XlLane& L, const float (&v)[kXlSeg],
                                            float (&D)[kXlSeg]) {
   const unsigned FULL = 0xffffffffu;
-  const int S = a.S;
-  const bool active = L.s < S;
-  const int first = L.lane - L.s, last = first + S - 1;
+  const int S = SF ? SF : a.S;
+  const int width = SF ? 32 : a.width;
+  const bool active = SF ? true : L.s < S;
+  const int first = SF ? 0 : L.lane - L.s, last = first + S - 1;
   const int rs = active ? S - 1 - L.s : -1;          // segments to the right
   float2 Y[kXlSeg];
   float2 y;
@@ -148,14 +167,14 @@ __device__ __forceinline__ void xl_apply_D(const XLineArgs& a, const XlLane& L, 
 #pragma unroll
     for (int t = 0; t < kXlSeg; ++t) w[t + 3] = v[t];
     // neighbouring segments' lanes (periodic wrap within the group)
-    const int left = !active ? L.lane : (L.s > 0 ? L.lane - 1 : last);
-    const int right = !active ? L.lane : (rs > 0 ? L.lane + 1 : first);
+    const int left = SF ? ((L.lane + 31) & 31) : (!active ? L.lane : (L.s > 0 ? L.lane - 1 : last));
+    const int right = SF ? ((L.lane + 1) & 31) : (!active ? L.lane : (rs > 0 ? L.lane + 1 : first));
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       w[k] = __shfl_sync(FULL, v[13 + k], left);
       w[19 + k] = __shfl_sync(FULL, v[k], right);
     }
-    if (a.bc == 1) {
+    if constexpr (BC == 1) {
       // Dirichlet: odd reflection about the end value, v_{-j} = 2 v_0 - v_j
       if (L.s == 0) {
 #pragma unroll
@@ -169,6 +188,18 @@ __device__ __forceinline__ void xl_apply_D(const XLineArgs& a, const XlLane& L, 
     float d[21];
 #pragma unroll
     for (int k = 0; k < 21; ++k) d[k] = w[k + 1] - w[k];
+#if MOLT_XL_PAIRED_TAPS
+    // Y[t] = (K_R(p0+t), K_L(p0+15-t)) as packed FP32x2 filters: with
+    // P[k] = (d[k], d[20-k]), Y[t] = sum_i (bR[i], bL[i]) P[t+i]
+#pragma unroll
+    for (int t = 0; t < kXlSeg; ++t) {
+      float2 r = mul2(make_float2(a.bR[0], a.bL[0]), make_float2(d[t], d[20 - t]));
+#pragma unroll
+      for (int i = 1; i < 5; ++i)
+        r = fma2(make_float2(a.bR[i], a.bL[i]), make_float2(d[t + i], d[20 - t - i]), r);
+      Y[t] = r;
+    }
+#else
 #pragma unroll
     for (int t = 0; t < kXlSeg; ++t) {
       float r = a.bR[0] * d[t];
@@ -183,8 +214,9 @@ __device__ __forceinline__ void xl_apply_D(const XLineArgs& a, const XlLane& L, 
       for (int i = 1; i < 5; ++i) l = fmaf(a.bL[i], d[u + 5 - i], l);
       Y[kXlSeg - 1 - u].y = l;
     }
+#endif
   }
-  if (a.bc == 1) {
+  if constexpr (BC == 1) {
     if (L.s == 0) Y[0].x = 0.f;      // K_R(x_0): the right-moving recurrence starts here
     if (rs == 0) Y[0].y = 0.f;     // K_L(x_{n-1})
   }
@@ -198,13 +230,14 @@ __device__ __forceinline__ void xl_apply_D(const XLineArgs& a, const XlLane& L, 
   for (int k = 0; k < 5; ++k) {
     const int dd = 1 << k;
     if (dd >= S) break;
-    const float tR = __shfl_up_sync(FULL, XR, dd, a.width);
-    const float tL = __shfl_down_sync(FULL, XL, dd, a.width);
-    if (L.s >= dd) XR = fmaf(a.qd[k], tR, XR);
-    if (rs >= dd) XL = fmaf(a.qd[k], tL, XL);
+    const float tR = __shfl_up_sync(FULL, XR, dd, width);
+    const float tL = __shfl_down_sync(FULL, XL, dd, width);
+    const float nR = fmaf(a.qd[k], tR, XR), nL = fmaf(a.qd[k], tL, XL);
+    XR = L.s >= dd ? nR : XR;
+    XL = rs >= dd ? nL : XL;
   }
-  float cR = __shfl_up_sync(FULL, XR, 1, a.width);
-  float cL = __shfl_down_sync(FULL, XL, 1, a.width);
+  float cR = __shfl_up_sync(FULL, XR, 1, width);
+  float cL = __shfl_down_sync(FULL, XL, 1, width);
   if (L.s == 0) cR = 0.f;
   if (rs == 0) cL = 0.f;
   if (a.needA || a.needB) {
@@ -237,20 +270,20 @@ __device__ __forceinline__ void xl_apply_D(const XLineArgs& a, const XlLane& L, 
   for (int t = 0; t < kXlSeg; ++t) D[t] = Y[t].x + Y[kXlSeg - 1 - t].y;
 }
 
-template <int EPI>
+template <int EPI, int BC, int SF>
 __global__ void __launch_bounds__(kXlWarps * 32, MOLT_XL_MIN_BLOCKS) xline_sweep_kernel(const XLineArgs a) {
   extern __shared__ __align__(128) float xl_smem[];
   const int warp = threadIdx.x >> 5;
   float* wbuf = xl_smem + warp * (kXlStages * kXlBuf);   // this warp's kXlStages group buffers
   XlLane L;
   L.lane = threadIdx.x & 31;
-  L.s = a.G > 1 ? (L.lane & (a.S - 1)) : L.lane;
+  L.s = (SF == 0 && a.G > 1) ? (L.lane & (a.S - 1)) : L.lane;
   const long long nw = (long long)gridDim.x * kXlWarps;
   long long grp = (long long)blockIdx.x * kXlWarps + warp;
   // copies of the first kXlStages - 1 groups, one commit group each
 #pragma unroll
   for (int i = 0; i < kXlStages - 1; ++i) {
-    if (grp + i * nw < a.ngroups) xl_issue(a, grp + i * nw, wbuf + i * kXlBuf, L.lane);
+    if (grp + i * nw < a.ngroups) xl_issue<SF>(a, grp + i * nw, wbuf + i * kXlBuf, L.lane);
     xl_commit();
   }
   for (int b = 0; grp < a.ngroups; grp += nw, b = b + 1 == kXlStages ? 0 : b + 1) {
@@ -260,7 +293,7 @@ __global__ void __launch_bounds__(kXlWarps * 32, MOLT_XL_MIN_BLOCKS) xline_sweep
     // iteration), then wait for this group's data
     const long long ahead = grp + (kXlStages - 1) * nw;
     const int bn = b == 0 ? kXlStages - 1 : b - 1;
-    if (ahead < a.ngroups) xl_issue(a, ahead, wbuf + bn * kXlBuf, L.lane);
+    if (ahead < a.ngroups) xl_issue<SF>(a, ahead, wbuf + bn * kXlBuf, L.lane);
     xl_commit();
     xl_wait_ahead();
     __syncwarp();
@@ -268,12 +301,12 @@ __global__ void __launch_bounds__(kXlWarps * 32, MOLT_XL_MIN_BLOCKS) xline_sweep
     {
       float v[kXlSeg];
       xl_load_own(buf, L.lane, v);
-      xl_apply_D(a, L, v, D);
+      xl_apply_D<BC, SF>(a, L, v, D);
     }
     if (a.P == 2) {
       xl_store_own(buf, L.lane, D);       // D of the first power, reread below
       float D2[kXlSeg];
-      xl_apply_D(a, L, D, D2);
+      xl_apply_D<BC, SF>(a, L, D, D2);
       xl_load_own(buf, L.lane, D);
 #pragma unroll
       for (int t = 0; t < kXlSeg; ++t) D[t] += D2[t];
@@ -284,8 +317,9 @@ __global__ void __launch_bounds__(kXlWarps * 32, MOLT_XL_MIN_BLOCKS) xline_sweep
     __syncwarp();
     const long long line0 = grp * a.G;
     const long long rem = a.nlines - line0;
-    const int avail = int((rem < a.G ? rem : a.G) * a.n);
+    const int avail = SF ? kXlBuf : int((rem < a.G ? rem : a.G) * a.n);
     float* dst = (EPI == EPI_STORE ? a.out : a.acc) + line0 * a.n;
+#pragma unroll 4
     for (int c = L.lane; 4 * c < avail; c += 32) {
       const float4 s4 = *reinterpret_cast<const float4*>(buf + xl_chunk(c));
       float4* g4 = reinterpret_cast<float4*>(dst + 4 * c);
