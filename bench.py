@@ -59,10 +59,10 @@ WORKLOAD = {
 # read acc + u^n + u^{n-1}, write u^{n+1} + copy
 BYTES_PER_DOF = {"x": 8, "yz": 12, "last_update": 36, "update": 32}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per DOF per launch
-# from one ncu capture of each kernel on the 512 x 256 x 512 grid, scaled to a
-# full launch by the points processed (traffic grows with the points); a
-# kernel changed since its capture has no entry
-TRAFFIC_PER_DOF = {"wave_update_kernel (FP64 leapfrog update)": 31.37}
+# from one ncu capture of each kernel on the 512^3 step itself (one-pass
+# metrics); a kernel changed since its capture has no entry
+TRAFFIC_PER_DOF = {"wave_update_kernel (FP64 leapfrog update)": 31.65,
+                   "lanes_sweep_kernel ACC_ADD (y lines)": 11.61}
 
 
 def dist_env():

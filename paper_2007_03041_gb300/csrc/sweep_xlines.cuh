@@ -248,9 +248,14 @@ __device__ __forceinline__ void xl_apply_D(const XLineArgs& a, const XlLane& L, 
       // boundary constants in FP64 (Sec. 2.3 / 3.3): C_R near the left end,
       // C_L near the right end, one product chain per lane (the rare lanes
       // of short lines that need both take a second one)
+      // one FP64 product for the lines whose constant takes one total
+      // (periodic; Dirichlet lines longer than the decay's reach), a second
+      // for the rest: each FP64 instruction holds the narrow FP64 pipe for
+      // a warp's worth of lanes
       const float same = nR ? TR : TL, other = nR ? TL : TR;
-      const double ts = f2d(same), to = f2d(other);
-      const double C = a.needA && a.needB ? fma(a.kA, ts, a.kB * to) : (a.needA ? a.kA * ts : a.kB * to);
+      const double k1 = a.needA ? a.kA : a.kB;
+      double C = k1 * f2d(a.needA ? same : other);
+      if (a.needA && a.needB) C = fma(a.kB, f2d(other), C);
       if (nR) cR = fmaf(xl_qpow(a, L.s), d2f(C), cR);
       else cL = fmaf(xl_qpow(a, rs), d2f(C), cL);
       if (nR && nL) {
