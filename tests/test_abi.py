@@ -40,3 +40,21 @@ def test_binding_names_match_the_header():
     for name in declared_functions():
         if name != "molt_last_error":
             assert callable(getattr(M, name)), name
+
+
+def test_binding_constants_match_the_header_enums():
+    """Every enumerator `MOLT_<NAME> = <value>` of the header that the binding
+    exposes as `<NAME>` carries the same value (options, kernel kinds,
+    boundary types, operators, precisions, ...)."""
+    from paper_2007_03041_gb300 import molt as M
+    src = pathlib.Path(ROOT, "include", "molt.h").read_text()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    pairs = re.findall(r"\bMOLT_([A-Z0-9_]+)\s*=\s*(-?\d+)", src)
+    checked = 0
+    for name, value in pairs:
+        if hasattr(M, name):
+            assert getattr(M, name) == int(value), (name, getattr(M, name), value)
+            checked += 1
+    for name in ("OPT_LANES", "OPT_AXIS_STREAMS", "OPT_XLINES", "KERNEL_XLINES_ACC_SET", "KERNEL_LANES_ACC_ADD"):
+        assert hasattr(M, name), name
+    assert checked >= 30, checked
