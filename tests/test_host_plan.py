@@ -61,6 +61,19 @@ def test_the_preferred_tiles():
     assert many["points_per_lane"] == 16
 
 
+def test_fp64_points_per_lane_of_grids_with_few_lines():
+    """The FP64 rule for grids with few lines (one sweep at a time; the SM
+    count taken as 152 without a GPU): the measured-fastest points per lane
+    of the heat steps, 256^2 -> 4 (two warps a line), 512^2 -> 8 (two warps
+    a line, not one of 16 points a lane), 1024^2 and 2048^2 -> 16."""
+    want = {256: (4, 2), 512: (8, 2), 1024: (16, 2), 2048: (16, 4)}
+    for n, (E, nwl) in want.items():
+        for axis in (0, 1):
+            plan = M.molt_plan_sweep(M.make_desc((n, n), P=3, quad_points=3, prec=M.PREC_F64), axis, M.OP_0, 3,
+                                     0.6 * n)
+            assert (plan["points_per_lane"], plan["warps_per_line"]) == (E, nwl), (n, axis, plan)
+
+
 def test_refused_plans():
     with pytest.raises(M.MoltError):
         M.molt_plan_sweep(M.make_desc((8193,)), 0, M.OP_0, 1, 100.0)          # longer than 8192 points
